@@ -1,0 +1,18 @@
+"""Seeded synthetic inputs for correlation plenoptic imaging (CPI).
+
+This package is input infrastructure shared by the tests, the benchmark and the
+oracle checks.  It simulates the two detectors of a chaotic-light CPI set-up and
+lays their frames out in memory; it contains none of the correlation or
+refocusing arithmetic of the method itself.
+"""
+
+from .frames import (  # noqa: F401
+    Acquisition,
+    CONFIGS,
+    batched_acquisitions,
+    generate,
+    model_maps,
+    pack_bits_lsb,
+    pack_side_by_side,
+    uniform_planes,
+)
