@@ -1,0 +1,454 @@
+"""Benchmark of the CPI hot path on GB300.
+
+One step = one pass of the whole path over one acquisition of synthetic frames
+already resident in HBM: ingest (bit-unpack + transpose + marginal sums), the
+raw-moment tensor-core contraction, the int64 fold + FP64 Gamma of Eq. (1), and
+refocusing into P planes.  Default workload: 64x64 spatial vs 32x32 angular
+binary SPAD frames, N = 20000 bit-packed side by side, 32 refocusing planes.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  `value` is the whole-step throughput in
+int8-equivalent tera-operations per second, 2 * M_a * M_b * N / t_step, summed
+over ranks for N > 1 (independent replicas, one per GPU: the correlation of one
+acquisition needs no exchange between GPUs).  `--impl reference` times the CPU
+oracle (plain C, OpenMP) on a bounded sample of the same workload instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    # name: (acquisition key, planes)
+    "spad_1bit": ("spad_1bit", 32),
+    "small_u8": ("small_u8", 4),
+    "large_u8": ("large_u8", 128),
+}
+L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.device_index = device_index
+
+    def __enter__(self):
+        try:
+            import torch
+
+            uuid = str(torch.cuda.get_device_properties(self.device_index).uuid)
+            sel = ["-i", uuid if uuid.startswith("GPU-") else "GPU-" + uuid]
+        except Exception:
+            sel = []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", *sel, f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+        return False
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in getattr(self, "lines", []):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist_init(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def _barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def _max_over_ranks(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(acq, planes, frames_host, lay, n_rows: int, n_planes: int):
+    """Time the oracle on a bounded sample and extrapolate one full step.
+    Returns (seconds per full step, cores, description)."""
+    import numpy as np
+
+    import oracle
+
+    oracle.build()
+    ma = lay["a"]["height"] * lay["a"]["width"]
+    mb = lay["b"]["height"] * lay["b"]["width"]
+    n = acq.n_frames
+    t0 = time.perf_counter()
+    oracle.unpack(frames_host, lay["a"], n)
+    oracle.unpack(frames_host, lay["b"], n)
+    t_unpack = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    r = oracle.correlate(frames_host, lay["a"], frames_host, lay["b"], n, rows=(0, n_rows))
+    t_rows = time.perf_counter() - t0
+    per_row = max(t_rows - t_unpack, 1e-9) / n_rows
+    t_corr = t_unpack + per_row * ma
+    ha, wa = lay["a"]["height"], lay["a"]["width"]
+    hb, wb = lay["b"]["height"], lay["b"]["width"]
+    alpha, beta = planes
+    g = r["gamma"]
+    t0 = time.perf_counter()
+    oracle.refocus(g, ha, wa, hb, wb, alpha[:n_planes], beta[:n_planes])
+    t_ref = (time.perf_counter() - t0) * len(alpha) / n_planes
+    desc = (f"Eq.(1) rows 0..{n_rows} of {ma} (all {n} frames, unpack timed separately) and "
+            f"{n_planes} of {len(alpha)} planes; extrapolated linearly to one full step")
+    _ = np, mb
+    return t_corr + t_ref, oracle.threads(), desc
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_native(args, world, rank, local):
+    import torch
+
+    import paper_2407_20692_gb300 as cpi
+    import synth
+
+    cpi.load()
+    key, n_planes = WORKLOADS[args.workload]
+    acq = synth.frames.replace(synth.CONFIGS[key], seed=1000 + rank)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    A, B = synth.generate(acq, dev)
+    fr, lay = synth.pack_side_by_side(A, B, acq.bits)
+    del A, B
+    la, lb = lay["a"], lay["b"]
+    ha, wa, hb, wb = la["height"], la["width"], lb["height"], lb["width"]
+    ma, mb, n = ha * wa, hb * wb, acq.n_frames
+    mk = lambda t, l: cpi.frames(t, l["bits"], l["height"], l["width"], l["x0"], l["y0"],
+                                 l["row_stride"], l["frame_stride_bytes"])
+    a, b = mk(fr, la), mk(fr, lb)
+    ws = torch.empty(cpi.cpi_correlate_workspace_size(a, b, n), dtype=torch.uint8, device=dev)
+    s_ab = torch.empty((ma, mb), dtype=torch.int64, device=dev)
+    s_a = torch.empty(ma, dtype=torch.int64, device=dev)
+    s_b = torch.empty(mb, dtype=torch.int64, device=dev)
+    gamma = torch.empty((ma, mb), dtype=torch.float64, device=dev)
+    g32 = torch.empty((mb, ma), dtype=torch.float32, device=dev)
+    alpha, beta = synth.uniform_planes(n_planes)
+    planes = cpi.plane_array(alpha, beta)
+    rws = torch.empty(cpi.cpi_refocus_workspace_size(ha, wa, hb, wb, n_planes), dtype=torch.uint8, device=dev)
+    out = torch.empty((n_planes, ha, wa), dtype=torch.float32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        cpi.cpi_correlate_stage(cpi.CPI_STAGE_INGEST, a, b, n, 0, s_ab, s_a, s_b, gamma, g32, ws, stream)
+        if ev:
+            ev[1].record(stream)
+        cpi.cpi_correlate_stage(cpi.CPI_STAGE_MOMENTS, a, b, n, 0, s_ab, s_a, s_b, gamma, g32, ws, stream)
+        if ev:
+            ev[2].record(stream)
+        cpi.cpi_correlate_stage(cpi.CPI_STAGE_FOLD, a, b, n, 0, s_ab, s_a, s_b, gamma, g32, ws, stream)
+        if ev:
+            ev[3].record(stream)
+        cpi.cpi_refocus(g32, ha, wa, hb, wb, planes, out, rws, stream)
+        if ev:
+            ev[4].record(stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    if cpi.cpi_device_status() != 0:
+        raise RuntimeError("device status error during warm-up")
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    _barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        t_wall0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            step(evs[k])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+    _barrier(world)
+    if cpi.cpi_device_status() != 0:
+        raise RuntimeError("device status error in the timed region")
+    parts = [[ev[i].elapsed_time(ev[i + 1]) for i in range(4)] for ev in evs]
+    step_ms = [sum(p) for p in parts]
+    total_s = sum(step_ms) / 1e3
+    total_s_max = _max_over_ranks(world, total_s)
+    ops = 2.0 * ma * mb * n
+    value = world * ops * args.steps / total_s_max / 1e12
+    mean = lambda i: sum(p[i] for p in parts) / args.steps
+    ingest_ms, moments_ms, fold_ms, refocus_ms = mean(0), mean(1), mean(2), mean(3)
+
+    # ---------------------------------------------------------------- roofline
+    peaks, src = _peaks()
+    fp8_peak = 2.0 * peaks["bf16_tflops"]          # E4M3 pipe: BF16 measured x nominal 4.5/2.25
+    kernels = {
+        "moments": moments_ms, "refocus": refocus_ms, "ingest": ingest_ms, "fold": fold_ms,
+    }
+    dominant = max(kernels, key=kernels.get)
+    bytes_ingest = (ma + mb) * n / 8 + (ma + mb) * ws_row_bytes(n, acq.bits)
+    bytes_fold = ma * mb * (4 + 8 + 8 + 4)
+    bytes_refocus = n_planes * ma * mb * 4 + n_planes * ma * 4
+    if dominant == "moments":
+        ach = ops / (moments_ms / 1e3) / 1e12
+        roof = {"kernel": "moments (tcgen05 kind::f8f6f4, E4M3 0/1 operands)", "bound": "tensor",
+                "achieved": ach, "peak": fp8_peak, "unit": "TFLOP/s", "frac": ach / fp8_peak,
+                "traffic": None,
+                "peak_source": f"{src} bf16 burst x 2 (nominal E4M3/BF16 dense ratio)"}
+    else:
+        by = {"refocus": bytes_refocus, "ingest": bytes_ingest, "fold": bytes_fold}[dominant]
+        ach = by / (kernels[dominant] / 1e3) / 1e9
+        roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"{src} hbm copy"}
+
+    # ---------------------------------------------------------------- e2e through the C ABI
+    e2e = e2e_run(args, cpi, fr, lay, n, stream, dev, planes, n_planes, ws, rws)
+    e2e_value = world * ops / _max_over_ranks(world, e2e["s_per_step"]) / 1e12
+
+    # ---------------------------------------------------------------- CPU baseline (rank 0)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        host = fr.cpu().numpy()
+        t_cpu, cores, desc = oracle_sample(acq, (alpha, beta), host, lay, args.cpu_rows, args.cpu_planes)
+        cpu = {"value": ops / t_cpu / 1e12, "unit": "TOPS (int8-equivalent)", "cores": cores,
+               "kind": "oracle", "sample": desc, "s_per_step_extrapolated": t_cpu}
+
+    if rank != 0:
+        return None
+    clocks = clk.summary()
+    line = {
+        "metric": "Gamma int8-equivalent TOPS per whole step (ingest + raw-moment GEMM + fold/FP64 "
+                  "Gamma + refocus)",
+        "value": value,
+        "unit": "TOPS (int8-equivalent, 2*Ma*Mb*N per step)",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": sum(step_ms) / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u1 -> e4m3 tensor-core (exact fp32 partials), int64 sums, f64 Gamma, f32 refocus",
+        "data": "synthetic (seeded chaotic-light source model; stand-in for the SwissSPAD2 dataset)",
+        "config": {"workload": f"{args.workload}: spatial {ha}x{wa} vs angular {hb}x{wb}, "
+                               f"{'binary bit-packed' if acq.bits == 1 else 'uint8'} frames side by side, "
+                               f"N={n}, {n_planes} refocus planes",
+                   "M_a": ma, "M_b": mb, "N": n, "planes": n_planes,
+                   "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) between steps"},
+        "parts_ms": {"ingest": ingest_ms, "moments": moments_ms, "fold": fold_ms, "refocus": refocus_ms},
+        "gamma_tops": ops / ((ingest_ms + moments_ms + fold_ms) / 1e3) / 1e12,
+        "refocus_planes_per_s": n_planes / (refocus_ms / 1e3),
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": "TOPS (int8-equivalent)",
+                "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
+                "ms_per_step": e2e["s_per_step"] * 1e3},
+        "gpu_launches": 5 * args.steps,
+        "clocks": clocks,
+        "wall_s_timed_region": t_wall,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    return line
+
+
+def ws_row_bytes(n, bits):
+    pad = 256 if bits == 1 else 128
+    k = (n + pad - 1) // pad * pad
+    return k * (1 if bits == 1 else 2)
+
+
+def e2e_run(args, cpi, fr, lay, n, stream, dev, planes, n_planes, ws, rws):
+    """Same step through the public API with host buffers: pinned frames copied
+    in, Gamma (f64) and the refocused stack copied out, inside the timed region."""
+    import torch
+
+    la, lb = lay["a"], lay["b"]
+    ha, wa, hb, wb = la["height"], la["width"], lb["height"], lb["width"]
+    ma, mb = ha * wa, hb * wb
+    host_in = fr.cpu().pin_memory()
+    dev_in = torch.empty_like(fr)
+    s_ab = torch.empty((ma, mb), dtype=torch.int64, device=dev)
+    s_a = torch.empty(ma, dtype=torch.int64, device=dev)
+    s_b = torch.empty(mb, dtype=torch.int64, device=dev)
+    gamma = torch.empty((ma, mb), dtype=torch.float64, device=dev)
+    g32 = torch.empty((mb, ma), dtype=torch.float32, device=dev)
+    out = torch.empty((n_planes, ha, wa), dtype=torch.float32, device=dev)
+    host_g = torch.empty((ma, mb), dtype=torch.float64).pin_memory()
+    host_o = torch.empty((n_planes, ha, wa), dtype=torch.float32).pin_memory()
+    mk = lambda t, l: cpi.frames(t, l["bits"], l["height"], l["width"], l["x0"], l["y0"],
+                                 l["row_stride"], l["frame_stride_bytes"])
+    a, b = mk(dev_in, la), mk(dev_in, lb)
+
+    def one():
+        dev_in.copy_(host_in, non_blocking=True)
+        cpi.cpi_correlate(a, b, n, s_ab, s_a, s_b, gamma, g32, ws, stream)
+        cpi.cpi_refocus(g32, ha, wa, hb, wb, planes, out, rws, stream)
+        host_g.copy_(gamma, non_blocking=True)
+        host_o.copy_(out, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        one()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k = max(1, args.steps)
+    e0.record(stream)
+    for _ in range(k):
+        one()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    s = e0.elapsed_time(e1) / 1e3 / k
+    return {"s_per_step": s, "h2d": host_in.numel(),
+            "d2h": host_g.numel() * 8 + host_o.numel() * 4}
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, world, rank):
+    """The CPU oracle as it stands, on a bounded sample of each step (rank 0 only)."""
+    if rank != 0:
+        return None
+    import torch
+
+    import synth
+
+    key, n_planes = WORKLOADS[args.workload]
+    acq = synth.CONFIGS[key]
+    A, B = synth.generate(acq, "cuda" if torch.cuda.is_available() else "cpu")
+    fr, lay = synth.pack_side_by_side(A, B, acq.bits)
+    host = fr.cpu().numpy()
+    alpha, beta = synth.uniform_planes(n_planes)
+    ma = lay["a"]["height"] * lay["a"]["width"]
+    mb = lay["b"]["height"] * lay["b"]["width"]
+    ops = 2.0 * ma * mb * acq.n_frames
+    for _ in range(args.warmup):
+        oracle_sample(acq, (alpha, beta), host, lay, 8, 1)
+    times = []
+    desc, cores = "", 1
+    for _ in range(args.steps):
+        t, cores, desc = oracle_sample(acq, (alpha, beta), host, lay, args.cpu_rows, args.cpu_planes)
+        times.append(t)
+    s = sum(times) / len(times)
+    value = ops / s / 1e12
+    return {
+        "impl": "reference",
+        "metric": "Gamma int8-equivalent TOPS per whole step (ingest + raw-moment GEMM + fold/FP64 "
+                  "Gamma + refocus)",
+        "value": value, "unit": "TOPS (int8-equivalent, 2*Ma*Mb*N per step)", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8/int64/f64 (CPU oracle)",
+        "data": "synthetic (seeded chaotic-light source model)",
+        "config": {"workload": args.workload, "M_a": ma, "M_b": mb, "N": acq.n_frames, "planes": n_planes},
+        "cpu_baseline": {"value": value, "unit": "TOPS (int8-equivalent)", "cores": cores,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": value, "unit": "TOPS (int8-equivalent)", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="spad_1bit")
+    ap.add_argument("--cpu-rows", type=int, default=256)
+    ap.add_argument("--cpu-planes", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    world, rank, local = _dist_init(args)
+    if args.impl == "reference":
+        line = run_reference(args, world, rank)
+    else:
+        line = run_native(args, world, rank, local)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,207 @@
+/*
+ * cpi.h -- C ABI of the GB300 (sm_103a) correlation plenoptic imaging library.
+ *
+ * The library computes the two steps of the CPI processing chain described in
+ * "GPU-based data processing for speeding-up correlation plenoptic imaging"
+ * (arXiv 2407.20692):
+ *   1. the correlation function Gamma of Eq. (1) (Section "CPI algorithm",
+ *      item 1) between the frames of a spatial detector A and an angular
+ *      detector B, and
+ *   2. refocusing of Gamma into a stack of planes (Section "CPI algorithm",
+ *      item 2; Section 4.1, "Refocusing Optimization").
+ *
+ * Conventions for every entry point:
+ *   - Every buffer pointer is DEVICE memory owned by the caller, unless marked
+ *     "host".  The library never allocates device memory; scratch space is a
+ *     caller-provided workspace whose size is given by the *_workspace_size
+ *     queries.  The library keeps no pointer after a call returns.
+ *   - Work is enqueued asynchronously on `stream` (NULL = legacy default stream).
+ *     Argument errors are detected on the host and returned before anything is
+ *     launched.  A launch failure returns CPI_ERR_CUDA.
+ *   - Errors found by a kernel while it runs (a pipeline wait that exceeded its
+ *     time limit) are recorded in a per-device status word and returned by
+ *     cpi_device_status(); kernels never trap.
+ *   - Gamma and the raw sums use the index map row = A pixel, column = B pixel,
+ *     pixel index = y * width + x inside each image's region of interest.
+ *   - Not thread-safe for concurrent calls that share a workspace.
+ */
+#ifndef CPI_H
+#define CPI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define CPI_API __attribute__((visibility("default")))
+#else
+#define CPI_API
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *cpi_stream; /* a cudaStream_t */
+
+typedef enum cpi_status {
+    CPI_OK = 0,
+    CPI_ERR_INVALID_ARG = 1, /* a NULL/misaligned pointer, a bad size or descriptor */
+    CPI_ERR_OVERFLOW = 2,    /* N^2 * max(A) * max(B) >= 2^63: int64 exactness not guaranteed */
+    CPI_ERR_WORKSPACE = 3,   /* workspace NULL or smaller than the size query */
+    CPI_ERR_UNSUPPORTED = 4, /* a valid request this build does not implement */
+    CPI_ERR_CUDA = 5,        /* a CUDA runtime call or kernel launch failed */
+    CPI_ERR_TIMEOUT = 6      /* a device-side wait ran out of its time limit */
+} cpi_status;
+
+/*
+ * Frames of one detector image (Section 2 of the paper: each SwissSPAD2 frame is
+ * a 256 x 512 image holding A on the left and B on the right, 1 bit per pixel).
+ * Pixel (y, x) of the region, frame i, is element
+ *     e = (y0 + y) * row_stride + (x0 + x)
+ * of frame i, which starts at byte i * frame_stride_bytes of `data`:
+ *   bits == 8: byte e;   bits == 1: bit (e % 8) of byte e / 8, counted from the
+ *   least significant bit (bit_order 0) or the most significant (bit_order 1).
+ * A and B may point into the same frame buffer with different regions.
+ */
+typedef struct cpi_frames {
+    const void *data;           /* device pointer to frame 0; caller-owned */
+    int32_t bits;               /* 1 (bit-packed binary frames) or 8 (uint8 counts) */
+    int32_t height, width;      /* region size in pixels, each >= 1 */
+    int32_t x0, y0;             /* region origin inside the frame, >= 0 */
+    int64_t row_stride;         /* elements (pixels) between frame rows, >= x0 + width */
+    int64_t frame_stride_bytes; /* bytes between consecutive frames, > 0 */
+    int32_t bit_order;          /* 0 = LSB first, 1 = MSB first (bits == 1 only) */
+} cpi_frames;
+
+/* One refocusing plane: sample point alpha * x + beta * rho_b~ (see cpi_refocus). */
+typedef struct cpi_plane {
+    double alpha, beta;
+} cpi_plane;
+
+/* Human-readable name of a status code (static string). */
+CPI_API const char *cpi_status_string(cpi_status s);
+
+/* ABI version of this header: 1. */
+CPI_API int32_t cpi_abi_version(void);
+
+/* --------------------------------------------------------------------------
+ * Correlation function, Eq. (1):
+ *   Gamma[a][b] = (1/N) sum_i A_i[a] B_i[b] - (1/N sum_i A_i[a]) (1/N sum_i B_i[b])
+ * computed as exact integer sums
+ *   S_ab[a][b] = sum_i A_i[a] B_i[b],  S_a[a] = sum_i A_i[a],  S_b[b] = sum_i B_i[b]
+ * and one correctly rounded double division of the exact int64 numerator:
+ *   Gamma = (double)(N * S_ab - S_a * S_b) / ((double)N * (double)N).
+ * The integer products run on the tensor cores with exact FP32 partial sums
+ * (every partial sum is an integer below 2^24) folded into int32/int64, so S_ab,
+ * S_a, S_b are bit-exact and Gamma is bit-identical to the exact-numerator
+ * formula.  (Section "CPI algorithm"; Section 4.1, "Cross-correlation
+ * Optimization": the binary frames stay bit-packed in memory and are unpacked
+ * inside the correlation path.)
+ *
+ * Shapes: M_a = a->height * a->width, M_b = b->height * b->width.
+ *   s_ab  : int64 [M_a][M_b] row-major (required)
+ *   s_a   : int64 [M_a] (required),  s_b : int64 [M_b] (required)
+ *   gamma : double [M_a][M_b] row-major, or NULL to skip
+ *   gamma_f32 : float [M_b][M_a] ("slice-major": one M_a image per angular
+ *           pixel, the input layout of cpi_refocus), or NULL to skip
+ * Requirements: 1 <= n_frames; N^2 * max(A) * max(B) < 2^63 (else
+ * CPI_ERR_OVERFLOW); M_a, M_b <= 2^24; output pointers 16-byte aligned.
+ * -------------------------------------------------------------------------- */
+
+/* Workspace bytes cpi_correlate / cpi_correlate_accumulate / cpi_correlate_stage
+ * need for these descriptors and n_frames (0 on invalid arguments). */
+CPI_API size_t cpi_correlate_workspace_size(const cpi_frames *a, const cpi_frames *b, int64_t n_frames);
+
+/* Whole Eq. (1): overwrites s_ab, s_a, s_b, and gamma / gamma_f32 when non-NULL. */
+CPI_API cpi_status cpi_correlate(const cpi_frames *a, const cpi_frames *b, int64_t n_frames,
+                         int64_t *s_ab, int64_t *s_a, int64_t *s_b, double *gamma,
+                         float *gamma_f32, void *workspace, size_t workspace_bytes,
+                         cpi_stream stream);
+
+/* Streaming form (the paper processes the acquisition in blocks of files):
+ * ADDS this block's sums into s_ab, s_a, s_b.  Call cpi_correlate_finalize with
+ * the total frame count once every block has been added.  The running sums are
+ * the complete state of a correlation, so saving them checkpoints it. */
+CPI_API cpi_status cpi_correlate_accumulate(const cpi_frames *a, const cpi_frames *b, int64_t n_frames,
+                                    int64_t *s_ab, int64_t *s_a, int64_t *s_b, void *workspace,
+                                    size_t workspace_bytes, cpi_stream stream);
+
+/* Gamma from accumulated sums: n_total frames in all; m_a x m_b entries.
+ * gamma and/or gamma_f32 (layouts as above) may be NULL, not both. */
+CPI_API cpi_status cpi_correlate_finalize(const int64_t *s_ab, const int64_t *s_a, const int64_t *s_b,
+                                  int64_t m_a, int64_t m_b, int64_t n_total, double *gamma,
+                                  float *gamma_f32, cpi_stream stream);
+
+/* The three steps of cpi_correlate as separate calls, for timing and for
+ * overlapping them with other work.  Call them in order with identical
+ * arguments and the same workspace:
+ *   CPI_STAGE_INGEST : frames -> tensor-core operands (in the workspace) and the
+ *                      marginal sums s_a, s_b (Eq. (1) second term);
+ *   CPI_STAGE_MOMENTS: the raw-moment contraction sum_i A_i[a] B_i[b] into exact
+ *                      int32 partial sums per frame chunk (in the workspace);
+ *   CPI_STAGE_FOLD   : partial sums -> s_ab (int64), then gamma / gamma_f32 if
+ *                      non-NULL (with N = n_frames).
+ * accumulate != 0 adds into s_ab, s_a, s_b instead of overwriting them. */
+enum { CPI_STAGE_INGEST = 1, CPI_STAGE_MOMENTS = 2, CPI_STAGE_FOLD = 3 };
+CPI_API cpi_status cpi_correlate_stage(int32_t stage, const cpi_frames *a, const cpi_frames *b,
+                               int64_t n_frames, int32_t accumulate, int64_t *s_ab, int64_t *s_a,
+                               int64_t *s_b, double *gamma, float *gamma_f32, void *workspace,
+                               size_t workspace_bytes, cpi_stream stream);
+
+/* --------------------------------------------------------------------------
+ * Refocusing (Section "CPI algorithm", item 2; Section 4.1, "Refocusing
+ * Optimization": interpolation coordinates are computed on the fly inside the
+ * refocusing kernel).  The paper gives no formula; this library implements the
+ * per-plane shift-and-sum of Gamma over the angular pixels with bilinear
+ * interpolation in the spatial coordinate:
+ *   x  = (c - (wa-1)/2, r - (ha-1)/2)             centred spatial pixel (r, c)
+ *   rb = ((bc - (wb-1)/2) * wa/wb, (br - (hb-1)/2) * ha/hb)   scaled angular pixel
+ *   out[p][r][c] = sum over (br, bc) of  Gamma~(alpha_p * x + beta_p * rb ; (br, bc))
+ * where Gamma~(u; b) interpolates the spatial image Gamma[.][b] bilinearly at
+ * the centred point u, taps outside the ha x wa grid counting as 0.
+ * (alpha, beta) = (1, 0) is the plane the spatial detector is focused on.
+ *
+ *   gamma_f32 : float [hb*wb][ha*wa], slice-major (cpi_correlate's gamma_f32)
+ *   planes    : HOST array of n_planes (alpha, beta), finite
+ *   out       : float [n_planes][ha][wa]
+ * Sums use compensated FP32 accumulation; coordinates and weights are computed
+ * in double.  Requires ha, wa, hb, wb >= 1, wa <= 512, ha*wa <= 2^20.
+ * -------------------------------------------------------------------------- */
+CPI_API size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb,
+                                  int32_t n_planes);
+
+CPI_API cpi_status cpi_refocus(const float *gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
+                       const cpi_plane *planes, int32_t n_planes, float *out, void *workspace,
+                       size_t workspace_bytes, cpi_stream stream);
+
+/* --------------------------------------------------------------------------
+ * Learned denoiser of Gamma (a small convolutional network mapping Gamma from
+ * few frames to Gamma from many).  Not part of the paper's method; not
+ * implemented in this build: always returns CPI_ERR_UNSUPPORTED.
+ * -------------------------------------------------------------------------- */
+CPI_API cpi_status cpi_denoise(const void *model, const float *gamma_in, float *gamma_out, int32_t ha,
+                       int32_t wa, int32_t hb, int32_t wb, cpi_stream stream);
+
+/* --------------------------------------------------------------------------
+ * Device status.  Kernels record failures (a wait on a pipeline barrier that
+ * exceeded the time limit; the kernel then drains its own copies, frees its
+ * tensor memory and returns) in a status word of the current device.
+ * cpi_device_status synchronizes `stream`, reads the word and clears it when
+ * clear != 0.  Returns CPI_OK, CPI_ERR_TIMEOUT or CPI_ERR_CUDA.
+ * -------------------------------------------------------------------------- */
+CPI_API cpi_status cpi_device_status(cpi_stream stream, int32_t clear);
+
+/* Time limit of every device-side wait, in nanoseconds (default 2e9). */
+CPI_API void cpi_set_wait_timeout_ns(int64_t ns);
+
+/* Self-test of the failure path: launches one CTA that waits on a barrier
+ * nothing arrives on, with limit timeout_ns.  The wait gives up, the kernel
+ * records CPI_ERR_TIMEOUT in the status word and returns; the context stays
+ * usable.  Returns the launch status. */
+CPI_API cpi_status cpi_selftest_wait_timeout(int64_t timeout_ns, cpi_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CPI_H */

@@ -1,0 +1,214 @@
+"""Python binding of the GB300 correlation plenoptic imaging library (libcpi.so).
+
+Argument marshalling only: every entry point below forwards to the function of
+the same name in the C ABI (include/cpi.h) with raw device pointers taken from
+torch tensors.  All computation happens in the library's CUDA kernels; there is
+no fallback, and ``load()`` raises if the library cannot be built or loaded.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+__all__ = [
+    "CpiError", "load", "frames", "plane_array", "cpi_status_string", "cpi_abi_version",
+    "cpi_correlate_workspace_size", "cpi_correlate", "cpi_correlate_accumulate",
+    "cpi_correlate_finalize", "cpi_correlate_stage", "cpi_refocus_workspace_size", "cpi_refocus",
+    "cpi_denoise", "cpi_device_status", "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout",
+    "CPI_STAGE_INGEST", "CPI_STAGE_MOMENTS", "CPI_STAGE_FOLD", "EXPORTED",
+]
+
+CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD = 1, 2, 3
+STATUS = {0: "CPI_OK", 1: "CPI_ERR_INVALID_ARG", 2: "CPI_ERR_OVERFLOW", 3: "CPI_ERR_WORKSPACE",
+          4: "CPI_ERR_UNSUPPORTED", 5: "CPI_ERR_CUDA", 6: "CPI_ERR_TIMEOUT"}
+
+# Every symbol include/cpi.h declares.
+EXPORTED = [
+    "cpi_status_string", "cpi_abi_version", "cpi_correlate_workspace_size", "cpi_correlate",
+    "cpi_correlate_accumulate", "cpi_correlate_finalize", "cpi_correlate_stage",
+    "cpi_refocus_workspace_size", "cpi_refocus", "cpi_denoise", "cpi_device_status",
+    "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout",
+]
+
+
+class CpiError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+class cpi_frames(ctypes.Structure):
+    _fields_ = [
+        ("data", ctypes.c_void_p),
+        ("bits", ctypes.c_int32),
+        ("height", ctypes.c_int32),
+        ("width", ctypes.c_int32),
+        ("x0", ctypes.c_int32),
+        ("y0", ctypes.c_int32),
+        ("row_stride", ctypes.c_int64),
+        ("frame_stride_bytes", ctypes.c_int64),
+        ("bit_order", ctypes.c_int32),
+    ]
+
+
+class cpi_plane(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+_F = ctypes.POINTER(cpi_frames)
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(path: str | None = None):
+    """Load libcpi.so (building it first when missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if path is None:
+        path = _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not found: {path}")
+    lib = ctypes.CDLL(path)
+    i32, i64, sz, st = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_int
+    sig = {
+        "cpi_status_string": ([st], ctypes.c_char_p),
+        "cpi_abi_version": ([], i32),
+        "cpi_correlate_workspace_size": ([_F, _F, i64], sz),
+        "cpi_correlate": ([_F, _F, i64, _P, _P, _P, _P, _P, _P, sz, _P], st),
+        "cpi_correlate_accumulate": ([_F, _F, i64, _P, _P, _P, _P, sz, _P], st),
+        "cpi_correlate_finalize": ([_P, _P, _P, i64, i64, i64, _P, _P, _P], st),
+        "cpi_correlate_stage": ([i32, _F, _F, i64, i32, _P, _P, _P, _P, _P, _P, sz, _P], st),
+        "cpi_refocus_workspace_size": ([i32, i32, i32, i32, i32], sz),
+        "cpi_refocus": ([_P, i32, i32, i32, i32, ctypes.POINTER(cpi_plane), i32, _P, _P, sz, _P], st),
+        "cpi_denoise": ([_P, _P, _P, i32, i32, i32, i32, _P], st),
+        "cpi_device_status": ([_P, i32], st),
+        "cpi_set_wait_timeout_ns": ([i64], None),
+        "cpi_selftest_wait_timeout": ([i64, _P], st),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+# ----------------------------------------------------------------------------- helpers
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(int(stream.cuda_stream)) if hasattr(stream, "cuda_stream") else ctypes.c_void_p(stream)
+
+
+def _check(code: int, where: str):
+    if code != 0:
+        raise CpiError(code, where)
+
+
+def frames(data, bits: int, height: int, width: int, x0: int = 0, y0: int = 0,
+           row_stride: int | None = None, frame_stride_bytes: int | None = None,
+           bit_order: int = 0) -> cpi_frames:
+    """Descriptor of one detector region inside a frame buffer (a CUDA uint8 tensor
+    or a raw device address)."""
+    addr = data.data_ptr() if hasattr(data, "data_ptr") else int(data)
+    rs = row_stride if row_stride is not None else width
+    fs = frame_stride_bytes
+    if fs is None:
+        fs = height * rs if bits == 8 else (height * rs + 7) // 8
+    return cpi_frames(addr, bits, height, width, x0, y0, rs, fs, bit_order)
+
+
+def plane_array(alpha, beta):
+    n = len(alpha)
+    arr = (cpi_plane * n)()
+    for i in range(n):
+        arr[i].alpha = float(alpha[i])
+        arr[i].beta = float(beta[i])
+    return arr
+
+
+# ----------------------------------------------------------------------------- entry points
+
+def cpi_status_string(code: int) -> str:
+    return load().cpi_status_string(code).decode()
+
+
+def cpi_abi_version() -> int:
+    return load().cpi_abi_version()
+
+
+def cpi_correlate_workspace_size(a: cpi_frames, b: cpi_frames, n_frames: int) -> int:
+    return load().cpi_correlate_workspace_size(ctypes.byref(a), ctypes.byref(b), n_frames)
+
+
+def cpi_correlate(a, b, n_frames, s_ab, s_a, s_b, gamma, gamma_f32, workspace, stream=None):
+    _check(load().cpi_correlate(ctypes.byref(a), ctypes.byref(b), n_frames, _ptr(s_ab), _ptr(s_a),
+                                _ptr(s_b), _ptr(gamma), _ptr(gamma_f32), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream)),
+           "cpi_correlate")
+
+
+def cpi_correlate_accumulate(a, b, n_frames, s_ab, s_a, s_b, workspace, stream=None):
+    _check(load().cpi_correlate_accumulate(ctypes.byref(a), ctypes.byref(b), n_frames, _ptr(s_ab),
+                                           _ptr(s_a), _ptr(s_b), _ptr(workspace),
+                                           workspace.numel() * workspace.element_size(),
+                                           _stream(stream)), "cpi_correlate_accumulate")
+
+
+def cpi_correlate_finalize(s_ab, s_a, s_b, m_a, m_b, n_total, gamma, gamma_f32, stream=None):
+    _check(load().cpi_correlate_finalize(_ptr(s_ab), _ptr(s_a), _ptr(s_b), m_a, m_b, n_total,
+                                         _ptr(gamma), _ptr(gamma_f32), _stream(stream)),
+           "cpi_correlate_finalize")
+
+
+def cpi_correlate_stage(stage, a, b, n_frames, accumulate, s_ab, s_a, s_b, gamma, gamma_f32,
+                        workspace, stream=None):
+    _check(load().cpi_correlate_stage(stage, ctypes.byref(a), ctypes.byref(b), n_frames,
+                                      1 if accumulate else 0, _ptr(s_ab), _ptr(s_a), _ptr(s_b),
+                                      _ptr(gamma), _ptr(gamma_f32), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), _stream(stream)),
+           "cpi_correlate_stage")
+
+
+def cpi_refocus_workspace_size(ha, wa, hb, wb, n_planes) -> int:
+    return load().cpi_refocus_workspace_size(ha, wa, hb, wb, n_planes)
+
+
+def cpi_refocus(gamma_f32, ha, wa, hb, wb, planes, out, workspace, stream=None):
+    """planes: a ctypes array from plane_array() (host memory)."""
+    _check(load().cpi_refocus(_ptr(gamma_f32), ha, wa, hb, wb, planes, len(planes), _ptr(out),
+                              _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              _stream(stream)), "cpi_refocus")
+
+
+def cpi_denoise(model, gamma_in, gamma_out, ha, wa, hb, wb, stream=None):
+    _check(load().cpi_denoise(None if model is None else ctypes.c_void_p(model), _ptr(gamma_in),
+                              _ptr(gamma_out), ha, wa, hb, wb, _stream(stream)), "cpi_denoise")
+
+
+def cpi_device_status(stream=None, clear: bool = True) -> int:
+    return load().cpi_device_status(_stream(stream), 1 if clear else 0)
+
+
+def cpi_set_wait_timeout_ns(ns: int) -> None:
+    load().cpi_set_wait_timeout_ns(int(ns))
+
+
+def cpi_selftest_wait_timeout(timeout_ns: int, stream=None):
+    _check(load().cpi_selftest_wait_timeout(int(timeout_ns), _stream(stream)),
+           "cpi_selftest_wait_timeout")

@@ -1,0 +1,416 @@
+// C ABI of the library (include/cpi.h): argument validation, the execution plan
+// of the correlation (operand format, tiles, frame chunks, workspace layout),
+// TMA descriptors, launches and the per-device status word.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+
+#include "../../include/cpi.h"
+#include "kernels.cuh"
+
+namespace cpi {
+
+// Status word of each device that loads the library (kernels atomically OR
+// error bits into it).  A file-scope __device__ variable: no allocation.
+__device__ unsigned int g_device_status;
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+constexpr int64_t kMaxPixels = (int64_t)1 << 24;
+constexpr int kChunkFrames = 32768;       // exactness bound of one int32 partial slot
+unsigned long long g_timeout_ns = 2000000000ull;
+
+struct DeviceInfo {
+    bool ready = false;
+    int sm_count = 0;
+    unsigned int* status = nullptr;       // device address of g_device_status
+};
+DeviceInfo g_dev[kMaxDevices];
+std::mutex g_dev_mu;
+
+cudaError_t device_info(DeviceInfo** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    DeviceInfo& d = g_dev[dev];
+    if (!d.ready) {
+        e = cudaDeviceGetAttribute(&d.sm_count, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return e;
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_device_status);
+        if (e != cudaSuccess) return e;
+        d.status = static_cast<unsigned int*>(p);
+        d.ready = true;
+    }
+    *out = &d;
+    return cudaSuccess;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2-D K-major operand [rows][kstride_bytes], tile box = 128 bytes x box_rows, 128B swizzle.
+bool make_operand_map(CUtensorMap* m, void* base, bool bf16, int64_t rows, int64_t kstride_bytes,
+                      int box_rows) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const int elem = bf16 ? 2 : 1;
+    cuuint64_t dims[2] = {(cuuint64_t)(kstride_bytes / elem), (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)kstride_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                     base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+cpi_status check_frames(const cpi_frames* f) {
+    if (!f || !f->data) return CPI_ERR_INVALID_ARG;
+    if (f->bits != 1 && f->bits != 8) return CPI_ERR_INVALID_ARG;
+    if (f->height < 1 || f->width < 1 || f->x0 < 0 || f->y0 < 0) return CPI_ERR_INVALID_ARG;
+    if (f->bit_order != 0 && f->bit_order != 1) return CPI_ERR_INVALID_ARG;
+    if (f->bits == 8 && f->bit_order != 0) return CPI_ERR_INVALID_ARG;
+    if (f->row_stride < (int64_t)f->x0 + f->width || f->frame_stride_bytes <= 0)
+        return CPI_ERR_INVALID_ARG;
+    if ((int64_t)f->height * f->width > kMaxPixels) return CPI_ERR_INVALID_ARG;
+    // the region must lie inside one frame
+    const int64_t last = ((int64_t)f->y0 + f->height - 1) * f->row_stride + f->x0 + f->width - 1;
+    const int64_t last_byte = f->bits == 8 ? last : last / 8;
+    if (last_byte >= f->frame_stride_bytes) return CPI_ERR_INVALID_ARG;
+    return CPI_OK;
+}
+
+FramesDev to_dev(const cpi_frames* f) {
+    FramesDev d;
+    d.data = static_cast<const uint8_t*>(f->data);
+    d.bits = f->bits;
+    d.height = f->height;
+    d.width = f->width;
+    d.x0 = f->x0;
+    d.y0 = f->y0;
+    d.row_stride = f->row_stride;
+    d.frame_stride = f->frame_stride_bytes;
+    d.bit_order = f->bit_order;
+    return d;
+}
+
+// Execution plan of one correlation.
+struct CorrPlan {
+    bool bf16;                 // BF16 operands (any 8-bit input) or FP8 (both binary)
+    int64_t Ma, Mb, n;
+    int64_t kstride_bytes;     // operand row length in bytes (frames padded to the ingest tile)
+    int k_blocks, kb_per_chunk, kb_per_fold, n_chunks;
+    int block_n, tiles_m, tiles_n, n_units;
+    size_t off_a, off_b, off_part, ws_bytes;
+};
+
+cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm_count,
+                     CorrPlan* pl) {
+    cpi_status s = check_frames(a);
+    if (s != CPI_OK) return s;
+    s = check_frames(b);
+    if (s != CPI_OK) return s;
+    if (n < 1 || n > ((int64_t)1 << 31) - 1) return CPI_ERR_INVALID_ARG;
+    const double va = a->bits == 1 ? 1.0 : 255.0, vb = b->bits == 1 ? 1.0 : 255.0;
+    if ((double)n * (double)n * va * vb >= 9.2e18) return CPI_ERR_OVERFLOW;
+    CorrPlan p{};
+    p.bf16 = !(a->bits == 1 && b->bits == 1);
+    p.Ma = (int64_t)a->height * a->width;
+    p.Mb = (int64_t)b->height * b->width;
+    p.n = n;
+    const int fpc = ingest_frames_per_cta(p.bf16);
+    const int64_t kpad = (int64_t)round_up((size_t)n, (size_t)fpc);
+    const int elem = p.bf16 ? 2 : 1;
+    p.kstride_bytes = kpad * elem;
+    const MomentsShape sh = moments_shape(p.bf16);
+    p.k_blocks = (int)(kpad / sh.k_per_block);
+    p.block_n = sh.block_n;
+    p.tiles_m = (int)((p.Ma + 127) / 128);
+    p.tiles_n = (int)((p.Mb + p.block_n - 1) / p.block_n);
+    const int max_kb_chunk = kChunkFrames / sh.k_per_block;
+    p.kb_per_fold = p.bf16 ? 256 / sh.k_per_block : max_kb_chunk;
+    const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;
+    int n_chunks = (p.k_blocks + max_kb_chunk - 1) / max_kb_chunk;
+    if (tiles < sm_count) {
+        // small outputs: split the frames further so every SM gets work, but keep
+        // each chunk at least one exact-fold segment long
+        int want = (int)(sm_count / tiles);
+        int max_by_len = p.k_blocks / (p.bf16 ? p.kb_per_fold : 8);
+        if (max_by_len < 1) max_by_len = 1;
+        if (want > max_by_len) want = max_by_len;
+        if (want > n_chunks) n_chunks = want;
+    }
+    p.kb_per_chunk = (p.k_blocks + n_chunks - 1) / n_chunks;
+    if (p.bf16) p.kb_per_chunk = (int)round_up((size_t)p.kb_per_chunk, (size_t)p.kb_per_fold);
+    if (p.kb_per_chunk > max_kb_chunk) p.kb_per_chunk = max_kb_chunk;
+    p.n_chunks = (p.k_blocks + p.kb_per_chunk - 1) / p.kb_per_chunk;
+    const int64_t units = tiles * p.n_chunks;
+    if (units > 0x7fffffff) return CPI_ERR_UNSUPPORTED;
+    p.n_units = (int)units;
+    p.off_a = 0;
+    p.off_b = round_up(p.off_a + (size_t)p.Ma * (size_t)p.kstride_bytes, 1024);
+    p.off_part = round_up(p.off_b + (size_t)p.Mb * (size_t)p.kstride_bytes, 1024);
+    p.ws_bytes = round_up(p.off_part + (size_t)p.n_chunks * (size_t)p.Ma * (size_t)p.Mb * 4, 1024);
+    *pl = p;
+    return CPI_OK;
+}
+
+cpi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CPI_OK : CPI_ERR_CUDA; }
+
+cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const cpi_frames* b,
+                     int accumulate, int64_t* s_ab, int64_t* s_a, int64_t* s_b, double* gamma,
+                     float* gamma_f32, void* ws, DeviceInfo* dev, cudaStream_t st) {
+    uint8_t* w = static_cast<uint8_t*>(ws);
+    uint8_t* op_a = w + pl.off_a;
+    uint8_t* op_b = w + pl.off_b;
+    int32_t* part = reinterpret_cast<int32_t*>(w + pl.off_part);
+    if (stage == CPI_STAGE_INGEST) {
+        if (!accumulate) {
+            cudaError_t e = cudaMemsetAsync(s_a, 0, (size_t)pl.Ma * 8, st);
+            if (e == cudaSuccess) e = cudaMemsetAsync(s_b, 0, (size_t)pl.Mb * 8, st);
+            if (e != cudaSuccess) return CPI_ERR_CUDA;
+        }
+        return cuda_status(launch_ingest(pl.bf16, to_dev(a), to_dev(b), pl.n, pl.kstride_bytes,
+                                         op_a, op_b, s_a, s_b, st));
+    }
+    if (stage == CPI_STAGE_MOMENTS) {
+        CUtensorMap tm_a, tm_b;
+        if (!make_operand_map(&tm_a, op_a, pl.bf16, pl.Ma, pl.kstride_bytes, 128) ||
+            !make_operand_map(&tm_b, op_b, pl.bf16, pl.Mb, pl.kstride_bytes, pl.block_n))
+            return CPI_ERR_CUDA;
+        MomentsParams p{};
+        p.partial = part;
+        p.M = (int32_t)pl.Ma;
+        p.N = (int32_t)pl.Mb;
+        p.k_blocks = pl.k_blocks;
+        p.kb_per_chunk = pl.kb_per_chunk;
+        p.kb_per_fold = pl.kb_per_fold;
+        p.n_chunks = pl.n_chunks;
+        p.tiles_m = pl.tiles_m;
+        p.tiles_n = pl.tiles_n;
+        p.n_units = pl.n_units;
+        p.status = dev->status;
+        p.timeout_ns = g_timeout_ns;
+        const int grid = pl.n_units < dev->sm_count ? pl.n_units : dev->sm_count;
+        return cuda_status(launch_moments(pl.bf16, tm_a, tm_b, p, grid, st));
+    }
+    if (stage == CPI_STAGE_FOLD) {
+        return cuda_status(launch_fold(part, pl.n_chunks, pl.Ma, pl.Mb, s_ab, accumulate, 1, s_a,
+                                       s_b, pl.n, gamma, gamma_f32, st));
+    }
+    return CPI_ERR_INVALID_ARG;
+}
+
+cpi_status correlate_common(const int32_t* stages, int n_stages, const cpi_frames* a,
+                            const cpi_frames* b, int64_t n_frames, int accumulate, int64_t* s_ab,
+                            int64_t* s_a, int64_t* s_b, double* gamma, float* gamma_f32, void* ws,
+                            size_t ws_bytes, cpi_stream stream) {
+    DeviceInfo* dev = nullptr;
+    if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+    CorrPlan pl;
+    cpi_status s = make_plan(a, b, n_frames, dev->sm_count, &pl);
+    if (s != CPI_OK) return s;
+    if (!s_ab || !s_a || !s_b || !aligned(s_ab, 16) || !aligned(s_a, 16) || !aligned(s_b, 16))
+        return CPI_ERR_INVALID_ARG;
+    if ((gamma && !aligned(gamma, 16)) || (gamma_f32 && !aligned(gamma_f32, 16)))
+        return CPI_ERR_INVALID_ARG;
+    if (!ws || ws_bytes < pl.ws_bytes || !aligned(ws, 256)) return CPI_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int i = 0; i < n_stages; ++i) {
+        s = run_stage(stages[i], pl, a, b, accumulate, s_ab, s_a, s_b, gamma, gamma_f32, ws, dev,
+                      st);
+        if (s != CPI_OK) return s;
+    }
+    return CPI_OK;
+}
+
+}  // namespace
+}  // namespace cpi
+
+using namespace cpi;
+
+extern "C" {
+
+const char* cpi_status_string(cpi_status s) {
+    switch (s) {
+        case CPI_OK: return "CPI_OK";
+        case CPI_ERR_INVALID_ARG: return "CPI_ERR_INVALID_ARG";
+        case CPI_ERR_OVERFLOW: return "CPI_ERR_OVERFLOW";
+        case CPI_ERR_WORKSPACE: return "CPI_ERR_WORKSPACE";
+        case CPI_ERR_UNSUPPORTED: return "CPI_ERR_UNSUPPORTED";
+        case CPI_ERR_CUDA: return "CPI_ERR_CUDA";
+        case CPI_ERR_TIMEOUT: return "CPI_ERR_TIMEOUT";
+    }
+    return "CPI_ERR_UNKNOWN";
+}
+
+int32_t cpi_abi_version(void) { return 1; }
+
+size_t cpi_correlate_workspace_size(const cpi_frames* a, const cpi_frames* b, int64_t n_frames) {
+    DeviceInfo* dev = nullptr;
+    int sm = 152;
+    if (device_info(&dev) == cudaSuccess) sm = dev->sm_count;
+    CorrPlan pl;
+    if (make_plan(a, b, n_frames, sm, &pl) != CPI_OK) return 0;
+    return pl.ws_bytes;
+}
+
+cpi_status cpi_correlate(const cpi_frames* a, const cpi_frames* b, int64_t n_frames,
+                         int64_t* s_ab, int64_t* s_a, int64_t* s_b, double* gamma,
+                         float* gamma_f32, void* workspace, size_t workspace_bytes,
+                         cpi_stream stream) {
+    static const int32_t stages[3] = {CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD};
+    return correlate_common(stages, 3, a, b, n_frames, 0, s_ab, s_a, s_b, gamma, gamma_f32,
+                            workspace, workspace_bytes, stream);
+}
+
+cpi_status cpi_correlate_accumulate(const cpi_frames* a, const cpi_frames* b, int64_t n_frames,
+                                    int64_t* s_ab, int64_t* s_a, int64_t* s_b, void* workspace,
+                                    size_t workspace_bytes, cpi_stream stream) {
+    static const int32_t stages[3] = {CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD};
+    return correlate_common(stages, 3, a, b, n_frames, 1, s_ab, s_a, s_b, nullptr, nullptr,
+                            workspace, workspace_bytes, stream);
+}
+
+cpi_status cpi_correlate_stage(int32_t stage, const cpi_frames* a, const cpi_frames* b,
+                               int64_t n_frames, int32_t accumulate, int64_t* s_ab, int64_t* s_a,
+                               int64_t* s_b, double* gamma, float* gamma_f32, void* workspace,
+                               size_t workspace_bytes, cpi_stream stream) {
+    if (stage < CPI_STAGE_INGEST || stage > CPI_STAGE_FOLD) return CPI_ERR_INVALID_ARG;
+    return correlate_common(&stage, 1, a, b, n_frames, accumulate ? 1 : 0, s_ab, s_a, s_b, gamma,
+                            gamma_f32, workspace, workspace_bytes, stream);
+}
+
+cpi_status cpi_correlate_finalize(const int64_t* s_ab, const int64_t* s_a, const int64_t* s_b,
+                                  int64_t m_a, int64_t m_b, int64_t n_total, double* gamma,
+                                  float* gamma_f32, cpi_stream stream) {
+    if (!s_ab || !s_a || !s_b || (!gamma && !gamma_f32)) return CPI_ERR_INVALID_ARG;
+    if (m_a < 1 || m_b < 1 || m_a > kMaxPixels || m_b > kMaxPixels || n_total < 1)
+        return CPI_ERR_INVALID_ARG;
+    if (!aligned(s_ab, 8) || !aligned(s_a, 8) || !aligned(s_b, 8)) return CPI_ERR_INVALID_ARG;
+    if ((gamma && !aligned(gamma, 8)) || (gamma_f32 && !aligned(gamma_f32, 4)))
+        return CPI_ERR_INVALID_ARG;
+    if ((double)n_total * (double)n_total * 65025.0 >= 9.2e18) return CPI_ERR_OVERFLOW;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return cuda_status(launch_fold(nullptr, 0, m_a, m_b, const_cast<int64_t*>(s_ab), 1, 0, s_a, s_b,
+                                   n_total, gamma, gamma_f32, st));
+}
+
+size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb,
+                                  int32_t n_planes) {
+    if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || n_planes < 1) return 0;
+    DeviceInfo* dev = nullptr;
+    int sm = 152;
+    if (device_info(&dev) == cudaSuccess) sm = dev->sm_count;
+    const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
+    const int ranges = refocus_ranges(hb, wb, per_launch, sm);
+    return round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(double), 256);
+}
+
+cpi_status cpi_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
+                       const cpi_plane* planes, int32_t n_planes, float* out, void* workspace,
+                       size_t workspace_bytes, cpi_stream stream) {
+    if (!gamma_f32 || !planes || !out || n_planes < 1) return CPI_ERR_INVALID_ARG;
+    if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || wa > 512) return CPI_ERR_INVALID_ARG;
+    if ((int64_t)hb * wb > kMaxPixels) return CPI_ERR_INVALID_ARG;
+    if (refocus_smem_bytes(ha, wa) > 200 * 1024) return CPI_ERR_UNSUPPORTED;
+    if (!aligned(gamma_f32, 4) || !aligned(out, 4)) return CPI_ERR_INVALID_ARG;
+    for (int i = 0; i < n_planes; ++i)
+        if (!std::isfinite(planes[i].alpha) || !std::isfinite(planes[i].beta))
+            return CPI_ERR_INVALID_ARG;
+    DeviceInfo* dev = nullptr;
+    if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+    const size_t need = cpi_refocus_workspace_size(ha, wa, hb, wb, n_planes);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return CPI_ERR_WORKSPACE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
+    const int ranges = refocus_ranges(hb, wb, per_launch, dev->sm_count);
+    const int nb = hb * wb;
+    double* partial = static_cast<double*>(workspace);
+    PlaneBlock pb;
+    for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {
+        const int np = n_planes - p0 < kRefocusMaxPlanesPerLaunch ? n_planes - p0
+                                                                  : kRefocusMaxPlanesPerLaunch;
+        std::memset(&pb, 0, sizeof(pb));
+        for (int i = 0; i < np; ++i) {
+            pb.alpha[i] = planes[p0 + i].alpha;
+            pb.beta[i] = planes[p0 + i].beta;
+        }
+        RefocusGeom g{};
+        g.ha = ha;
+        g.wa = wa;
+        g.hb = hb;
+        g.wb = wb;
+        g.n_ranges = ranges;
+        g.b_per_range = (nb + ranges - 1) / ranges;
+        g.n_planes = np;
+        g.plane_offset = p0;
+        g.total_planes = n_planes;
+        cudaError_t e = launch_refocus(gamma_f32, g, pb, partial, st);
+        if (e != cudaSuccess) return CPI_ERR_CUDA;
+    }
+    return cuda_status(
+        launch_refocus_reduce(partial, ranges, (int64_t)n_planes * ha * wa, out, st));
+}
+
+cpi_status cpi_denoise(const void* model, const float* gamma_in, float* gamma_out, int32_t ha,
+                       int32_t wa, int32_t hb, int32_t wb, cpi_stream stream) {
+    (void)model, (void)gamma_in, (void)gamma_out, (void)ha, (void)wa, (void)hb, (void)wb,
+        (void)stream;
+    return CPI_ERR_UNSUPPORTED;
+}
+
+cpi_status cpi_device_status(cpi_stream stream, int32_t clear) {
+    DeviceInfo* dev = nullptr;
+    if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CPI_ERR_CUDA;
+    unsigned int word = 0;
+    if (cudaMemcpyFromSymbol(&word, g_device_status, sizeof(word)) != cudaSuccess)
+        return CPI_ERR_CUDA;
+    if (clear && word) {
+        const unsigned int zero = 0;
+        if (cudaMemcpyToSymbol(g_device_status, &zero, sizeof(zero)) != cudaSuccess)
+            return CPI_ERR_CUDA;
+    }
+    return (word & kStatusTimeoutBit) ? CPI_ERR_TIMEOUT : CPI_OK;
+}
+
+void cpi_set_wait_timeout_ns(int64_t ns) {
+    g_timeout_ns = ns > 0 ? (unsigned long long)ns : 2000000000ull;
+}
+
+cpi_status cpi_selftest_wait_timeout(int64_t timeout_ns, cpi_stream stream) {
+    if (timeout_ns <= 0 || timeout_ns > 10000000000ll) return CPI_ERR_INVALID_ARG;
+    DeviceInfo* dev = nullptr;
+    if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+    return cuda_status(launch_wait_selftest(dev->status, (unsigned long long)timeout_ns,
+                                            reinterpret_cast<cudaStream_t>(stream)));
+}
+
+}  // extern "C"

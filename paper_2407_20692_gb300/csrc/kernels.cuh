@@ -1,0 +1,86 @@
+// Host-side declarations shared by the library's translation units: kernel
+// parameter blocks and launchers.  Nothing here is part of the public ABI.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+namespace cpi {
+
+// Status bits recorded by kernels in the per-device status word.
+constexpr unsigned int kStatusTimeoutBit = 1u;
+
+// One detector image's frames as the kernels see them (validated copy of cpi_frames).
+struct FramesDev {
+    const uint8_t* data;
+    int32_t bits, height, width, x0, y0;
+    int64_t row_stride, frame_stride;
+    int32_t bit_order;
+};
+
+// ------------------------------------------------------------------ ingest
+// Frames -> K-major tensor-core operands [M][kstride] and marginal sums.
+// kBf16: values as BF16 (any bit depth); else 1-bit values as FP8 E4M3.
+constexpr int kIngestPixels = 32;                 // pixels per CTA
+constexpr int kIngestRowBytes = 256;              // operand bytes per pixel per CTA
+inline int ingest_frames_per_cta(bool bf16) { return bf16 ? 128 : 256; }
+
+cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int64_t n_frames,
+                          int64_t kstride_bytes, uint8_t* op_a, uint8_t* op_b, int64_t* s_a,
+                          int64_t* s_b, cudaStream_t st);
+
+// ------------------------------------------------------------------ moments
+struct MomentsParams {
+    int32_t* partial;        // [n_chunks][M][N] exact partial sums
+    int32_t M, N;            // A pixels (rows), B pixels (columns)
+    int32_t k_blocks;        // K blocks of 128 bytes per operand row
+    int32_t kb_per_chunk;    // K blocks per frame chunk (one partial slot each)
+    int32_t kb_per_fold;     // K blocks per exact FP32 segment (BF16 path)
+    int32_t n_chunks, tiles_m, tiles_n, n_units;
+    unsigned int* status;
+    unsigned long long timeout_ns;
+};
+
+struct MomentsShape {
+    int block_n;             // N tile
+    int k_per_block;         // elements per K block (128 bytes)
+    int stages;
+    size_t smem_bytes;
+};
+MomentsShape moments_shape(bool bf16);
+
+cudaError_t launch_moments(bool bf16, const CUtensorMap& tm_a, const CUtensorMap& tm_b,
+                           const MomentsParams& p, int grid, cudaStream_t st);
+
+// ------------------------------------------------------------------ fold / finalize
+cudaError_t launch_fold(const int32_t* partial, int n_chunks, int64_t M, int64_t N,
+                        int64_t* s_ab, int accumulate, int write_sab, const int64_t* s_a,
+                        const int64_t* s_b, int64_t n_frames, double* gamma, float* gamma_f32,
+                        cudaStream_t st);
+
+// ------------------------------------------------------------------ refocus
+constexpr int kRefocusMaxPlanesPerLaunch = 128;
+struct PlaneBlock {
+    double alpha[kRefocusMaxPlanesPerLaunch];
+    double beta[kRefocusMaxPlanesPerLaunch];
+};
+struct RefocusGeom {
+    int32_t ha, wa, hb, wb;
+    int32_t n_ranges, b_per_range;
+    int32_t n_planes;        // planes in this launch
+    int32_t plane_offset;    // index of this launch's first plane in the partial buffer
+    int32_t total_planes;
+};
+size_t refocus_smem_bytes(int ha, int wa);
+int refocus_ranges(int hb, int wb, int n_planes, int sm_count);
+cudaError_t launch_refocus(const float* gamma_f32, const RefocusGeom& g, const PlaneBlock& pl,
+                           double* partial, cudaStream_t st);
+cudaError_t launch_refocus_reduce(const double* partial, int n_ranges, int64_t per_range,
+                                  float* out, cudaStream_t st);
+
+// ------------------------------------------------------------------ self test
+cudaError_t launch_wait_selftest(unsigned int* status, unsigned long long timeout_ns,
+                                 cudaStream_t st);
+
+}  // namespace cpi

@@ -1,0 +1,331 @@
+// Step a2: the raw-moment contraction S_ab[a][b] = sum_i A_i[a] B_i[b] (the
+// first term of Eq. (1)) on the 5th-generation tensor cores.
+//
+// Operands are the K-major rows written by the ingest step (one row per pixel,
+// K = frames): FP8 E4M3 0/1 values for binary frames (tcgen05 kind::f8f6f4), or
+// BF16 integers 0..255 (kind::f16).  Products are small integers, accumulated
+// in FP32 in tensor memory; a sum of integers stays exact while it is below
+// 2^24, and the schedule guarantees that:
+//   - binary frames: a frame chunk has at most 32768 frames, so every sum is
+//     <= 32768;
+//   - 8-bit values: products are <= 255^2 = 65025, and the accumulator is
+//     folded into exact int32 registers every 256 frames
+//     (256 * 65025 = 16,646,400 < 2^24); a chunk of <= 32768 frames keeps the
+//     int32 total below 2^31.
+// Each (frame chunk, 128 x BLOCK_N output tile) is one work unit; its exact
+// int32 partial sum goes to its own slot of the workspace, and the fold step
+// adds the slots into int64.  Integer addition is associative, so the split
+// over chunks and CTAs never changes the result.
+//
+// Persistent, warp-specialised CTA (one per SM, 192 threads):
+//   warp 0  : TMA producer (128-byte swizzled tiles, STAGES-deep ring)
+//   warp 1  : tensor-memory allocator and single-thread MMA issuer
+//   warps 2-5: epilogue, tensor memory -> registers -> global (TMEM lanes 32*(w%4)..)
+// Two TMEM accumulators let the epilogue of one segment overlap the MMAs of the
+// next.  Every barrier wait is bounded; on a time-out the CTA records the error,
+// drains its own copies and MMAs, frees its tensor memory and returns.
+#include "kernels.cuh"
+#include "ptx.cuh"
+
+namespace cpi {
+namespace {
+
+constexpr int kBlockM = 128;
+constexpr int kRowBytes = 128;                 // K-block: one 128-byte swizzle row
+constexpr int kThreads = 192;
+
+template <bool kBf16>
+struct MomentsCfg {
+    static constexpr int kBlockN = kBf16 ? 128 : 256;
+    static constexpr int kStages = kBf16 ? 6 : 4;
+    static constexpr int kElem = kBf16 ? 2 : 1;
+    static constexpr int kKPerBlock = kRowBytes / kElem;     // 64 / 128 elements
+    static constexpr int kMmaK = 32 / kElem;                  // 16 / 32 elements per MMA
+    static constexpr int kABytes = kBlockM * kRowBytes;       // 16 KiB
+    static constexpr int kBBytes = kBlockN * kRowBytes;       // 16 / 32 KiB
+    static constexpr uint32_t kTmemCols = 2 * kBlockN;        // two accumulators
+    static constexpr size_t kSmem = 1024 + (size_t)kStages * (kABytes + kBBytes) + 256;
+};
+
+template <bool kBf16>
+__global__ void __launch_bounds__(kThreads, 1)
+    moments_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
+                   const MomentsParams p) {
+    using C = MomentsCfg<kBf16>;
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                               ~static_cast<uintptr_t>(1023));
+    uint8_t* sA = smem;
+    uint8_t* sB = sA + C::kStages * C::kABytes;
+    uint64_t* full = reinterpret_cast<uint64_t*>(sB + C::kStages * C::kBBytes);
+    uint64_t* empty = full + C::kStages;
+    uint64_t* tfull = empty + C::kStages;      // [2] accumulator ready for the epilogue
+    uint64_t* tempty = tfull + 2;              // [2] accumulator drained by the epilogue
+    uint64_t* drain = tempty + 2;              // MMA drain on abort
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint64_t tmo = p.timeout_ns;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < C::kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < 2; ++s) {
+            mbar_init(&tfull[s], 1);
+            mbar_init(&tempty[s], 128);
+        }
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        fence_barrier_init();
+        fence_proxy_async_smem();
+        tma_prefetch_desc(&tm_a);
+        tma_prefetch_desc(&tm_b);
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, C::kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+    const int units_per_chunk = p.tiles_m * p.tiles_n;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------------------------------------------------- producer
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t issued_mask = 0, issued_phase = 0;   // per stage: loaded at least once / parity
+            bool ok = true;
+            for (int u = blockIdx.x; ok && u < p.n_units; u += gridDim.x) {
+                const int chunk = u / units_per_chunk;
+                const int t = u - chunk * units_per_chunk;
+                const int tm = t / p.tiles_n, tn = t - tm * p.tiles_n;
+                const int kb0 = chunk * p.kb_per_chunk;
+                const int kb1 = min(kb0 + p.kb_per_chunk, p.k_blocks);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1, abort_flag, p.status, tmo)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], C::kABytes + C::kBBytes);
+                    tma_load_2d(sA + stage * C::kABytes, &tm_a, &full[stage], kb * C::kKPerBlock,
+                                tm * kBlockM);
+                    tma_load_2d(sB + stage * C::kBBytes, &tm_b, &full[stage], kb * C::kKPerBlock,
+                                tn * C::kBlockN);
+                    issued_mask |= 1u << stage;
+                    issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+                    if (++stage == C::kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                }
+            }
+            if (!ok) {
+                // Wait (bounded, regardless of the abort flag) for the copies this
+                // thread issued, so no TMA write lands after the CTA exits.
+                for (int s = 0; s < C::kStages; ++s)
+                    if (issued_mask & (1u << s))
+                        mbar_wait_bounded(&full[s], (issued_phase >> s) & 1u, nullptr, nullptr, tmo);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------------------------------------------------- MMA issuer
+            constexpr uint32_t idesc = idesc_f32acc<kBf16>(kBlockM, C::kBlockN);
+            int stage = 0;
+            uint32_t phase = 0;
+            int acc = 0;
+            uint32_t acc_phase = 0;
+            bool ok = true, issued_any = false;
+            for (int u = blockIdx.x; ok && u < p.n_units; u += gridDim.x) {
+                const int chunk = u / units_per_chunk;
+                const int kb0 = chunk * p.kb_per_chunk;
+                const int kb1 = min(kb0 + p.kb_per_chunk, p.k_blocks);
+                for (int kb = kb0; kb < kb1; ++kb) {
+                    const int local = kb - kb0;
+                    const bool seg_start = kBf16 ? (local % p.kb_per_fold == 0) : (local == 0);
+                    const bool seg_end =
+                        kBf16 ? ((local + 1) % p.kb_per_fold == 0 || kb + 1 == kb1) : (kb + 1 == kb1);
+                    if (seg_start) {
+                        if (!mbar_wait_bounded(&tempty[acc], acc_phase ^ 1, abort_flag, p.status, tmo)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                    }
+                    if (!mbar_wait_bounded(&full[stage], phase, abort_flag, p.status, tmo)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem_base + (uint32_t)(acc * C::kBlockN);
+                    const uint64_t da = sdesc_kmajor_sw128(smem_u32(sA + stage * C::kABytes));
+                    const uint64_t db = sdesc_kmajor_sw128(smem_u32(sB + stage * C::kBBytes));
+#pragma unroll
+                    for (int k = 0; k < kRowBytes / 32; ++k) {
+                        // advance the start address by 32 bytes (2 x 16-byte units) per MMA
+                        umma_f32<kBf16>(d, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc,
+                                        (seg_start && k == 0) ? 0u : 1u);
+                    }
+                    issued_any = true;
+                    umma_commit(&empty[stage]);
+                    if (++stage == C::kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                    if (seg_end) {
+                        umma_commit(&tfull[acc]);
+                        acc ^= 1;
+                        if (acc == 0) acc_phase ^= 1;
+                    }
+                }
+            }
+            if (!ok && issued_any) {
+                umma_commit(drain);
+                mbar_wait_bounded(drain, 0, nullptr, nullptr, tmo);
+            }
+        }
+    } else {
+        // -------------------------------------------------------------- epilogue
+        const int q = warp & 3;                       // TMEM lane quarter of this warp
+        const int row = q * 32 + lane;
+        const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        bool ok = true;
+        for (int u = blockIdx.x; ok && u < p.n_units; u += gridDim.x) {
+            const int chunk = u / units_per_chunk;
+            const int t = u - chunk * units_per_chunk;
+            const int tm = t / p.tiles_n, tn = t - tm * p.tiles_n;
+            const int kb0 = chunk * p.kb_per_chunk;
+            const int kb1 = min(kb0 + p.kb_per_chunk, p.k_blocks);
+            const int m = tm * kBlockM + row;
+            const int n0 = tn * C::kBlockN;
+            int32_t* out = p.partial + ((size_t)chunk * p.M + (size_t)(m < p.M ? m : 0)) * p.N;
+            const bool vec_ok = (p.N & 3) == 0;
+            if constexpr (!kBf16) {
+                if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, p.status, tmo)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+#pragma unroll 1
+                for (int c = 0; c < C::kBlockN / 32; ++c) {
+                    uint32_t r[32];
+                    tmem_ld_32x32b_x32(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN + c * 32), r);
+                    tmem_ld_wait();
+                    const int nb = n0 + c * 32;
+                    if (m < p.M) {
+                        if (vec_ok && nb + 32 <= p.N) {
+                            int4* o4 = reinterpret_cast<int4*>(out + nb);
+#pragma unroll
+                            for (int j = 0; j < 8; ++j)
+                                o4[j] = make_int4(__float2int_rn(__uint_as_float(r[4 * j + 0])),
+                                                  __float2int_rn(__uint_as_float(r[4 * j + 1])),
+                                                  __float2int_rn(__uint_as_float(r[4 * j + 2])),
+                                                  __float2int_rn(__uint_as_float(r[4 * j + 3])));
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 32; ++j)
+                                if (nb + j < p.N) out[nb + j] = __float2int_rn(__uint_as_float(r[j]));
+                        }
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(&tempty[acc]);
+                acc ^= 1;
+                if (acc == 0) acc_phase ^= 1;
+            } else {
+                int32_t sum[C::kBlockN];
+#pragma unroll
+                for (int j = 0; j < C::kBlockN; ++j) sum[j] = 0;
+                const int nseg = (kb1 - kb0 + p.kb_per_fold - 1) / p.kb_per_fold;
+                for (int sgm = 0; sgm < nseg; ++sgm) {
+                    if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, p.status, tmo)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+#pragma unroll
+                    for (int c = 0; c < C::kBlockN / 32; ++c) {
+                        uint32_t r[32];
+                        tmem_ld_32x32b_x32(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN + c * 32),
+                                           r);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) sum[c * 32 + j] += __float2int_rn(__uint_as_float(r[j]));
+                    }
+                    tc_fence_before();
+                    mbar_arrive(&tempty[acc]);
+                    acc ^= 1;
+                    if (acc == 0) acc_phase ^= 1;
+                }
+                if (!ok) break;
+                if (m < p.M) {
+                    if (vec_ok && n0 + C::kBlockN <= p.N) {
+                        int4* o4 = reinterpret_cast<int4*>(out + n0);
+#pragma unroll
+                        for (int j = 0; j < C::kBlockN / 4; ++j)
+                            o4[j] = make_int4(sum[4 * j], sum[4 * j + 1], sum[4 * j + 2], sum[4 * j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < C::kBlockN; ++j)
+                            if (n0 + j < p.N) out[n0 + j] = sum[j];
+                    }
+                }
+            }
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, C::kTmemCols);
+    }
+}
+
+}  // namespace
+
+MomentsShape moments_shape(bool bf16) {
+    if (bf16)
+        return {MomentsCfg<true>::kBlockN, MomentsCfg<true>::kKPerBlock, MomentsCfg<true>::kStages,
+                MomentsCfg<true>::kSmem};
+    return {MomentsCfg<false>::kBlockN, MomentsCfg<false>::kKPerBlock, MomentsCfg<false>::kStages,
+            MomentsCfg<false>::kSmem};
+}
+
+cudaError_t launch_moments(bool bf16, const CUtensorMap& tm_a, const CUtensorMap& tm_b,
+                           const MomentsParams& p, int grid, cudaStream_t st) {
+    // The shared-memory opt-in is a per-device function attribute: set it once per device.
+    static bool attr_set[2][64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (bf16) {
+        if (!attr_set[1][dev]) {
+            e = cudaFuncSetAttribute(moments_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)MomentsCfg<true>::kSmem);
+            if (e != cudaSuccess) return e;
+            attr_set[1][dev] = true;
+        }
+        moments_kernel<true><<<grid, kThreads, MomentsCfg<true>::kSmem, st>>>(tm_a, tm_b, p);
+    } else {
+        if (!attr_set[0][dev]) {
+            e = cudaFuncSetAttribute(moments_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)MomentsCfg<false>::kSmem);
+            if (e != cudaSuccess) return e;
+            attr_set[0][dev] = true;
+        }
+        moments_kernel<false><<<grid, kThreads, MomentsCfg<false>::kSmem, st>>>(tm_a, tm_b, p);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace cpi

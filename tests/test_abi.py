@@ -1,0 +1,65 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+symbol include/cpi.h declares; host-side planning answers without a device."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_2407_20692_gb300 as cpi
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "cpi.h")).read()
+    return sorted(set(re.findall(r"^CPI_API[^(]*?\b(cpi_\w+)\(", src, flags=re.M)))
+
+
+def test_header_declares_the_binding_names():
+    assert _declared() == sorted(cpi.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol():
+    lib = cpi.load()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert cpi.cpi_abi_version() == 1
+    assert cpi.cpi_status_string(0) == "CPI_OK"
+    assert cpi.cpi_status_string(6) == "CPI_ERR_TIMEOUT"
+
+
+def test_library_has_no_cpu_fallback_symbols():
+    """The product library contains no oracle code."""
+    data = open(cpi.library_path(), "rb").read()
+    assert b"oracle_correlate" not in data and b"oracle_refocus" not in data
+
+
+def _fd(bits, h, w, x0=0, rs=None, fs=None):
+    rs = rs or (x0 + w)
+    fs = fs or (h * rs if bits == 8 else (h * rs + 7) // 8)
+    return cpi.cpi_frames(0x1000, bits, h, w, x0, 0, rs, fs, 0)
+
+
+def test_workspace_query_host_logic():
+    # binary 64x64 vs 32x32, 20000 frames: FP8 operands padded to 256 frames
+    a, b = _fd(1, 64, 64, 0, 96), _fd(1, 32, 32, 64, 96, 64 * 96 // 8)
+    a.frame_stride_bytes = 64 * 96 // 8
+    ws = cpi.cpi_correlate_workspace_size(a, b, 20000)
+    kpad = 20224
+    assert ws >= (4096 + 1024) * kpad + 4096 * 1024 * 4
+    # uint8 inputs use BF16 operands (2 bytes per frame)
+    a8, b8 = _fd(8, 16, 16), _fd(8, 16, 16)
+    ws8 = cpi.cpi_correlate_workspace_size(a8, b8, 2000)
+    assert ws8 >= (256 + 256) * 2048 * 2 + 256 * 256 * 4
+    # invalid descriptors and sizes answer 0
+    assert cpi.cpi_correlate_workspace_size(a8, b8, 0) == 0
+    bad = _fd(8, 16, 16)
+    bad.bits = 3
+    assert cpi.cpi_correlate_workspace_size(bad, b8, 10) == 0
+    outside = _fd(8, 16, 16)
+    outside.frame_stride_bytes = 100          # region does not fit in one frame
+    assert cpi.cpi_correlate_workspace_size(outside, b8, 10) == 0
+    assert cpi.cpi_refocus_workspace_size(64, 64, 32, 32, 32) > 0
+    assert cpi.cpi_refocus_workspace_size(0, 64, 32, 32, 32) == 0

@@ -1,0 +1,225 @@
+"""GPU parity of Eq. (1): the CUDA path through the C ABI against the CPU oracle.
+
+S_ab, S_a, S_b must be bit-exact and Gamma bit-identical (same exact int64
+numerator, one correctly rounded conversion and division on both sides)."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2407_20692_gb300 as cpi
+import synth
+from gpu_util import assert_exact, desc, gpu_correlate, make_frames, oracle_correlate
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ready(cuda_ready, oracle_mod):
+    yield
+
+
+@pytest.mark.parametrize("case", json.load(open(os.path.join(GOLD, "eq1_hand.json")))["cases"],
+                         ids=lambda c: c["name"])
+def test_hand_worked_cases(case):
+    fr = torch.tensor(case["frames"], dtype=torch.uint8, device="cuda")
+    common = dict(bits=case["bits"], row_stride=case["row_stride"],
+                  frame_stride_bytes=case["frame_stride_bytes"], bit_order=case["bit_order"])
+    la, lb = dict(common, **case["a"]), dict(common, **case["b"])
+    got = gpu_correlate(fr, la, lb, len(case["frames"]))
+    assert got["s_ab"].tolist() == case["s_ab"]
+    assert got["s_a"].tolist() == case["s_a"]
+    from fractions import Fraction
+
+    want = np.array([[float(Fraction(x)) for x in row] for row in case["gamma"]])
+    assert np.array_equal(got["gamma"].numpy(), want)
+
+
+@pytest.mark.parametrize("side_a,side_b,n,counts", [
+    (16, 16, 2000, "poisson8"),          # the small 16x16 vs 16x16 uint8 workload, full size
+    (24, 12, 3001, "bernoulli"),         # ragged tiles and a ragged frame count
+    (20, 9, 777, "poisson8"),
+    (40, 36, 4500, "bernoulli"),         # several M and N tiles, N tile ragged
+    (8, 40, 300, "binomial255"),         # M_a < one tile, large counts
+])
+def test_correlate_matches_oracle(side_a, side_b, n, counts):
+    acq = synth.Acquisition(side_a, side_b, n, 2.0 if counts == "poisson8" else 0.3, counts, seed=7)
+    fr, lay = make_frames(acq)
+    got = gpu_correlate(fr, lay["a"], lay["b"], n)
+    want = oracle_correlate(fr.cpu().numpy(), lay["a"], lay["b"], n)
+    assert_exact(got, want)
+
+
+def test_correlate_spad_1bit_full_size():
+    """64x64 vs 32x32 binary frames, 20000 frames, bit-packed side by side."""
+    acq = synth.CONFIGS["spad_1bit"]
+    fr, lay = make_frames(acq)
+    got = gpu_correlate(fr, lay["a"], lay["b"], acq.n_frames)
+    want = oracle_correlate(fr.cpu().numpy(), lay["a"], lay["b"], acq.n_frames)
+    assert_exact(got, want)
+
+
+def test_correlate_large_u8_sampled_rows():
+    """128x128 vs 64x64 uint8 (sums of 255 binary sub-frames), 50000 frames:
+    two frame chunks; full S_a, S_b and sampled row blocks of S_ab / Gamma."""
+    acq = synth.CONFIGS["large_u8"]
+    fr, lay = make_frames(acq)
+    got = gpu_correlate(fr, lay["a"], lay["b"], acq.n_frames, want_f32=False)
+    host = fr.cpu().numpy()
+    del fr
+    torch.cuda.empty_cache()
+    for rows in [(0, 24), (8100, 8140), (16384 - 16, 16384)]:
+        want = oracle_correlate(host, lay["a"], lay["b"], acq.n_frames, rows=rows)
+        assert_exact(got, want, rows=rows)
+
+
+def test_exactness_adversarial_all_ones_and_max_counts():
+    """Partial sums at the exactness bounds: all-ones binary frames over more than
+    one 32768-frame chunk, and all-255 counts (products 65025) over 33000 frames."""
+    n = 32768 + 300
+    ha, wa, hb, wb = 4, 8, 2, 8
+    W = wa + wb
+    img = torch.ones((n, ha, W), dtype=torch.uint8)
+    bits = synth.pack_bits_lsb(img.reshape(n, ha * W))
+    fr = bits.cuda()
+    la = dict(bits=1, height=ha, width=wa, x0=0, y0=0, row_stride=W, frame_stride_bytes=ha * W // 8)
+    lb = dict(la, height=hb, width=wb, x0=wa)
+    got = gpu_correlate(fr, la, lb, n)
+    assert (got["s_ab"] == n).all() and (got["s_a"] == n).all() and (got["s_b"] == n).all()
+    assert (got["gamma"] == 0).all()
+    n2 = 33000
+    fr8 = torch.full((n2, ha * W), 255, dtype=torch.uint8, device="cuda")
+    fr8[::3, 0] = 254        # break the symmetry a little
+    l8a = dict(bits=8, height=ha, width=wa, x0=0, y0=0, row_stride=W, frame_stride_bytes=ha * W)
+    l8b = dict(l8a, height=hb, width=wb, x0=wa)
+    got = gpu_correlate(fr8, l8a, l8b, n2)
+    want = oracle_correlate(fr8.cpu().numpy(), l8a, l8b, n2)
+    assert_exact(got, want)
+
+
+def test_mixed_bit_depths():
+    """A binary, B uint8 from different buffers."""
+    acq = synth.Acquisition(20, 10, 2500, 1.0, "poisson8", seed=3)
+    A, B = synth.generate(acq, "cuda")
+    Ab = (A > 0).to(torch.uint8)
+    fa, la = synth.pack_side_by_side(Ab, torch.zeros((acq.n_frames, 1, 1), dtype=torch.uint8, device="cuda"), 1)
+    fb = B.reshape(acq.n_frames, -1).contiguous()
+    lb = dict(bits=8, height=10, width=10, x0=0, y0=0, row_stride=10, frame_stride_bytes=100)
+    a, b = desc(fa, la["a"]), desc(fb, lb)
+    n = acq.n_frames
+    ws = torch.empty(cpi.cpi_correlate_workspace_size(a, b, n), dtype=torch.uint8, device="cuda")
+    s_ab = torch.empty((400, 100), dtype=torch.int64, device="cuda")
+    s_a = torch.empty(400, dtype=torch.int64, device="cuda")
+    s_b = torch.empty(100, dtype=torch.int64, device="cuda")
+    g = torch.empty((400, 100), dtype=torch.float64, device="cuda")
+    cpi.cpi_correlate(a, b, n, s_ab, s_a, s_b, g, None, ws)
+    torch.cuda.synchronize()
+    import oracle
+
+    want = oracle.correlate(fa.cpu().numpy(), la["a"], fb.cpu().numpy(), lb, n)
+    assert np.array_equal(s_ab.cpu().numpy(), want["s_ab"])
+    assert np.array_equal(g.cpu().numpy().view(np.int64), want["gamma"].view(np.int64))
+
+
+def test_accumulate_then_finalize_equals_single_call():
+    acq = synth.Acquisition(32, 16, 6000, 0.3, "bernoulli", seed=5)
+    fr, lay = make_frames(acq)
+    n = acq.n_frames
+    full = gpu_correlate(fr, lay["a"], lay["b"], n)
+    a1, b1 = desc(fr, lay["a"]), desc(fr, lay["b"])
+    ma, mb = 32 * 32, 16 * 16
+    s_ab = torch.zeros((ma, mb), dtype=torch.int64, device="cuda")
+    s_a = torch.zeros(ma, dtype=torch.int64, device="cuda")
+    s_b = torch.zeros(mb, dtype=torch.int64, device="cuda")
+    fb = lay["frame_bytes"]
+    for f0, f1 in [(0, 2500), (2500, 2501), (2501, 6000)]:
+        sub = fr[f0:f1]
+        a, b = desc(sub, lay["a"]), desc(sub, lay["b"])
+        ws = torch.empty(cpi.cpi_correlate_workspace_size(a, b, f1 - f0), dtype=torch.uint8, device="cuda")
+        cpi.cpi_correlate_accumulate(a, b, f1 - f0, s_ab, s_a, s_b, ws)
+    g = torch.empty((ma, mb), dtype=torch.float64, device="cuda")
+    g32 = torch.empty((mb, ma), dtype=torch.float32, device="cuda")
+    cpi.cpi_correlate_finalize(s_ab, s_a, s_b, ma, mb, n, g, g32)
+    torch.cuda.synchronize()
+    assert torch.equal(s_ab.cpu(), full["s_ab"])
+    assert torch.equal(g.cpu(), full["gamma"])
+    assert torch.equal(g32, full["gamma_f32"])
+    assert fb > 0
+
+
+def test_stages_equal_single_call():
+    acq = synth.Acquisition(48, 24, 3000, 0.3, "bernoulli", seed=9)
+    fr, lay = make_frames(acq)
+    n = acq.n_frames
+    full = gpu_correlate(fr, lay["a"], lay["b"], n)
+    a, b = desc(fr, lay["a"]), desc(fr, lay["b"])
+    ma, mb = 48 * 48, 24 * 24
+    ws = torch.empty(cpi.cpi_correlate_workspace_size(a, b, n), dtype=torch.uint8, device="cuda")
+    s_ab = torch.empty((ma, mb), dtype=torch.int64, device="cuda")
+    s_a = torch.empty(ma, dtype=torch.int64, device="cuda")
+    s_b = torch.empty(mb, dtype=torch.int64, device="cuda")
+    g = torch.empty((ma, mb), dtype=torch.float64, device="cuda")
+    for st in (cpi.CPI_STAGE_INGEST, cpi.CPI_STAGE_MOMENTS, cpi.CPI_STAGE_FOLD):
+        cpi.cpi_correlate_stage(st, a, b, n, 0, s_ab, s_a, s_b, g, None, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(s_ab.cpu(), full["s_ab"])
+    assert torch.equal(g.cpu(), full["gamma"])
+
+
+def test_gamma_f32_is_slice_major_copy():
+    acq = synth.Acquisition(24, 12, 1000, 2.0, "poisson8", seed=2)
+    fr, lay = make_frames(acq)
+    got = gpu_correlate(fr, lay["a"], lay["b"], acq.n_frames)
+    assert torch.equal(got["gamma_f32"].cpu(), got["gamma"].float().T.contiguous())
+
+
+def test_same_detector_symmetric():
+    acq = synth.Acquisition(16, 16, 4000, 0.3, "bernoulli", seed=4)
+    fr, lay = make_frames(acq)
+    got = gpu_correlate(fr, lay["a"], lay["a"], acq.n_frames)
+    g = got["gamma"]
+    assert torch.equal(g, g.T)
+
+
+def test_argument_errors_are_reported_before_launch():
+    fr = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    good = dict(bits=1, height=4, width=4, x0=0, y0=0, row_stride=8, frame_stride_bytes=4)
+    a = desc(fr, good)
+    s = torch.zeros((16, 16), dtype=torch.int64, device="cuda")
+    v = torch.zeros(16, dtype=torch.int64, device="cuda")
+    ws = torch.empty(cpi.cpi_correlate_workspace_size(a, a, 16), dtype=torch.uint8, device="cuda")
+    with pytest.raises(cpi.CpiError) as e:
+        cpi.cpi_correlate(a, a, 0, s, v, v, None, None, ws)
+    assert e.value.code == 1
+    with pytest.raises(cpi.CpiError) as e:
+        cpi.cpi_correlate(a, a, 16, s, v, v, None, None, ws[:16])
+    assert e.value.code == 3
+    bad = desc(fr, dict(good, bits=4))
+    with pytest.raises(cpi.CpiError) as e:
+        cpi.cpi_correlate(bad, a, 16, s, v, v, None, None, ws)
+    assert e.value.code == 1
+    big8 = desc(fr, dict(good, bits=8, frame_stride_bytes=32))
+    with pytest.raises(cpi.CpiError) as e:
+        cpi.cpi_correlate(big8, big8, 20_000_000, s, v, v, None, None, ws)
+    assert e.value.code == 2
+    with pytest.raises(cpi.CpiError) as e:
+        cpi.cpi_denoise(None, None, None, 4, 4, 4, 4)
+    assert e.value.code == 4
+
+
+def test_wait_timeout_is_reported_and_context_survives():
+    """A barrier wait that nothing satisfies gives up after its limit; the status
+    word reports CPI_ERR_TIMEOUT and later work still runs."""
+    assert cpi.cpi_device_status() == 0
+    cpi.cpi_selftest_wait_timeout(50_000_000)          # 50 ms
+    assert cpi.cpi_device_status(clear=True) == 6
+    assert cpi.cpi_device_status() == 0
+    acq = synth.Acquisition(16, 16, 500, 2.0, "poisson8", seed=1)
+    fr, lay = make_frames(acq)
+    got = gpu_correlate(fr, lay["a"], lay["b"], acq.n_frames)
+    want = oracle_correlate(fr.cpu().numpy(), lay["a"], lay["b"], acq.n_frames)
+    assert_exact(got, want)
