@@ -127,8 +127,11 @@ CPI_API cpi_status cpi_correlate_accumulate(const cpi_frames *a, const cpi_frame
                                     int64_t *s_ab, int64_t *s_a, int64_t *s_b, void *workspace,
                                     size_t workspace_bytes, cpi_stream stream);
 
-/* Gamma from accumulated sums: n_total frames in all; m_a x m_b entries.
- * gamma and/or gamma_f32 (layouts as above) may be NULL, not both. */
+/* Gamma from accumulated sums: n_total frames in all (1 <= n_total < 2^31);
+ * m_a x m_b entries.  The caller guarantees that n_total * s_ab and s_a * s_b
+ * fit in int64 (true for sums produced by this library, which checks
+ * N^2 max(A) max(B) < 2^63).  gamma and/or gamma_f32 (layouts as above) may be
+ * NULL, not both. */
 CPI_API cpi_status cpi_correlate_finalize(const int64_t *s_ab, const int64_t *s_a, const int64_t *s_b,
                                   int64_t m_a, int64_t m_b, int64_t n_total, double *gamma,
                                   float *gamma_f32, cpi_stream stream);

@@ -315,7 +315,7 @@ cpi_status cpi_correlate_finalize(const int64_t* s_ab, const int64_t* s_a, const
     if (!aligned(s_ab, 8) || !aligned(s_a, 8) || !aligned(s_b, 8)) return CPI_ERR_INVALID_ARG;
     if ((gamma && !aligned(gamma, 8)) || (gamma_f32 && !aligned(gamma_f32, 4)))
         return CPI_ERR_INVALID_ARG;
-    if ((double)n_total * (double)n_total * 65025.0 >= 9.2e18) return CPI_ERR_OVERFLOW;
+    if (n_total > ((int64_t)1 << 31) - 1) return CPI_ERR_OVERFLOW;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     return cuda_status(launch_fold(nullptr, 0, m_a, m_b, const_cast<int64_t*>(s_ab), 1, 0, s_a, s_b,
                                    n_total, gamma, gamma_f32, st));
@@ -328,7 +328,7 @@ size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb
     int sm = 152;
     if (device_info(&dev) == cudaSuccess) sm = dev->sm_count;
     const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
-    const int ranges = refocus_ranges(hb, wb, per_launch, sm);
+    const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, sm);
     return round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(double), 256);
 }
 
@@ -349,8 +349,7 @@ cpi_status cpi_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return CPI_ERR_WORKSPACE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
-    const int ranges = refocus_ranges(hb, wb, per_launch, dev->sm_count);
-    const int nb = hb * wb;
+    const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, dev->sm_count);
     double* partial = static_cast<double*>(workspace);
     PlaneBlock pb;
     for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {
@@ -367,7 +366,7 @@ cpi_status cpi_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
         g.hb = hb;
         g.wb = wb;
         g.n_ranges = ranges;
-        g.b_per_range = (nb + ranges - 1) / ranges;
+        g.b_per_range = refocus_range_size(ha, wa, hb, wb, ranges);
         g.n_planes = np;
         g.plane_offset = p0;
         g.total_planes = n_planes;

@@ -67,13 +67,18 @@ struct PlaneBlock {
 };
 struct RefocusGeom {
     int32_t ha, wa, hb, wb;
-    int32_t n_ranges, b_per_range;
+    int32_t n_ranges, b_per_range;   // ranges, and angular rows (or pixels) per range
     int32_t n_planes;        // planes in this launch
     int32_t plane_offset;    // index of this launch's first plane in the partial buffer
     int32_t total_planes;
 };
 size_t refocus_smem_bytes(int ha, int wa);
-int refocus_ranges(int hb, int wb, int n_planes, int sm_count);
+bool refocus_separable(int ha, int wa);
+// Number of ranges the angular pixels are split into (one partial image each),
+// and the size of one range (angular rows for the separable kernel, angular
+// pixels for the direct one).
+int refocus_ranges(int ha, int wa, int hb, int wb, int n_planes, int sm_count);
+int refocus_range_size(int ha, int wa, int hb, int wb, int n_ranges);
 cudaError_t launch_refocus(const float* gamma_f32, const RefocusGeom& g, const PlaneBlock& pl,
                            double* partial, cudaStream_t st);
 cudaError_t launch_refocus_reduce(const double* partial, int n_ranges, int64_t per_range,
