@@ -168,8 +168,9 @@ CPI_API cpi_status cpi_correlate_stage(int32_t stage, const cpi_frames *a, const
  *   gamma_f32 : float [hb*wb][ha*wa], slice-major (cpi_correlate's gamma_f32)
  *   planes    : HOST array of n_planes (alpha, beta), finite
  *   out       : float [n_planes][ha][wa]
- * Sums use compensated FP32 accumulation; coordinates and weights are computed
- * in double.  Requires ha, wa, hb, wb >= 1, wa <= 512, ha*wa <= 2^20.
+ * Sums use compensated FP32 accumulation; coordinates are computed on the fly
+ * with ~48-bit (double-float) precision.  Requires ha, wa, hb, wb >= 1,
+ * wa <= 512, (ha + 2) * (wa + 2) * 4 bytes <= 200 KiB, gamma_f32 16-byte aligned.
  * -------------------------------------------------------------------------- */
 CPI_API size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb,
                                   int32_t n_planes);

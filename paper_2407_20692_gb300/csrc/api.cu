@@ -86,6 +86,21 @@ bool make_operand_map(CUtensorMap* m, void* base, bool bf16, int64_t rows, int64
     return r == CUDA_SUCCESS;
 }
 
+// Slice-major FP32 Gamma as [Mb * ha rows][wa columns]; box (wa + 8) x ha starting
+// at column -4 returns each slice with 4 zero columns on both sides.
+bool make_slice_map(CUtensorMap* m, const float* g, int ha, int wa, int64_t mb) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)wa, (cuuint64_t)(mb * ha)};
+    cuuint64_t strides[1] = {(cuuint64_t)wa * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)(wa + 8), (cuuint32_t)ha};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(g), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -216,6 +231,13 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
         p.n_units = pl.n_units;
         p.status = dev->status;
         p.timeout_ns = g_timeout_ns;
+        p.fused = 0;   // the separate fold kernel is faster: see the note in the moments kernel
+        p.s_ab = s_ab;
+        p.s_a = s_a;
+        p.s_b = s_b;
+        p.gamma = gamma;
+        p.gamma_f32 = gamma_f32;
+        p.gd = make_gamma_div(pl.n);
         const int grid = pl.n_units < dev->sm_count ? pl.n_units : dev->sm_count;
         return cuda_status(launch_moments(pl.bf16, tm_a, tm_b, p, grid, st));
     }
@@ -329,7 +351,7 @@ size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb
     if (device_info(&dev) == cudaSuccess) sm = dev->sm_count;
     const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
     const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, sm);
-    return round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(double), 256);
+    return round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(float), 256);
 }
 
 cpi_status cpi_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
@@ -339,7 +361,7 @@ cpi_status cpi_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
     if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || wa > 512) return CPI_ERR_INVALID_ARG;
     if ((int64_t)hb * wb > kMaxPixels) return CPI_ERR_INVALID_ARG;
     if (refocus_smem_bytes(ha, wa) > 200 * 1024) return CPI_ERR_UNSUPPORTED;
-    if (!aligned(gamma_f32, 4) || !aligned(out, 4)) return CPI_ERR_INVALID_ARG;
+    if (!aligned(gamma_f32, 16) || !aligned(out, 4)) return CPI_ERR_INVALID_ARG;
     for (int i = 0; i < n_planes; ++i)
         if (!std::isfinite(planes[i].alpha) || !std::isfinite(planes[i].beta))
             return CPI_ERR_INVALID_ARG;
@@ -350,7 +372,11 @@ cpi_status cpi_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
     const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, dev->sm_count);
-    double* partial = static_cast<double*>(workspace);
+    float* partial = static_cast<float*>(workspace);
+    CUtensorMap tm;
+    const bool sep = refocus_separable(ha, wa);
+    if (sep && (int64_t)hb * wb * ha >= ((int64_t)1 << 31)) return CPI_ERR_UNSUPPORTED;
+    if (sep && !make_slice_map(&tm, gamma_f32, ha, wa, (int64_t)hb * wb)) return CPI_ERR_CUDA;
     PlaneBlock pb;
     for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {
         const int np = n_planes - p0 < kRefocusMaxPlanesPerLaunch ? n_planes - p0
@@ -370,7 +396,9 @@ cpi_status cpi_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
         g.n_planes = np;
         g.plane_offset = p0;
         g.total_planes = n_planes;
-        cudaError_t e = launch_refocus(gamma_f32, g, pb, partial, st);
+        g.status = dev->status;
+        g.timeout_ns = g_timeout_ns;
+        cudaError_t e = launch_refocus(gamma_f32, sep ? &tm : nullptr, g, pb, partial, st);
         if (e != cudaSuccess) return CPI_ERR_CUDA;
     }
     return cuda_status(

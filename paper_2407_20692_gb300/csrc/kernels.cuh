@@ -6,6 +6,8 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include "gamma_div.cuh"
+
 namespace cpi {
 
 // Status bits recorded by kernels in the per-device status word.
@@ -40,6 +42,15 @@ struct MomentsParams {
     int32_t n_chunks, tiles_m, tiles_n, n_units;
     unsigned int* status;
     unsigned long long timeout_ns;
+    // Fused fold (single frame chunk, no accumulation): the epilogue writes
+    // S_ab, Gamma and the slice-major FP32 copy directly; partial is unused.
+    int32_t fused;
+    int64_t* s_ab;
+    const int64_t* s_a;
+    const int64_t* s_b;
+    double* gamma;
+    float* gamma_f32;
+    GammaDiv gd;
 };
 
 struct MomentsShape {
@@ -71,6 +82,8 @@ struct RefocusGeom {
     int32_t n_planes;        // planes in this launch
     int32_t plane_offset;    // index of this launch's first plane in the partial buffer
     int32_t total_planes;
+    unsigned int* status;           // device status word (bounded waits)
+    unsigned long long timeout_ns;
 };
 size_t refocus_smem_bytes(int ha, int wa);
 bool refocus_separable(int ha, int wa);
@@ -79,9 +92,11 @@ bool refocus_separable(int ha, int wa);
 // pixels for the direct one).
 int refocus_ranges(int ha, int wa, int hb, int wb, int n_planes, int sm_count);
 int refocus_range_size(int ha, int wa, int hb, int wb, int n_ranges);
-cudaError_t launch_refocus(const float* gamma_f32, const RefocusGeom& g, const PlaneBlock& pl,
-                           double* partial, cudaStream_t st);
-cudaError_t launch_refocus_reduce(const double* partial, int n_ranges, int64_t per_range,
+// tm: 2-D tensor map over gamma_f32 viewed as [Mb * ha rows][wa columns] with a
+// (wa + 8) x ha box, required when refocus_separable(ha, wa).
+cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const RefocusGeom& g,
+                           const PlaneBlock& pl, float* partial, cudaStream_t st);
+cudaError_t launch_refocus_reduce(const float* partial, int n_ranges, int64_t per_range,
                                   float* out, cudaStream_t st);
 
 // ------------------------------------------------------------------ self test

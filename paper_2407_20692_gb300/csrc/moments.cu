@@ -24,6 +24,7 @@
 // Two TMEM accumulators let the epilogue of one segment overlap the MMAs of the
 // next.  Every barrier wait is bounded; on a time-out the CTA records the error,
 // drains its own copies and MMAs, frees its tensor memory and returns.
+#include "gamma_div.cuh"
 #include "kernels.cuh"
 #include "ptx.cuh"
 
@@ -32,7 +33,8 @@ namespace {
 
 constexpr int kBlockM = 128;
 constexpr int kRowBytes = 128;                 // K-block: one 128-byte swizzle row
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;                  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpiThreads = 256;
 
 template <bool kBf16>
 struct MomentsCfg {
@@ -46,6 +48,46 @@ struct MomentsCfg {
     static constexpr uint32_t kTmemCols = 2 * kBlockN;        // two accumulators
     static constexpr size_t kSmem = 1024 + (size_t)kStages * (kABytes + kBBytes) + 256;
 };
+
+// Write 32 exact sums of output row m, columns nb .. nb+31 (those < N): either
+// to the chunk's int32 partial slot, or -- when the whole frame range is one
+// chunk and nothing is accumulated -- straight to S_ab, Gamma (row-major) and
+// the slice-major FP32 copy (the fused fold of Eq. (1)).  Measured on GB300 the
+// fused form is slower for one tile per CTA: each lane owns a row, so the
+// row-major stores touch 32 lines per instruction and nothing overlaps them;
+// the host keeps it off (MomentsParams::fused = 0) and runs the fold kernel.
+__device__ __forceinline__ void store_row_chunk(const MomentsParams& p, int chunk, int m, int nb,
+                                                const int32_t (&v)[32]) {
+    if (m >= p.M) return;
+    if (!p.fused) {
+        int32_t* out = p.partial + ((size_t)chunk * p.M + (size_t)m) * p.N;
+        if ((p.N & 3) == 0 && nb + 32 <= p.N) {
+            int4* o4 = reinterpret_cast<int4*>(out + nb);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) o4[j] = make_int4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (nb + j < p.N) out[nb + j] = v[j];
+        }
+        return;
+    }
+    const int64_t sa = __ldg(p.s_a + m);
+    const size_t rowoff = (size_t)m * p.N;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+        const int n = nb + j;
+        if (n < p.N) {
+            const int64_t S = v[j];
+            p.s_ab[rowoff + n] = S;
+            if (p.gamma != nullptr || p.gamma_f32 != nullptr) {
+                const double g = gamma_from_num(p.gd.n * S - sa * __ldg(p.s_b + n), p.gd);
+                if (p.gamma) p.gamma[rowoff + n] = g;
+                if (p.gamma_f32) p.gamma_f32[(size_t)n * p.M + m] = double_to_float_rn(g);
+            }
+        }
+    }
+}
 
 template <bool kBf16>
 __global__ void __launch_bounds__(kThreads, 1)
@@ -75,7 +117,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int s = 0; s < 2; ++s) {
             mbar_init(&tfull[s], 1);
-            mbar_init(&tempty[s], 128);
+            mbar_init(&tempty[s], kEpiThreads);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -192,7 +234,11 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // -------------------------------------------------------------- epilogue
+        // Warps 2..9: warp w reads TMEM lanes 32*(w%4).. (its rows) and one half
+        // of the tile's columns.
         const int q = warp & 3;                       // TMEM lane quarter of this warp
+        const int half = (warp - 2) >> 2;             // column half
+        constexpr int kHalf = C::kBlockN / 2;
         const int row = q * 32 + lane;
         const uint32_t lane_addr = (uint32_t)(q * 32) << 16;
         int acc = 0;
@@ -205,9 +251,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int kb0 = chunk * p.kb_per_chunk;
             const int kb1 = min(kb0 + p.kb_per_chunk, p.k_blocks);
             const int m = tm * kBlockM + row;
-            const int n0 = tn * C::kBlockN;
-            int32_t* out = p.partial + ((size_t)chunk * p.M + (size_t)(m < p.M ? m : 0)) * p.N;
-            const bool vec_ok = (p.N & 3) == 0;
+            const int n0 = tn * C::kBlockN + half * kHalf;
+            const uint32_t col0 = (uint32_t)(half * kHalf);
             if constexpr (!kBf16) {
                 if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, p.status, tmo)) {
                     ok = false;
@@ -215,35 +260,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
 #pragma unroll 1
-                for (int c = 0; c < C::kBlockN / 32; ++c) {
+                for (int c = 0; c < kHalf / 32; ++c) {
                     uint32_t r[32];
-                    tmem_ld_32x32b_x32(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN + c * 32), r);
+                    tmem_ld_32x32b_x32(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN) + col0 + c * 32, r);
                     tmem_ld_wait();
-                    const int nb = n0 + c * 32;
-                    if (m < p.M) {
-                        if (vec_ok && nb + 32 <= p.N) {
-                            int4* o4 = reinterpret_cast<int4*>(out + nb);
+                    int32_t v[32];
 #pragma unroll
-                            for (int j = 0; j < 8; ++j)
-                                o4[j] = make_int4(__float2int_rn(__uint_as_float(r[4 * j + 0])),
-                                                  __float2int_rn(__uint_as_float(r[4 * j + 1])),
-                                                  __float2int_rn(__uint_as_float(r[4 * j + 2])),
-                                                  __float2int_rn(__uint_as_float(r[4 * j + 3])));
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 32; ++j)
-                                if (nb + j < p.N) out[nb + j] = __float2int_rn(__uint_as_float(r[j]));
-                        }
-                    }
+                    for (int j = 0; j < 32; ++j) v[j] = __float2int_rn(__uint_as_float(r[j]));
+                    store_row_chunk(p, chunk, m, n0 + c * 32, v);
                 }
                 tc_fence_before();
                 mbar_arrive(&tempty[acc]);
                 acc ^= 1;
                 if (acc == 0) acc_phase ^= 1;
             } else {
-                int32_t sum[C::kBlockN];
+                int32_t sum[kHalf];
 #pragma unroll
-                for (int j = 0; j < C::kBlockN; ++j) sum[j] = 0;
+                for (int j = 0; j < kHalf; ++j) sum[j] = 0;
                 const int nseg = (kb1 - kb0 + p.kb_per_fold - 1) / p.kb_per_fold;
                 for (int sgm = 0; sgm < nseg; ++sgm) {
                     if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, p.status, tmo)) {
@@ -252,9 +285,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tc_fence_after();
 #pragma unroll
-                    for (int c = 0; c < C::kBlockN / 32; ++c) {
+                    for (int c = 0; c < kHalf / 32; ++c) {
                         uint32_t r[32];
-                        tmem_ld_32x32b_x32(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN + c * 32),
+                        tmem_ld_32x32b_x32(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN) + col0 + c * 32,
                                            r);
                         tmem_ld_wait();
 #pragma unroll
@@ -266,17 +299,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (acc == 0) acc_phase ^= 1;
                 }
                 if (!ok) break;
-                if (m < p.M) {
-                    if (vec_ok && n0 + C::kBlockN <= p.N) {
-                        int4* o4 = reinterpret_cast<int4*>(out + n0);
 #pragma unroll
-                        for (int j = 0; j < C::kBlockN / 4; ++j)
-                            o4[j] = make_int4(sum[4 * j], sum[4 * j + 1], sum[4 * j + 2], sum[4 * j + 3]);
-                    } else {
+                for (int c = 0; c < kHalf / 32; ++c) {
+                    int32_t v[32];
 #pragma unroll
-                        for (int j = 0; j < C::kBlockN; ++j)
-                            if (n0 + j < p.N) out[n0 + j] = sum[j];
-                    }
+                    for (int j = 0; j < 32; ++j) v[j] = sum[c * 32 + j];
+                    store_row_chunk(p, chunk, m, n0 + c * 32, v);
                 }
             }
         }

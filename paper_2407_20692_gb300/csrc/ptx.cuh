@@ -56,6 +56,34 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
+// try_wait that lets the hardware suspend the thread for up to hint_ns while the
+// phase is incomplete (no issue slots spent spinning).
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for a single waiting thread whose CTA is parked in a barrier:
+// sleeps in try_wait between checks instead of spinning.
+__device__ __forceinline__ bool mbar_wait_sleepy(uint64_t* bar, uint32_t parity, unsigned int* status,
+                                                 uint64_t timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    for (;;) {
+        if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+        if (global_timer_ns() - t0 > timeout_ns) {
+            if (status != nullptr) atomicOr(status, kStatusTimeoutBit);
+            return false;
+        }
+    }
+}
+
 // Wait until the phase with parity `parity` of `bar` has completed.  Gives up
 // (returns false) when *abort becomes non-zero or after timeout_ns; on a time
 // out it raises *abort and records kStatusTimeoutBit in *status.  Never spins

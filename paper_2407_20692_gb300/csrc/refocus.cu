@@ -30,6 +30,7 @@
 // This file is compiled without FMA contraction: the double-float and Kahan
 // steps depend on the written rounding order; the products use explicit fmaf.
 #include "kernels.cuh"
+#include "ptx.cuh"
 
 namespace cpi {
 namespace {
@@ -37,6 +38,8 @@ namespace {
 constexpr int kThreads = 512;
 constexpr int kPadL = 4;      // zero columns left of the interior (keeps 16-byte alignment)
 constexpr int kPadR = 4;
+constexpr int kSepPlanes = 2;  // planes per CTA of the separable kernel
+constexpr int kSepStages = 3;  // staged slices (TMA pipeline depth)
 
 // ------------------------------------------------------------ double-float helpers
 struct DF {
@@ -99,22 +102,6 @@ __device__ __forceinline__ void kahan_add(float& acc, float& cmp, float v) {
     acc = t;
 }
 
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
-                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-                 "l"(src)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
 struct PlaneCoef {
     DF alpha, qx, qy;     // alpha, beta*sx, beta*sy
 };
@@ -126,140 +113,192 @@ __device__ __forceinline__ PlaneCoef plane_coef(const PlaneBlock& pl, int p, int
 }
 
 // ------------------------------------------------------------ separable kernel
-// CTA = (range of angular rows, plane).  Thread t owns column c = t % wa and rows
-// rp + R*k (R = 512 / wa row phases), for both U and the output.
-template <int KR>
-__global__ void __launch_bounds__(kThreads, (KR >= 16 ? 1 : 2)) refocus_sep_kernel(const float* __restrict__ gamma,
-                                                               const RefocusGeom geo,
-                                                               const PlaneBlock pl,
-                                                               double* __restrict__ partial) {
-    extern __shared__ __align__(16) float sm[];
-    const int ha = geo.ha, wa = geo.wa, hb = geo.hb, wb = geo.wb;
-    const int WS = wa + kPadL + kPadR;                 // staged slice row stride
-    const int slice_f = ha * WS;
-    float* const buf0 = sm;                            // slice buffers: buf0 + (s & 1) * slice_f
-    float* U = sm + 2 * slice_f;                       // (ha + 2) x wa, zero rows -1 and ha
-    Tap* xt = reinterpret_cast<Tap*>(U + (ha + 2) * wa);   // [2][wa]
-    Tap* yt = xt + 2 * wa;                             // [ha]
+// CTA = (angular row br, block of PB planes).  Thread t owns column c = t % wa
+// and rows rp + R*k (R = 512 / wa row phases).  Each slice (br, bc) is staged by
+// one 2-D TMA copy of a (wa + 8) x ha box starting at column -4: the columns
+// outside the image come back as zeros, which are exactly the out-of-grid taps.
+// Every staged slice is interpolated along x for all PB planes; after the last
+// bc the row's U images are interpolated along y and this angular row's
+// contribution to each output pixel is written to partial[br][plane][pixel].
+// The reduce kernel adds the angular rows in double, in a fixed order.
+// kWA > 0 fixes the image width (and kHA the height) at compile time, so every
+// row offset of the inner loop is an immediate; kWA == 0 is the general form.
+template <int KR, int PB, int kWA, int kHA>
+__global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_constant__ CUtensorMap tm,
+                                                                  const RefocusGeom geo,
+                                                                  const PlaneBlock pl,
+                                                                  float* __restrict__ partial) {
+    extern __shared__ __align__(128) float sm_raw[];
+    const int ha = kWA ? kHA : geo.ha, wa = kWA ? kWA : geo.wa, hb = geo.hb, wb = geo.wb;
+    const int WS = wa + kPadL + kPadR;                 // staged slice row stride (TMA box width)
+    const int slice_f = (ha * WS + 31) & ~31;          // buffer stride: 128-byte multiples
+    float* const buf0 = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) &
+                                                 ~static_cast<uintptr_t>(127));
+    float* const U = buf0 + kSepStages * slice_f;      // PB x (ha + 2) x wa, zero rows -1 and ha
+    Tap* const xt = reinterpret_cast<Tap*>(U + PB * (ha + 2) * wa);   // [kSepStages][PB][wa]
+    Tap* const yt = xt + kSepStages * PB * wa;                        // [PB][ha]
+    __shared__ PlaneCoef coef[PB];                     // per-plane coefficients, computed once
+    __shared__ __align__(8) uint64_t full[kSepStages]; // TMA completion of each slice buffer
+    __shared__ int abort_flag;
 
     const int tid = threadIdx.x;
     const int R = kThreads / wa;
     const int c = tid % wa, rp = tid / wa;
     const bool active = rp < R;
-    const int p = blockIdx.y;
-    const PlaneCoef pc = plane_coef(pl, p, ha, wa, hb, wb);
+    const int nk = active ? (ha - rp + R - 1) / R : 0;      // rows of this thread
+    const int br = blockIdx.x;
+    const int pbase = blockIdx.y * PB;                  // first plane of this CTA (in this launch)
+    const int np = min(PB, geo.n_planes - pbase);
     const float cxa = 0.5f * (float)(wa - 1), cya = 0.5f * (float)(ha - 1);
     const float cxb = 0.5f * (float)(wb - 1), cyb = 0.5f * (float)(hb - 1);
     const int64_t Ma = (int64_t)ha * wa;
-    const bool vec = (wa % 4) == 0 && (reinterpret_cast<uintptr_t>(gamma) % 16) == 0;
+    const uint32_t slice_bytes = (uint32_t)(ha * WS * sizeof(float));
 
-    // zero the pad columns of both slice buffers and the pad rows of U
-    for (int i = tid; i < 2 * ha; i += kThreads) {
-        float* row = buf0 + (i / ha) * slice_f + (i % ha) * WS;
-#pragma unroll
-        for (int q = 0; q < kPadL; ++q) row[q] = 0.0f;
-#pragma unroll
-        for (int q = 0; q < kPadR; ++q) row[kPadL + wa + q] = 0.0f;
+    if (tid == 0) {
+        for (int i = 0; i < kSepStages; ++i) mbar_init(&full[i], 1);
+        abort_flag = 0;
+        fence_barrier_init();
     }
-    for (int i = tid; i < wa; i += kThreads) {
-        U[i] = 0.0f;
-        U[(ha + 1) * wa + i] = 0.0f;
+    if (tid < np) coef[tid] = plane_coef(pl, pbase + tid, ha, wa, hb, wb);
+    for (int i = tid; i < PB * wa; i += kThreads) {
+        const int j = i / wa, x = i - j * wa;
+        U[j * (ha + 2) * wa + x] = 0.0f;
+        U[j * (ha + 2) * wa + (ha + 1) * wa + x] = 0.0f;
     }
-
-    const int br0 = blockIdx.x * geo.b_per_range;            // b_per_range counts angular ROWS here
-    const int br1 = min(br0 + geo.b_per_range, hb);
-    const int n_slices = (br1 - br0) * wb;
-
-    // stage slice s of this range into buffer s & 1, with its x taps
-    auto stage = [&](int s) {
-        const int br = br0 + s / wb, bc = s % wb;
-        const float* src = gamma + ((int64_t)br * wb + bc) * Ma;
-        float* dst = buf0 + (s & 1) * slice_f;
-        if (vec) {
-            const int per_row = wa / 4;
-            for (int i = tid; i < ha * per_row; i += kThreads) {
-                const int r = i / per_row, q = i - r * per_row;
-                cp_async16(dst + r * WS + kPadL + 4 * q, src + (int64_t)r * wa + 4 * q);
-            }
-        } else {
-            for (int i = tid; i < ha * wa; i += kThreads) {
-                const int r = i / wa, q = i - r * wa;
-                cp_async4(dst + r * WS + kPadL + q, src + (int64_t)r * wa + q);
-            }
-        }
-        for (int j = tid; j < wa; j += kThreads)
-            xt[(s & 1) * wa + j] = axis_tap(pc.alpha, (float)j - cxa, pc.qx, (float)bc - cxb, cxa, wa, kPadL);
+    __syncthreads();   // barriers initialised, coef visible
+    auto issue = [&](int bc) {   // one thread: slice (br, bc) -> buffer bc % kSepStages
+        const int sb = bc % kSepStages;
+        mbar_arrive_expect_tx(&full[sb], slice_bytes);
+        tma_load_2d(buf0 + sb * slice_f, &tm, &full[sb], -kPadL, (br * wb + bc) * ha);
     };
-
-    // U accumulates plainly over groups of <= 4 slices (Ug), and the group sums
-    // are Kahan-added (Ua, Uc): error <= (3 + 2) * 2^-24 of the summed magnitudes.
-    float Ug[KR], Ua[KR], Uc[KR], Ra[KR], Rc[KR];
-#pragma unroll
-    for (int k = 0; k < KR; ++k) Ug[k] = Ua[k] = Uc[k] = Ra[k] = Rc[k] = 0.0f;
-
-    if (n_slices > 0) stage(0);
-    cp_async_commit();
-    for (int s = 0; s < n_slices; ++s) {
-        if (s + 1 < n_slices) stage(s + 1);
-        cp_async_commit();
-        cp_async_wait_1();
-        __syncthreads();   // slice s and its taps visible to all threads
-        const int bc = s % wb;
-        if (active) {
-            const Tap tx = xt[(s & 1) * wa + c];
-            const float* S = buf0 + (s & 1) * slice_f + tx.off;
-            const bool group_end = (bc & 3) == 3 || bc == wb - 1;
-#pragma unroll
-            for (int k = 0; k < KR; ++k) {
-                const int y = rp + R * k;
-                if (y < ha) {
-                    const float v0 = S[y * WS], v1 = S[y * WS + 1];
-                    Ug[k] += __fmaf_rn(tx.w1, v1, tx.w0 * v0);
-                }
-                if (group_end) {
-                    kahan_add(Ua[k], Uc[k], Ug[k]);
-                    Ug[k] = 0.0f;
-                }
-            }
+    auto taps = [&](int bc) {    // x taps of slice bc for every plane
+        const int sb = bc % kSepStages;
+        for (int i = tid; i < np * wa; i += kThreads) {
+            const int j = i / wa, x = i - j * wa;
+            xt[(sb * PB + j) * wa + x] =
+                axis_tap(coef[j].alpha, (float)x - cxa, coef[j].qx, (float)bc - cxb, cxa, wa, kPadL);
         }
-        if (bc == wb - 1) {
-            // angular row complete: y-interpolate U into the output
-            const int br = br0 + s / wb;
-            if (active) {
+    };
+    // prologue: the first kSepStages - 1 slices in flight, their taps ready
+    int last_issue[kSepStages];
 #pragma unroll
-                for (int k = 0; k < KR; ++k) {
-                    const int y = rp + R * k;
-                    if (y < ha) U[(y + 1) * wa + c] = Ua[k] - Uc[k];
-                    Ua[k] = Uc[k] = 0.0f;
-                }
-            }
-            for (int j = tid; j < ha; j += kThreads) {
-                Tap t = axis_tap(pc.alpha, (float)j - cya, pc.qy, (float)br - cyb, cya, ha, 1);
-                t.off *= wa;
-                yt[j] = t;
-            }
-            __syncthreads();
-            if (active) {
+    for (int i = 0; i < kSepStages; ++i) last_issue[i] = -1;
+    for (int bc = 0; bc < kSepStages - 1 && bc < wb; ++bc) {
+        if (tid == 0) {
+            issue(bc);
+            last_issue[bc % kSepStages] = bc;
+        }
+        taps(bc);
+    }
+
+    // U accumulates plainly (two fused multiply-adds per slice) over groups of
+    // <= 4 slices (Ug); the group sums are Kahan-added (Ua, Uc): error <=
+    // (8 + 2) 2^-24 of the summed magnitudes, to first order.
+    float Ug[PB][KR], Ua[PB][KR], Uc[PB][KR];
 #pragma unroll
-                for (int k = 0; k < KR; ++k) {
-                    const int r = rp + R * k;
-                    if (r < ha) {
-                        const Tap ty = yt[r];
-                        const float v0 = U[ty.off + c], v1 = U[ty.off + wa + c];
-                        kahan_add(Ra[k], Rc[k], __fmaf_rn(ty.w1, v1, ty.w0 * v0));
+    for (int j = 0; j < PB; ++j)
+#pragma unroll
+        for (int k = 0; k < KR; ++k) Ug[j][k] = Ua[j][k] = Uc[j][k] = 0.0f;
+
+    for (int bc = 0; bc < wb; ++bc) {
+        const int sb = bc % kSepStages;
+        const uint32_t parity = (uint32_t)((bc / kSepStages) & 1);
+        // one thread waits for the copy; the others sleep in the barrier below
+        if (tid == 0 && !mbar_wait_sleepy(&full[sb], parity, geo.status, geo.timeout_ns)) abort_flag = 1;
+        __syncthreads();   // slice bc landed; every thread is done with slice bc - 1
+        if (abort_flag) break;
+        // refill the buffer slice bc - 1 used, and prepare its taps
+        const int nxt = bc + kSepStages - 1;
+        if (nxt < wb) {
+            if (tid == 0) {
+                issue(nxt);
+                last_issue[nxt % kSepStages] = nxt;
+            }
+            taps(nxt);
+        }
+        mbar_wait_bounded(&full[sb], parity, &abort_flag, geo.status, geo.timeout_ns);   // completes at once
+        if (active) {
+            const float* S = buf0 + sb * slice_f + rp * WS;
+            const int step = R * WS;
+#pragma unroll
+            for (int j = 0; j < PB; ++j) {
+                if (j < np) {
+                    const Tap tx = xt[(sb * PB + j) * wa + c];
+                    const float* q = S + tx.off;
+                    if constexpr (kWA > 0 && kHA % (kThreads / kWA) == 0) {
+                        constexpr int kStep = (kThreads / kWA) * (kWA + kPadL + kPadR);
+#pragma unroll
+                        for (int k = 0; k < KR; ++k)
+                            Ug[j][k] = __fmaf_rn(tx.w1, q[k * kStep + 1], __fmaf_rn(tx.w0, q[k * kStep], Ug[j][k]));
+                    } else if (nk == KR) {
+#pragma unroll
+                        for (int k = 0; k < KR; ++k) {
+                            Ug[j][k] = __fmaf_rn(tx.w1, q[1], __fmaf_rn(tx.w0, q[0], Ug[j][k]));
+                            q += step;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < KR; ++k) {
+                            if (k < nk) Ug[j][k] = __fmaf_rn(tx.w1, q[1], __fmaf_rn(tx.w0, q[0], Ug[j][k]));
+                            q += step;
+                        }
                     }
                 }
             }
         }
-        __syncthreads();   // buffer s & 1, U and yt free for reuse
-    }
-    cp_async_wait_0();
-    if (!active) return;
-    double* dst = partial + ((int64_t)blockIdx.x * geo.total_planes + geo.plane_offset + p) * Ma;
+        if ((bc & 3) == 3 || bc == wb - 1) {   // uniform: every thread takes it together
 #pragma unroll
-    for (int k = 0; k < KR; ++k) {
-        const int r = rp + R * k;
-        if (r < ha) dst[(int64_t)r * wa + c] = (double)Ra[k] - (double)Rc[k];
+            for (int j = 0; j < PB; ++j)
+#pragma unroll
+                for (int k = 0; k < KR; ++k) {
+                    kahan_add(Ua[j][k], Uc[j][k], Ug[j][k]);
+                    Ug[j][k] = 0.0f;
+                }
+        }
+    }
+    if (abort_flag) {
+        // drain any copy still in flight before the CTA exits
+        if (tid == 0)
+            for (int i = 0; i < kSepStages; ++i)
+                if (last_issue[i] >= 0)
+                    mbar_wait_bounded(&full[i], (uint32_t)((last_issue[i] / kSepStages) & 1), nullptr,
+                                      nullptr, geo.timeout_ns);
+        return;
+    }
+    __syncthreads();   // all slices consumed before U is written
+
+    // y-interpolation of this angular row
+    if (active) {
+#pragma unroll
+        for (int j = 0; j < PB; ++j)
+#pragma unroll
+            for (int k = 0; k < KR; ++k) {
+                const int y = rp + R * k;
+                if (k < nk) U[(j * (ha + 2) + y + 1) * wa + c] = Ua[j][k] - Uc[j][k];
+            }
+    }
+    for (int i = tid; i < np * ha; i += kThreads) {
+        const int j = i / ha, y = i - j * ha;
+        Tap t = axis_tap(coef[j].alpha, (float)y - cya, coef[j].qy, (float)br - cyb, cya, ha, 1);
+        t.off = (j * (ha + 2) + t.off) * wa;
+        yt[j * ha + y] = t;
+    }
+    __syncthreads();
+    if (!active) return;
+#pragma unroll
+    for (int j = 0; j < PB; ++j) {
+        if (j < np) {
+            float* dst = partial + ((int64_t)br * geo.total_planes + geo.plane_offset + pbase + j) * Ma;
+#pragma unroll
+            for (int k = 0; k < KR; ++k) {
+                const int r = rp + R * k;
+                if (k < nk) {
+                    const Tap ty = yt[j * ha + r];
+                    const float v0 = U[ty.off + c], v1 = U[ty.off + wa + c];
+                    dst[(int64_t)r * wa + c] = __fmaf_rn(ty.w1, v1, ty.w0 * v0);
+                }
+            }
+        }
     }
 }
 
@@ -271,7 +310,7 @@ template <int KR>
 __global__ void __launch_bounds__(kThreads) refocus_direct_kernel(const float* __restrict__ gamma,
                                                                   const RefocusGeom geo,
                                                                   const PlaneBlock pl,
-                                                                  double* __restrict__ partial) {
+                                                                  float* __restrict__ partial) {
     extern __shared__ __align__(16) float sm[];
     const int ha = geo.ha, wa = geo.wa, hb = geo.hb, wb = geo.wb;
     const int W2 = wa + 2;
@@ -332,20 +371,20 @@ __global__ void __launch_bounds__(kThreads) refocus_direct_kernel(const float* _
         }
     }
     if (!active) return;
-    double* dst = partial + ((int64_t)blockIdx.x * geo.total_planes + geo.plane_offset + p) * Ma;
+    float* dst = partial + ((int64_t)blockIdx.x * geo.total_planes + geo.plane_offset + p) * Ma;
 #pragma unroll
     for (int k = 0; k < KR; ++k) {
         const int r = row0 + rp + R * k;
-        if (r < ha) dst[(int64_t)r * wa + c] = (double)acc[k] - (double)cmp[k];
+        if (r < ha) dst[(int64_t)r * wa + c] = acc[k] - cmp[k];
     }
 }
 
-__global__ void refocus_reduce_kernel(const double* __restrict__ partial, int n_ranges,
+__global__ void refocus_reduce_kernel(const float* __restrict__ partial, int n_ranges,
                                       int64_t per_range, float* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_range;
          i += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
-        for (int r = 0; r < n_ranges; ++r) s += partial[(int64_t)r * per_range + i];
+        for (int r = 0; r < n_ranges; ++r) s += (double)partial[(int64_t)r * per_range + i];
         out[i] = (float)s;
     }
 }
@@ -365,18 +404,20 @@ cudaError_t set_smem_attr(K kernel, int slot) {
     return cudaSuccess;
 }
 
-template <int KR>
-cudaError_t launch_sep(const float* g, const RefocusGeom& geo, const PlaneBlock& pl, double* partial,
-                       size_t smem, cudaStream_t st, int slot) {
-    cudaError_t e = set_smem_attr(refocus_sep_kernel<KR>, slot);
+template <int KR, int kWA = 0, int kHA = 0>
+cudaError_t launch_sep(const CUtensorMap& tm, const RefocusGeom& geo, const PlaneBlock& pl,
+                       float* partial, size_t smem, cudaStream_t st, int slot) {
+    cudaError_t e = set_smem_attr(refocus_sep_kernel<KR, kSepPlanes, kWA, kHA>, slot);
     if (e != cudaSuccess) return e;
-    refocus_sep_kernel<KR><<<dim3(geo.n_ranges, geo.n_planes), kThreads, smem, st>>>(g, geo, pl, partial);
+    const int pblocks = (geo.n_planes + kSepPlanes - 1) / kSepPlanes;
+    refocus_sep_kernel<KR, kSepPlanes, kWA, kHA><<<dim3(geo.hb, pblocks), kThreads, smem, st>>>(tm, geo, pl,
+                                                                                                partial);
     return cudaGetLastError();
 }
 
 template <int KR>
 cudaError_t launch_direct(const float* g, const RefocusGeom& geo, const PlaneBlock& pl,
-                          double* partial, int zchunks, size_t smem, cudaStream_t st, int slot) {
+                          float* partial, int zchunks, size_t smem, cudaStream_t st, int slot) {
     cudaError_t e = set_smem_attr(refocus_direct_kernel<KR>, slot);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)geo.n_ranges, (unsigned)geo.n_planes, (unsigned)zchunks);
@@ -393,24 +434,31 @@ int kr_for(int ha, int wa, int cap) {
 
 }  // namespace
 
+static size_t sep_smem(int ha, int wa) {
+    const size_t slice_f = ((size_t)ha * (wa + kPadL + kPadR) + 31) & ~(size_t)31;
+    return 128 + sizeof(float) * (kSepStages * slice_f + (size_t)kSepPlanes * (ha + 2) * wa) +
+           sizeof(Tap) * (kSepStages * (size_t)kSepPlanes * wa + (size_t)kSepPlanes * ha);
+}
+
 bool refocus_separable(int ha, int wa) {
+    // TMA staging: the box is (wa + 8) x ha floats, each side <= 256, rows 16-byte multiples
+    if (wa % 4 != 0 || wa + kPadL + kPadR > 256 || ha > 256) return false;
     if (wa > kThreads) return false;
     const int R = kThreads / wa;
-    if ((ha + R - 1) / R > 16) return false;
-    return refocus_smem_bytes(ha, wa) <= 200 * 1024;
+    if ((ha + R - 1) / R > 8) return false;
+    return sep_smem(ha, wa) <= 112 * 1024;
 }
 
 size_t refocus_smem_bytes(int ha, int wa) {
-    const size_t sep = sizeof(float) * (2 * (size_t)ha * (wa + kPadL + kPadR) + (size_t)(ha + 2) * wa) +
-                       sizeof(Tap) * (2 * (size_t)wa + (size_t)ha);
-    const int R = wa <= kThreads ? kThreads / wa : 1;
-    if (wa <= kThreads && (ha + R - 1) / R <= 16 && sep <= 200 * 1024) return sep;
+    if (refocus_separable(ha, wa)) return sep_smem(ha, wa);
     return sizeof(float) * (size_t)(ha + 2) * (wa + 2) + sizeof(Tap) * ((size_t)wa + ha);
 }
 
 int refocus_ranges(int ha, int wa, int hb, int wb, int n_planes, int sm_count) {
-    // ranges of angular rows (separable kernel) or of angular pixels (direct kernel)
-    const int units = refocus_separable(ha, wa) ? hb : hb * wb;
+    // separable kernel: one range per angular row; direct kernel: ranges of
+    // angular pixels sized to fill the GPU
+    if (refocus_separable(ha, wa)) return hb;
+    const int units = hb * wb;
     int target = (4 * sm_count + n_planes - 1) / (n_planes > 0 ? n_planes : 1);
     if (target < 1) target = 1;
     if (target > units) target = units;
@@ -419,20 +467,23 @@ int refocus_ranges(int ha, int wa, int hb, int wb, int n_planes, int sm_count) {
 }
 
 int refocus_range_size(int ha, int wa, int hb, int wb, int n_ranges) {
-    const int units = refocus_separable(ha, wa) ? hb : hb * wb;
-    return (units + n_ranges - 1) / n_ranges;
+    if (refocus_separable(ha, wa)) return 1;
+    return (hb * wb + n_ranges - 1) / n_ranges;
 }
 
-cudaError_t launch_refocus(const float* gamma_f32, const RefocusGeom& geo, const PlaneBlock& pl,
-                           double* partial, cudaStream_t st) {
+cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const RefocusGeom& geo,
+                           const PlaneBlock& pl, float* partial, cudaStream_t st) {
     const size_t smem = refocus_smem_bytes(geo.ha, geo.wa);
     if (refocus_separable(geo.ha, geo.wa)) {
-        switch (kr_for(geo.ha, geo.wa, 16)) {
-            case 1: return launch_sep<1>(gamma_f32, geo, pl, partial, smem, st, 0);
-            case 2: return launch_sep<2>(gamma_f32, geo, pl, partial, smem, st, 1);
-            case 4: return launch_sep<4>(gamma_f32, geo, pl, partial, smem, st, 2);
-            case 8: return launch_sep<8>(gamma_f32, geo, pl, partial, smem, st, 3);
-            default: return launch_sep<16>(gamma_f32, geo, pl, partial, smem, st, 4);
+        if (tm == nullptr) return cudaErrorInvalidValue;
+        // compile-time shapes of the common square detector sizes
+        if (geo.wa == 64 && geo.ha == 64) return launch_sep<8, 64, 64>(*tm, geo, pl, partial, smem, st, 10);
+        if (geo.wa == 32 && geo.ha == 32) return launch_sep<2, 32, 32>(*tm, geo, pl, partial, smem, st, 11);
+        switch (kr_for(geo.ha, geo.wa, 8)) {
+            case 1: return launch_sep<1>(*tm, geo, pl, partial, smem, st, 0);
+            case 2: return launch_sep<2>(*tm, geo, pl, partial, smem, st, 1);
+            case 4: return launch_sep<4>(*tm, geo, pl, partial, smem, st, 2);
+            default: return launch_sep<8>(*tm, geo, pl, partial, smem, st, 3);
         }
     }
     const int R = kThreads / geo.wa;
@@ -447,7 +498,7 @@ cudaError_t launch_refocus(const float* gamma_f32, const RefocusGeom& geo, const
     }
 }
 
-cudaError_t launch_refocus_reduce(const double* partial, int n_ranges, int64_t per_range,
+cudaError_t launch_refocus_reduce(const float* partial, int n_ranges, int64_t per_range,
                                   float* out, cudaStream_t st) {
     int64_t blocks = (per_range + 255) / 256;
     if (blocks > 4096) blocks = 4096;

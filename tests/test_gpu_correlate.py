@@ -223,3 +223,31 @@ def test_wait_timeout_is_reported_and_context_survives():
     got = gpu_correlate(fr, lay["a"], lay["b"], acq.n_frames)
     want = oracle_correlate(fr.cpu().numpy(), lay["a"], lay["b"], acq.n_frames)
     assert_exact(got, want)
+
+
+@pytest.mark.parametrize("bit_order,xa,xb,wa,wb", [(0, 0, 64, 64, 32), (1, 0, 64, 64, 32),
+                                                   (0, 5, 77, 64, 32), (1, 3, 70, 32, 64),
+                                                   (0, 1, 40, 37, 20)])
+def test_bit_layouts_match_oracle(bit_order, xa, xb, wa, wb):
+    """Region origins off word boundaries, MSB-first bytes, widths that are and
+    are not multiples of 32 (word-load path and per-pixel path)."""
+    rng = np.random.default_rng(bit_order * 100 + xa)
+    n, H = 1500, 6
+    W = max(xa + wa, xb + wb) + 3
+    img = (rng.random((n, H, W)) < 0.35).astype(np.uint8)
+    flat = torch.from_numpy(img.reshape(n, H * W))
+    pad = (-flat.shape[1]) % 32
+    flat = torch.cat([flat, torch.zeros((n, pad), dtype=torch.uint8)], 1)
+    packed = synth.pack_bits_lsb(flat)
+    if bit_order == 1:
+        lut = torch.tensor([int('{:08b}'.format(v)[::-1], 2) for v in range(256)], dtype=torch.uint8)
+        packed = lut[packed.long()]
+    fs = packed.shape[1]
+    fr = packed.contiguous().cuda()
+    la = dict(bits=1, height=H, width=wa, x0=xa, y0=0, row_stride=W, frame_stride_bytes=fs, bit_order=bit_order)
+    lb = dict(bits=1, height=H - 1, width=wb, x0=xb, y0=1, row_stride=W, frame_stride_bytes=fs, bit_order=bit_order)
+    got = gpu_correlate(fr, la, lb, n)
+    want = oracle_correlate(fr.cpu().numpy(), la, lb, n)
+    assert_exact(got, want)
+    A = img[:, 0:H, xa:xa + wa].reshape(n, -1).astype(np.int64)
+    assert np.array_equal(got["s_a"].numpy(), A.sum(0))
