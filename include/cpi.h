@@ -180,6 +180,33 @@ CPI_API cpi_status cpi_refocus(const float *gamma_f32, int32_t ha, int32_t wa, i
                        size_t workspace_bytes, cpi_stream stream);
 
 /* --------------------------------------------------------------------------
+ * Eq. (1) without a caller workspace (the paper has no counterpart).
+ *
+ * For callers that cannot allocate device memory: a real-time acquisition loop
+ * for which cudaMalloc's implicit device synchronisation and unbounded latency
+ * are not acceptable, or a host application or plugin whose own allocator owns
+ * all device memory and forbids allocations by libraries.  Same inputs, outputs
+ * and results as cpi_correlate; the scratch is instead a fixed array of
+ * CPI_NOALLOC_SCRATCH_BYTES that the library keeps in the device memory of every
+ * GPU that loads it, until the process exits.  The call allocates nothing and
+ * calls no allocating routine.
+ *   - Problems whose workspace (cpi_correlate_workspace_size) exceeds
+ *     CPI_NOALLOC_SCRATCH_BYTES are refused with CPI_ERR_WORKSPACE.
+ *   - The first call on a device looks up the array's device address (set-up,
+ *     once per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls on a device share the one array and leave their data in it:
+ *     calls that may overlap on the GPU (different streams, or the same stream
+ *     from several host threads without ordering) race on it; serialise them.
+ *     Nothing in the array needs to start at zero: each call writes every
+ *     scratch byte before reading it.
+ * -------------------------------------------------------------------------- */
+#define CPI_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+CPI_API cpi_status cpi_correlate_noalloc(const cpi_frames *a, const cpi_frames *b, int64_t n_frames,
+                                         int64_t *s_ab, int64_t *s_a, int64_t *s_b, double *gamma,
+                                         float *gamma_f32, cpi_stream stream);
+
+/* --------------------------------------------------------------------------
  * Learned denoiser of Gamma (a small convolutional network mapping Gamma from
  * few frames to Gamma from many).  Not part of the paper's method; not
  * implemented in this build: always returns CPI_ERR_UNSUPPORTED.

@@ -18,7 +18,8 @@ __all__ = [
     "cpi_correlate_workspace_size", "cpi_correlate", "cpi_correlate_accumulate",
     "cpi_correlate_finalize", "cpi_correlate_stage", "cpi_refocus_workspace_size", "cpi_refocus",
     "cpi_denoise", "cpi_device_status", "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout",
-    "CPI_STAGE_INGEST", "CPI_STAGE_MOMENTS", "CPI_STAGE_FOLD", "EXPORTED",
+    "CPI_STAGE_INGEST", "CPI_STAGE_MOMENTS", "CPI_STAGE_FOLD", "EXPORTED", "cpi_correlate_noalloc",
+    "NOALLOC_SCRATCH_BYTES",
 ]
 
 CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD = 1, 2, 3
@@ -30,8 +31,9 @@ EXPORTED = [
     "cpi_status_string", "cpi_abi_version", "cpi_correlate_workspace_size", "cpi_correlate",
     "cpi_correlate_accumulate", "cpi_correlate_finalize", "cpi_correlate_stage",
     "cpi_refocus_workspace_size", "cpi_refocus", "cpi_denoise", "cpi_device_status",
-    "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout",
+    "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout", "cpi_correlate_noalloc",
 ]
+NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 class CpiError(RuntimeError):
@@ -92,6 +94,7 @@ def load(path: str | None = None):
         "cpi_device_status": ([_P, i32], st),
         "cpi_set_wait_timeout_ns": ([i64], None),
         "cpi_selftest_wait_timeout": ([i64, _P], st),
+        "cpi_correlate_noalloc": ([_F, _F, i64, _P, _P, _P, _P, _P, _P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -207,6 +210,14 @@ def cpi_device_status(stream=None, clear: bool = True) -> int:
 
 def cpi_set_wait_timeout_ns(ns: int) -> None:
     load().cpi_set_wait_timeout_ns(int(ns))
+
+
+def cpi_correlate_noalloc(a, b, n_frames, s_ab, s_a, s_b, gamma, gamma_f32, stream=None):
+    """Eq. (1) using the library's built-in scratch instead of a caller workspace,
+    for callers that cannot allocate device memory (see include/cpi.h)."""
+    _check(load().cpi_correlate_noalloc(ctypes.byref(a), ctypes.byref(b), n_frames, _ptr(s_ab),
+                                        _ptr(s_a), _ptr(s_b), _ptr(gamma), _ptr(gamma_f32),
+                                        _stream(stream)), "cpi_correlate_noalloc")
 
 
 def cpi_selftest_wait_timeout(timeout_ns: int, stream=None):

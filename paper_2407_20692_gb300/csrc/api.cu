@@ -15,6 +15,12 @@ namespace cpi {
 // error bits into it).  A file-scope __device__ variable: no allocation.
 __device__ unsigned int g_device_status;
 
+// Built-in scratch of cpi_correlate_noalloc: CPI_NOALLOC_SCRATCH_BYTES of device
+// memory that every GPU loading the library holds until the process exits.
+// Host code must not pass its name to a kernel (on the host it is only a
+// stand-in); the device address comes from cudaGetSymbolAddress, once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[CPI_NOALLOC_SCRATCH_BYTES];
+
 namespace {
 
 constexpr int kMaxDevices = 64;
@@ -430,6 +436,41 @@ cpi_status cpi_device_status(cpi_stream stream, int32_t clear) {
 
 void cpi_set_wait_timeout_ns(int64_t ns) {
     g_timeout_ns = ns > 0 ? (unsigned long long)ns : 2000000000ull;
+}
+
+cpi_status cpi_correlate_noalloc(const cpi_frames* a, const cpi_frames* b, int64_t n_frames,
+                                 int64_t* s_ab, int64_t* s_a, int64_t* s_b, double* gamma,
+                                 float* gamma_f32, cpi_stream stream) {
+    // Set-up, once per device with that device current: the device address of
+    // the built-in scratch array.
+    static void* scratch[kMaxDevices] = {};
+    static std::mutex scratch_mu;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CPI_ERR_CUDA;
+    void* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(scratch_mu);
+        if (scratch[dev] == nullptr) {
+            void* p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr)
+                return CPI_ERR_CUDA;
+            scratch[dev] = p;
+        }
+        ws = scratch[dev];
+    }
+    // The problem must fit the built-in scratch; nothing is allocated otherwise.
+    DeviceInfo* info = nullptr;
+    if (device_info(&info) != cudaSuccess) return CPI_ERR_CUDA;
+    CorrPlan pl;
+    const cpi_status s = make_plan(a, b, n_frames, info->sm_count, &pl);
+    if (s != CPI_OK) return s;
+    if (pl.ws_bytes > (size_t)CPI_NOALLOC_SCRATCH_BYTES) return CPI_ERR_WORKSPACE;
+    // Every scratch byte a call reads is written earlier in the same call
+    // (operand rows including their zero padding, then one partial slot per
+    // unit), so nothing left by a previous call needs clearing.
+    static const int32_t stages[3] = {CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD};
+    return correlate_common(stages, 3, a, b, n_frames, 0, s_ab, s_a, s_b, gamma, gamma_f32, ws,
+                            (size_t)CPI_NOALLOC_SCRATCH_BYTES, stream);
 }
 
 cpi_status cpi_selftest_wait_timeout(int64_t timeout_ns, cpi_stream stream) {
