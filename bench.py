@@ -143,6 +143,13 @@ def _max_over_ranks(world, x: float) -> float:
     return float(t.item())
 
 
+def replica_throughput(world: int, work_per_rank: float, seconds: float):
+    """Whole-job throughput of `world` independent replicas: the work all ranks
+    did divided by the slowest rank's time (tera-units per second)."""
+    t_max = _max_over_ranks(world, seconds)
+    return world * work_per_rank / t_max / 1e12, t_max
+
+
 # ----------------------------------------------------------------------------- CPU oracle
 
 def oracle_sample(acq, planes, frames_host, lay, n_rows: int, n_planes: int):
@@ -251,35 +258,16 @@ def run_native(args, world, rank, local):
     parts = [[ev[i].elapsed_time(ev[i + 1]) for i in range(4)] for ev in evs]
     step_ms = [sum(p) for p in parts]
     total_s = sum(step_ms) / 1e3
-    total_s_max = _max_over_ranks(world, total_s)
     ops = 2.0 * ma * mb * n
-    value = world * ops * args.steps / total_s_max / 1e12
+    value, total_s_max = replica_throughput(world, ops * args.steps, total_s)
     mean = lambda i: sum(p[i] for p in parts) / args.steps
     ingest_ms, moments_ms, fold_ms, refocus_ms = mean(0), mean(1), mean(2), mean(3)
 
     # ---------------------------------------------------------------- roofline
-    peaks, src = _peaks()
-    fp8_peak = 2.0 * peaks["bf16_tflops"]          # E4M3 pipe: BF16 measured x nominal 4.5/2.25
-    kernels = {
-        "moments": moments_ms, "refocus": refocus_ms, "ingest": ingest_ms, "fold": fold_ms,
-    }
-    dominant = max(kernels, key=kernels.get)
-    bytes_ingest = (ma + mb) * n / 8 + (ma + mb) * ws_row_bytes(n, acq.bits)
-    bytes_fold = ma * mb * (4 + 8 + 8 + 4)
-    bytes_refocus = n_planes * ma * mb * 4 + n_planes * ma * 4
-    if dominant == "moments":
-        ach = ops / (moments_ms / 1e3) / 1e12
-        roof = {"kernel": "moments (tcgen05 kind::f8f6f4, E4M3 0/1 operands)", "bound": "tensor",
-                "achieved": ach, "peak": fp8_peak, "unit": "TFLOP/s", "frac": ach / fp8_peak,
-                "traffic": None,
-                "peak_source": f"{src} bf16 burst x 2 (nominal E4M3/BF16 dense ratio)"}
-    else:
-        by = {"refocus": bytes_refocus, "ingest": bytes_ingest, "fold": bytes_fold}[dominant]
-        ach = by / (kernels[dominant] / 1e3) / 1e9
-        roof = {"kernel": dominant, "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": f"{src} hbm copy"}
-
+    roofs = rooflines(ma, mb, n, n_planes, acq.bits, dict(ingest=ingest_ms, moments=moments_ms,
+                                                          fold=fold_ms, refocus=refocus_ms))
+    dominant = max(roofs, key=lambda k: roofs[k]["ms"])
+    roof = dict(roofs[dominant])
     # ---------------------------------------------------------------- e2e through the C ABI
     e2e = e2e_run(args, cpi, fr, lay, n, stream, dev, planes, n_planes, ws, rws)
     e2e_value = world * ops / _max_over_ranks(world, e2e["s_per_step"]) / 1e12
@@ -307,7 +295,10 @@ def run_native(args, world, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "u1 -> e4m3 tensor-core (exact fp32 partials), int64 sums, f64 Gamma, f32 refocus",
+        "dtype": ("u1 -> e4m3 tensor-core (exact fp32 partials), int64 sums, f64 Gamma, f32 refocus"
+                  if acq.bits == 1 else
+                  "u8 -> bf16 tensor-core (exact fp32 partials folded every 256 frames), int64 sums, "
+                  "f64 Gamma, f32 refocus"),
         "data": "synthetic (seeded chaotic-light source model; stand-in for the SwissSPAD2 dataset)",
         "config": {"workload": f"{args.workload}: spatial {ha}x{wa} vs angular {hb}x{wb}, "
                                f"{'binary bit-packed' if acq.bits == 1 else 'uint8'} frames side by side, "
@@ -318,6 +309,7 @@ def run_native(args, world, rank, local):
         "gamma_tops": ops / ((ingest_ms + moments_ms + fold_ms) / 1e3) / 1e12,
         "refocus_planes_per_s": n_planes / (refocus_ms / 1e3),
         "roofline": roof,
+        "rooflines_all": roofs,
         "e2e": {"value": e2e_value, "unit": "TOPS (int8-equivalent)",
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                 "ms_per_step": e2e["s_per_step"] * 1e3},
@@ -328,6 +320,77 @@ def run_native(args, world, rank, local):
     if cpu is not None:
         line["cpu_baseline"] = cpu
     return line
+
+
+SM_COUNT = 152
+SMEM_BYTES_PER_CLK = 128          # shared-memory load bandwidth per SM per clock
+
+
+def _traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, valid only while the
+    kernel's source files are unchanged since the capture (else None)."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        table = json.load(f)
+    ent = table.get(kernel_key)
+    if not ent:
+        return None
+    h = hashlib.sha256()
+    for rel in ent["sources"]:
+        src = os.path.join(ROOT, rel)
+        if not os.path.exists(src):
+            return None
+        h.update(open(src, "rb").read())
+    if h.hexdigest() != ent["sha256"]:
+        return None
+    return ent["dram_bytes_per_launch"]
+
+
+def rooflines(ma, mb, n, n_planes, bits, ms):
+    """Roofline of each stage: algorithmic work per launch / measured time,
+    against the measured peak of its bound (MEASURED_PEAKS.json)."""
+    peaks, src = _peaks()
+    ops = 2.0 * ma * mb * n
+    out = {}
+    if bits == 1:
+        tc_peak, tc_src = 2.0 * peaks["bf16_tflops"], f"{src} bf16 burst x 2 (nominal E4M3/BF16 dense ratio)"
+        kname = "moments (tcgen05 kind::f8f6f4, E4M3 0/1 operands)"
+    else:
+        tc_peak, tc_src = peaks["bf16_tflops"], f"{src} bf16 burst"
+        kname = "moments (tcgen05 kind::f16, BF16 integer operands)"
+    a = ops / (ms["moments"] / 1e3) / 1e12
+    out["moments"] = {"kernel": kname, "bound": "tensor", "achieved": a, "peak": tc_peak,
+                      "unit": "TFLOP/s", "frac": a / tc_peak, "traffic": _traffic("moments"),
+                      "peak_source": tc_src, "ms": ms["moments"],
+                      "work": "2*Ma*Mb*N int8-equivalent ops"}
+    kpad = (n + 255) // 256 * 256 if bits == 1 else (n + 127) // 128 * 128
+    ing = (ma + mb) * n * bits / 8 + (ma + mb) * kpad * (1 if bits == 1 else 2)
+    a = ing / (ms["ingest"] / 1e3) / 1e9
+    out["ingest"] = {"kernel": "ingest (frames -> K-major operands, marginals)", "bound": "hbm",
+                     "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
+                     "traffic": _traffic("ingest"), "peak_source": f"{src} hbm copy", "ms": ms["ingest"],
+                     "work": "frame bytes read + operand bytes written"}
+    fb = ma * mb * (4 + 8 + 8 + 4)
+    a = fb / (ms["fold"] / 1e3) / 1e9
+    out["fold"] = {"kernel": "fold (int64 S_ab, FP64 Gamma, FP32 slice-major copy)", "bound": "hbm",
+                   "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
+                   "traffic": _traffic("fold"), "peak_source": f"{src} hbm copy", "ms": ms["fold"],
+                   "work": "24 B per Gamma entry"}
+    smem = n_planes * ma * mb * 8.0
+    smem_peak = SM_COUNT * SMEM_BYTES_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+    a = smem / (ms["refocus"] / 1e3) / 1e9
+    eff = n_planes * ma * mb * 4.0 / (ms["refocus"] / 1e3) / 1e9
+    out["refocus"] = {"kernel": "refocus (separable bilinear shift-and-sum + row reduce)", "bound": "smem",
+                      "achieved": a, "peak": smem_peak, "unit": "GB/s", "frac": a / smem_peak,
+                      "traffic": _traffic("refocus"),
+                      "peak_source": "derived: 152 SMs x 128 B/clk shared-memory loads x max SM clock",
+                      "ms": ms["refocus"], "work": "8 B of shared-memory reads per (plane, row, column, angular pixel)",
+                      "per_plane_gamma_gbs": eff, "per_plane_gamma_frac_of_hbm": eff / peaks["hbm_gbs"]}
+    return out
 
 
 def ws_row_bytes(n, bits):

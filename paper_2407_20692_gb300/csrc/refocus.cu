@@ -19,9 +19,9 @@
 // point of Section 4.1), per slice for the W_a columns and per angular row for
 // the H_a rows, in double-float arithmetic on the FP32 pipe (~48-bit
 // significands; GB300's FP64 pipe is a small fraction of its FP32 rate).  All
-// sums are Kahan-compensated FP32; partial images of each range of angular rows
-// are written in double and added in a fixed order by a second kernel, so the
-// result is deterministic.
+// sums are Kahan-compensated FP32; the partial image of each angular row is
+// written in FP32 and the rows are added in a fixed order (Kahan-compensated)
+// by a second kernel, so the result is deterministic.
 //
 // Layout: Gamma arrives slice-major, float [Mb][Ma]; slice b is one contiguous
 // spatial image, staged into shared memory with cp.async (double-buffered),
@@ -120,7 +120,7 @@ __device__ __forceinline__ PlaneCoef plane_coef(const PlaneBlock& pl, int p, int
 // Every staged slice is interpolated along x for all PB planes; after the last
 // bc the row's U images are interpolated along y and this angular row's
 // contribution to each output pixel is written to partial[br][plane][pixel].
-// The reduce kernel adds the angular rows in double, in a fixed order.
+// The reduce kernel adds the angular rows in a fixed order (compensated FP32).
 // kWA > 0 fixes the image width (and kHA the height) at compile time, so every
 // row offset of the inner loop is an immediate; kWA == 0 is the general form.
 template <int KR, int PB, int kWA, int kHA>
@@ -132,8 +132,9 @@ __global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_c
     const int ha = kWA ? kHA : geo.ha, wa = kWA ? kWA : geo.wa, hb = geo.hb, wb = geo.wb;
     const int WS = wa + kPadL + kPadR;                 // staged slice row stride (TMA box width)
     const int slice_f = (ha * WS + 31) & ~31;          // buffer stride: 128-byte multiples
-    float* const buf0 = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sm_raw) + 127) &
-                                                 ~static_cast<uintptr_t>(127));
+    // 128-byte aligned start, computed on the shared-window offset so that the
+    // pointers stay shared-space (the loads below compile to shared loads)
+    float* const buf0 = sm_raw + (((128u - (static_cast<uint32_t>(__cvta_generic_to_shared(sm_raw)) & 127u)) & 127u) >> 2);
     float* const U = buf0 + kSepStages * slice_f;      // PB x (ha + 2) x wa, zero rows -1 and ha
     Tap* const xt = reinterpret_cast<Tap*>(U + PB * (ha + 2) * wa);   // [kSepStages][PB][wa]
     Tap* const yt = xt + kSepStages * PB * wa;                        // [PB][ha]
@@ -191,9 +192,9 @@ __global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_c
         taps(bc);
     }
 
-    // U accumulates plainly (two fused multiply-adds per slice) over groups of
-    // <= 4 slices (Ug); the group sums are Kahan-added (Ua, Uc): error <=
-    // (8 + 2) 2^-24 of the summed magnitudes, to first order.
+    // U accumulates plainly (two fused multiply-adds per slice) over pairs of
+    // slices (Ug); the pair sums are Kahan-added (Ua, Uc): error <= (4 + 2) 2^-24
+    // of the summed magnitudes, to first order.
     float Ug[PB][KR], Ua[PB][KR], Uc[PB][KR];
 #pragma unroll
     for (int j = 0; j < PB; ++j)
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_c
                 }
             }
         }
-        if ((bc & 3) == 3 || bc == wb - 1) {   // uniform: every thread takes it together
+        if ((bc & 1) == 1 || bc == wb - 1) {   // uniform: every thread takes it together
 #pragma unroll
             for (int j = 0; j < PB; ++j)
 #pragma unroll
@@ -379,13 +380,15 @@ __global__ void __launch_bounds__(kThreads) refocus_direct_kernel(const float* _
     }
 }
 
+// Sum of the per-range partial images in a fixed order, Kahan-compensated in
+// FP32 (error <= 2 * 2^-24 of the summed magnitudes, to first order).
 __global__ void refocus_reduce_kernel(const float* __restrict__ partial, int n_ranges,
                                       int64_t per_range, float* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_range;
          i += (int64_t)gridDim.x * blockDim.x) {
-        double s = 0.0;
-        for (int r = 0; r < n_ranges; ++r) s += (double)partial[(int64_t)r * per_range + i];
-        out[i] = (float)s;
+        float acc = 0.0f, cmp = 0.0f;
+        for (int r = 0; r < n_ranges; ++r) kahan_add(acc, cmp, __ldg(partial + (int64_t)r * per_range + i));
+        out[i] = acc - cmp;
     }
 }
 
