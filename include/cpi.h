@@ -180,6 +180,46 @@ CPI_API cpi_status cpi_refocus(const float *gamma_f32, int32_t ha, int32_t wa, i
                        size_t workspace_bytes, cpi_stream stream);
 
 /* --------------------------------------------------------------------------
+ * Batches of independent acquisitions of uneven sizes (many correlations and
+ * their refocusings in one call).  The paper processes one acquisition at a
+ * time; a batch runs every item's Eq. (1) and refocusing as above, but the
+ * raw-moment units of all items of one operand kind share persistent grouped
+ * tensor-core launches (up to 64 problems each, larger units first), and the
+ * whole sequence can be replayed as one CUDA graph.
+ *
+ * Per item: a, b, n_frames and the outputs exactly as for cpi_correlate (s_ab,
+ * s_a, s_b required; gamma optional; gamma_f32 optional unless refocusing);
+ * n_planes > 0 also refocuses gamma_f32 into refocus_out [n_planes][ha][wa]
+ * with the HOST array planes (as cpi_refocus).  Items must not share outputs.
+ *
+ * flags: CPI_BATCH_GRAPH captures the launches into a CUDA graph on first use
+ *   and replays it on later calls whose items (shapes, pointers, planes),
+ *   workspace and settings are the same (a small per-device cache; the CUDA
+ *   driver may reserve memory for each instantiated graph).
+ *   CPI_BATCH_TUNE chooses, on first use of a batch shape, the frame-chunk
+ *   split of the grouped launches (1, 2 or 4 times the minimum) by timing
+ *   them; this first call synchronises the stream.
+ * -------------------------------------------------------------------------- */
+typedef struct cpi_batch_item {
+    cpi_frames a, b;
+    int64_t n_frames;
+    int64_t *s_ab, *s_a, *s_b;  /* device, as cpi_correlate */
+    double *gamma;              /* device, [Ma][Mb], or NULL */
+    float *gamma_f32;           /* device, [Mb][Ma] slice-major; required when n_planes > 0 */
+    const cpi_plane *planes;    /* HOST, n_planes entries */
+    int32_t n_planes;           /* 0: no refocusing */
+    float *refocus_out;         /* device, [n_planes][ha][wa] */
+} cpi_batch_item;
+
+enum { CPI_BATCH_GRAPH = 1, CPI_BATCH_TUNE = 2 };
+
+/* Workspace bytes of a batch (0 on invalid items). */
+CPI_API size_t cpi_batch_workspace_size(const cpi_batch_item *items, int32_t n_items);
+
+CPI_API cpi_status cpi_batch_correlate(const cpi_batch_item *items, int32_t n_items, void *workspace,
+                                       size_t workspace_bytes, int32_t flags, cpi_stream stream);
+
+/* --------------------------------------------------------------------------
  * Eq. (1) without a caller workspace (the paper has no counterpart).
  *
  * For callers that cannot allocate device memory: a real-time acquisition loop

@@ -19,8 +19,10 @@ __all__ = [
     "cpi_correlate_finalize", "cpi_correlate_stage", "cpi_refocus_workspace_size", "cpi_refocus",
     "cpi_denoise", "cpi_device_status", "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout",
     "CPI_STAGE_INGEST", "CPI_STAGE_MOMENTS", "CPI_STAGE_FOLD", "EXPORTED", "cpi_correlate_noalloc",
-    "NOALLOC_SCRATCH_BYTES",
+    "NOALLOC_SCRATCH_BYTES", "cpi_batch_item", "batch_items", "CPI_BATCH_GRAPH", "CPI_BATCH_TUNE",
+    "cpi_batch_workspace_size", "cpi_batch_correlate",
 ]
+CPI_BATCH_GRAPH, CPI_BATCH_TUNE = 1, 2
 
 CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD = 1, 2, 3
 STATUS = {0: "CPI_OK", 1: "CPI_ERR_INVALID_ARG", 2: "CPI_ERR_OVERFLOW", 3: "CPI_ERR_WORKSPACE",
@@ -32,6 +34,7 @@ EXPORTED = [
     "cpi_correlate_accumulate", "cpi_correlate_finalize", "cpi_correlate_stage",
     "cpi_refocus_workspace_size", "cpi_refocus", "cpi_denoise", "cpi_device_status",
     "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout", "cpi_correlate_noalloc",
+    "cpi_batch_workspace_size", "cpi_batch_correlate",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -58,6 +61,22 @@ class cpi_frames(ctypes.Structure):
 
 class cpi_plane(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
+class cpi_batch_item(ctypes.Structure):
+    _fields_ = [
+        ("a", cpi_frames),
+        ("b", cpi_frames),
+        ("n_frames", ctypes.c_int64),
+        ("s_ab", ctypes.c_void_p),
+        ("s_a", ctypes.c_void_p),
+        ("s_b", ctypes.c_void_p),
+        ("gamma", ctypes.c_void_p),
+        ("gamma_f32", ctypes.c_void_p),
+        ("planes", ctypes.POINTER(cpi_plane)),
+        ("n_planes", ctypes.c_int32),
+        ("refocus_out", ctypes.c_void_p),
+    ]
 
 
 _lib = None
@@ -95,6 +114,8 @@ def load(path: str | None = None):
         "cpi_set_wait_timeout_ns": ([i64], None),
         "cpi_selftest_wait_timeout": ([i64, _P], st),
         "cpi_correlate_noalloc": ([_F, _F, i64, _P, _P, _P, _P, _P, _P], st),
+        "cpi_batch_workspace_size": ([ctypes.POINTER(cpi_batch_item), i32], sz),
+        "cpi_batch_correlate": ([ctypes.POINTER(cpi_batch_item), i32, _P, sz, i32, _P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -218,6 +239,33 @@ def cpi_correlate_noalloc(a, b, n_frames, s_ab, s_a, s_b, gamma, gamma_f32, stre
     _check(load().cpi_correlate_noalloc(ctypes.byref(a), ctypes.byref(b), n_frames, _ptr(s_ab),
                                         _ptr(s_a), _ptr(s_b), _ptr(gamma), _ptr(gamma_f32),
                                         _stream(stream)), "cpi_correlate_noalloc")
+
+
+def batch_items(entries):
+    """ctypes array of cpi_batch_item from dicts with keys a, b, n_frames, s_ab,
+    s_a, s_b, gamma, gamma_f32 (tensors or None), planes (plane_array or None),
+    refocus_out (tensor or None).  Keep `entries` alive while the array is used."""
+    arr = (cpi_batch_item * len(entries))()
+    for i, e in enumerate(entries):
+        it = arr[i]
+        it.a, it.b, it.n_frames = e["a"], e["b"], e["n_frames"]
+        for k in ("s_ab", "s_a", "s_b", "gamma", "gamma_f32", "refocus_out"):
+            t = e.get(k)
+            setattr(it, k, None if t is None else t.data_ptr())
+        pl = e.get("planes")
+        it.planes = ctypes.cast(pl, ctypes.POINTER(cpi_plane)) if pl is not None else None
+        it.n_planes = len(pl) if pl is not None else 0
+    return arr
+
+
+def cpi_batch_workspace_size(items) -> int:
+    return load().cpi_batch_workspace_size(items, len(items))
+
+
+def cpi_batch_correlate(items, workspace, flags=CPI_BATCH_GRAPH | CPI_BATCH_TUNE, stream=None):
+    _check(load().cpi_batch_correlate(items, len(items), _ptr(workspace),
+                                      workspace.numel() * workspace.element_size(), flags,
+                                      _stream(stream)), "cpi_batch_correlate")
 
 
 def cpi_selftest_wait_timeout(timeout_ns: int, stream=None):

@@ -1,10 +1,14 @@
 // C ABI of the library (include/cpi.h): argument validation, the execution plan
 // of the correlation (operand format, tiles, frame chunks, workspace layout),
 // TMA descriptors, launches and the per-device status word.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
+#include <unordered_map>
+#include <vector>
 
 #include "../../include/cpi.h"
 #include "kernels.cuh"
@@ -150,8 +154,10 @@ struct CorrPlan {
     size_t off_a, off_b, off_part, ws_bytes;
 };
 
+// split == 0: single correlation (more frame chunks when the tiles alone cannot
+// fill the GPU); split >= 1: member of a batch, split x the minimum chunk count.
 cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm_count,
-                     CorrPlan* pl) {
+                     CorrPlan* pl, int split = 0) {
     cpi_status s = check_frames(a);
     if (s != CPI_OK) return s;
     s = check_frames(b);
@@ -177,7 +183,11 @@ cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm
     p.kb_per_fold = p.bf16 ? 256 / sh.k_per_block : max_kb_chunk;
     const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;
     int n_chunks = (p.k_blocks + max_kb_chunk - 1) / max_kb_chunk;
-    if (tiles < sm_count) {
+    if (split >= 1) {
+        const int max_by_len = p.k_blocks / (p.bf16 ? p.kb_per_fold : 8) > 0
+                                   ? p.k_blocks / (p.bf16 ? p.kb_per_fold : 8) : 1;
+        n_chunks = n_chunks * split < max_by_len ? n_chunks * split : (max_by_len > n_chunks ? max_by_len : n_chunks);
+    } else if (tiles < sm_count) {
         // small outputs: split the frames further so every SM gets work, but keep
         // each chunk at least one exact-fold segment long
         int want = (int)(sm_count / tiles);
@@ -203,6 +213,19 @@ cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm
 
 cpi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CPI_OK : CPI_ERR_CUDA; }
 
+void fill_problem(const CorrPlan& pl, int32_t* part, int unit_begin, MomentsProblem* P) {
+    P->partial = part;
+    P->M = (int32_t)pl.Ma;
+    P->N = (int32_t)pl.Mb;
+    P->k_blocks = pl.k_blocks;
+    P->kb_per_chunk = pl.kb_per_chunk;
+    P->kb_per_fold = pl.kb_per_fold;
+    P->n_chunks = pl.n_chunks;
+    P->tiles_m = pl.tiles_m;
+    P->tiles_n = pl.tiles_n;
+    P->unit_begin = unit_begin;
+}
+
 cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const cpi_frames* b,
                      int accumulate, int64_t* s_ab, int64_t* s_a, int64_t* s_b, double* gamma,
                      float* gamma_f32, void* ws, DeviceInfo* dev, cudaStream_t st) {
@@ -224,28 +247,17 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
         if (!make_operand_map(&tm_a, op_a, pl.bf16, pl.Ma, pl.kstride_bytes, 128) ||
             !make_operand_map(&tm_b, op_b, pl.bf16, pl.Mb, pl.kstride_bytes, pl.block_n))
             return CPI_ERR_CUDA;
-        MomentsParams p{};
-        p.partial = part;
-        p.M = (int32_t)pl.Ma;
-        p.N = (int32_t)pl.Mb;
-        p.k_blocks = pl.k_blocks;
-        p.kb_per_chunk = pl.kb_per_chunk;
-        p.kb_per_fold = pl.kb_per_fold;
-        p.n_chunks = pl.n_chunks;
-        p.tiles_m = pl.tiles_m;
-        p.tiles_n = pl.tiles_n;
-        p.n_units = pl.n_units;
-        p.status = dev->status;
-        p.timeout_ns = g_timeout_ns;
-        p.fused = 0;   // the separate fold kernel is faster: see the note in the moments kernel
-        p.s_ab = s_ab;
-        p.s_a = s_a;
-        p.s_b = s_b;
-        p.gamma = gamma;
-        p.gamma_f32 = gamma_f32;
-        p.gd = make_gamma_div(pl.n);
+        MomentsLaunch<1> L;
+        std::memset(&L, 0, sizeof(L));
+        L.map_a[0] = tm_a;
+        L.map_b[0] = tm_b;
+        fill_problem(pl, part, 0, &L.prob[0]);
+        L.n_problems = 1;
+        L.n_units = pl.n_units;
+        L.status = dev->status;
+        L.timeout_ns = g_timeout_ns;
         const int grid = pl.n_units < dev->sm_count ? pl.n_units : dev->sm_count;
-        return cuda_status(launch_moments(pl.bf16, tm_a, tm_b, p, grid, st));
+        return cuda_status(launch_moments(pl.bf16, L, grid, st));
     }
     if (stage == CPI_STAGE_FOLD) {
         return cuda_status(launch_fold(part, pl.n_chunks, pl.Ma, pl.Mb, s_ab, accumulate, 1, s_a,
@@ -274,6 +286,285 @@ cpi_status correlate_common(const int32_t* stages, int n_stages, const cpi_frame
                       st);
         if (s != CPI_OK) return s;
     }
+    return CPI_OK;
+}
+
+size_t refocus_ws_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb, int32_t n_planes, int sm) {
+    if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || n_planes < 1) return 0;
+    const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
+    const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, sm);
+    return round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(float), 256);
+}
+
+cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
+                       const cpi_plane* planes, int32_t n_planes, float* out, void* workspace,
+                       size_t workspace_bytes, cudaStream_t st) {
+    if (!gamma_f32 || !planes || !out || n_planes < 1) return CPI_ERR_INVALID_ARG;
+    if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || wa > 512) return CPI_ERR_INVALID_ARG;
+    if ((int64_t)hb * wb > kMaxPixels) return CPI_ERR_INVALID_ARG;
+    if (refocus_smem_bytes(ha, wa) > 200 * 1024) return CPI_ERR_UNSUPPORTED;
+    if (!aligned(gamma_f32, 16) || !aligned(out, 4)) return CPI_ERR_INVALID_ARG;
+    for (int i = 0; i < n_planes; ++i)
+        if (!std::isfinite(planes[i].alpha) || !std::isfinite(planes[i].beta))
+            return CPI_ERR_INVALID_ARG;
+    DeviceInfo* dev = nullptr;
+    if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+    const size_t need = refocus_ws_size(ha, wa, hb, wb, n_planes, dev->sm_count);
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return CPI_ERR_WORKSPACE;
+    const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
+    const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, dev->sm_count);
+    float* partial = static_cast<float*>(workspace);
+    CUtensorMap tm;
+    const bool sep = refocus_separable(ha, wa);
+    if (sep && (int64_t)hb * wb * ha >= ((int64_t)1 << 31)) return CPI_ERR_UNSUPPORTED;
+    if (sep && !make_slice_map(&tm, gamma_f32, ha, wa, (int64_t)hb * wb)) return CPI_ERR_CUDA;
+    PlaneBlock pb;
+    for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {
+        const int np = n_planes - p0 < kRefocusMaxPlanesPerLaunch ? n_planes - p0
+                                                                  : kRefocusMaxPlanesPerLaunch;
+        std::memset(&pb, 0, sizeof(pb));
+        for (int i = 0; i < np; ++i) {
+            pb.alpha[i] = planes[p0 + i].alpha;
+            pb.beta[i] = planes[p0 + i].beta;
+        }
+        RefocusGeom g{};
+        g.ha = ha;
+        g.wa = wa;
+        g.hb = hb;
+        g.wb = wb;
+        g.n_ranges = ranges;
+        g.b_per_range = refocus_range_size(ha, wa, hb, wb, ranges);
+        g.n_planes = np;
+        g.plane_offset = p0;
+        g.total_planes = n_planes;
+        g.status = dev->status;
+        g.timeout_ns = g_timeout_ns;
+        cudaError_t e = launch_refocus(gamma_f32, sep ? &tm : nullptr, g, pb, partial, st);
+        if (e != cudaSuccess) return CPI_ERR_CUDA;
+    }
+    return cuda_status(
+        launch_refocus_reduce(partial, ranges, (int64_t)n_planes * ha * wa, out, st));
+}
+
+
+// ------------------------------------------------------------------ batches
+// A batch of independent correlations (and refocusings): every item gets its
+// own region of the workspace; the items' ingest, fold and refocus kernels are
+// launched per item, and the raw-moment units of all items of one operand kind
+// run in persistent grouped launches of up to kMaxGroup problems, larger units
+// first.  The whole sequence can be captured once into a CUDA graph and
+// replayed.
+struct BatchItemPlan {
+    CorrPlan pl;
+    size_t ws_off = 0, rws_off = 0, rws_bytes = 0;
+};
+struct BatchPlan {
+    std::vector<BatchItemPlan> it;
+    size_t ws_bytes = 0;
+};
+
+constexpr int kSplitCandidates[3] = {1, 2, 4};
+
+cpi_status check_batch_item(const cpi_batch_item& b) {
+    if (!b.s_ab || !b.s_a || !b.s_b || !aligned(b.s_ab, 16) || !aligned(b.s_a, 16) || !aligned(b.s_b, 16))
+        return CPI_ERR_INVALID_ARG;
+    if ((b.gamma && !aligned(b.gamma, 16)) || (b.gamma_f32 && !aligned(b.gamma_f32, 16)))
+        return CPI_ERR_INVALID_ARG;
+    if (b.n_planes < 0) return CPI_ERR_INVALID_ARG;
+    if (b.n_planes > 0) {
+        if (!b.planes || !b.refocus_out || !b.gamma_f32) return CPI_ERR_INVALID_ARG;
+        if (b.a.width > 512 || refocus_smem_bytes(b.a.height, b.a.width) > 200 * 1024)
+            return CPI_ERR_UNSUPPORTED;
+        for (int i = 0; i < b.n_planes; ++i)
+            if (!std::isfinite(b.planes[i].alpha) || !std::isfinite(b.planes[i].beta))
+                return CPI_ERR_INVALID_ARG;
+    }
+    return CPI_OK;
+}
+
+cpi_status make_batch_plan(const cpi_batch_item* items, int n, int sm, int split, BatchPlan* bp) {
+    if (!items || n < 1) return CPI_ERR_INVALID_ARG;
+    bp->it.assign(n, BatchItemPlan{});
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const cpi_batch_item& b = items[i];
+        cpi_status s = check_batch_item(b);
+        if (s != CPI_OK) return s;
+        BatchItemPlan& ip = bp->it[i];
+        s = make_plan(&b.a, &b.b, b.n_frames, sm, &ip.pl, split);
+        if (s != CPI_OK) return s;
+        ip.ws_off = off;
+        off = round_up(off + ip.pl.ws_bytes, 1024);
+        if (b.n_planes > 0) {
+            ip.rws_bytes = refocus_ws_size(b.a.height, b.a.width, b.b.height, b.b.width, b.n_planes, sm);
+            ip.rws_off = off;
+            off = round_up(off + ip.rws_bytes, 1024);
+        }
+    }
+    bp->ws_bytes = off;
+    return CPI_OK;
+}
+
+// Grouped raw-moment launches of the batch: one operand kind at a time, items
+// ordered by decreasing units (K blocks per unit, then unit count).
+cpi_status launch_batch_moments(const cpi_batch_item* items, const BatchPlan& bp, uint8_t* ws,
+                                DeviceInfo* dev, cudaStream_t st) {
+    std::unique_ptr<MomentsLaunch<kMaxGroup>> L(new MomentsLaunch<kMaxGroup>);
+    for (int kind = 0; kind < 2; ++kind) {
+        std::vector<int> idx;
+        for (int i = 0; i < (int)bp.it.size(); ++i)
+            if ((int)bp.it[i].pl.bf16 == kind) idx.push_back(i);
+        std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+            const CorrPlan &p = bp.it[x].pl, &q = bp.it[y].pl;
+            if (p.kb_per_chunk != q.kb_per_chunk) return p.kb_per_chunk > q.kb_per_chunk;
+            return p.n_units > q.n_units;
+        });
+        for (size_t g0 = 0; g0 < idx.size(); g0 += kMaxGroup) {
+            std::memset(L.get(), 0, sizeof(*L));
+            int units = 0, np = 0;
+            for (size_t g = g0; g < idx.size() && g < g0 + kMaxGroup; ++g, ++np) {
+                const BatchItemPlan& ip = bp.it[idx[g]];
+                uint8_t* w = ws + ip.ws_off;
+                if (!make_operand_map(&L->map_a[np], w + ip.pl.off_a, ip.pl.bf16, ip.pl.Ma,
+                                      ip.pl.kstride_bytes, 128) ||
+                    !make_operand_map(&L->map_b[np], w + ip.pl.off_b, ip.pl.bf16, ip.pl.Mb,
+                                      ip.pl.kstride_bytes, ip.pl.block_n))
+                    return CPI_ERR_CUDA;
+                fill_problem(ip.pl, reinterpret_cast<int32_t*>(w + ip.pl.off_part), units, &L->prob[np]);
+                if ((int64_t)units + ip.pl.n_units > 0x7fffffff) return CPI_ERR_UNSUPPORTED;
+                units += ip.pl.n_units;
+            }
+            L->n_problems = np;
+            L->n_units = units;
+            L->status = dev->status;
+            L->timeout_ns = g_timeout_ns;
+            const int grid = units < dev->sm_count ? units : dev->sm_count;
+            if (launch_moments_group(kind == 1, *L, grid, st) != cudaSuccess) return CPI_ERR_CUDA;
+        }
+    }
+    (void)items;
+    return CPI_OK;
+}
+
+cpi_status run_batch(const cpi_batch_item* items, const BatchPlan& bp, uint8_t* ws, DeviceInfo* dev,
+                     cudaStream_t st) {
+    const int n = (int)bp.it.size();
+    for (int i = 0; i < n; ++i) {
+        const cpi_batch_item& b = items[i];
+        cpi_status s = run_stage(CPI_STAGE_INGEST, bp.it[i].pl, &b.a, &b.b, 0, b.s_ab, b.s_a, b.s_b,
+                                 b.gamma, b.gamma_f32, ws + bp.it[i].ws_off, dev, st);
+        if (s != CPI_OK) return s;
+    }
+    cpi_status s = launch_batch_moments(items, bp, ws, dev, st);
+    if (s != CPI_OK) return s;
+    for (int i = 0; i < n; ++i) {
+        const cpi_batch_item& b = items[i];
+        s = run_stage(CPI_STAGE_FOLD, bp.it[i].pl, &b.a, &b.b, 0, b.s_ab, b.s_a, b.s_b, b.gamma,
+                      b.gamma_f32, ws + bp.it[i].ws_off, dev, st);
+        if (s != CPI_OK) return s;
+    }
+    for (int i = 0; i < n; ++i) {
+        const cpi_batch_item& b = items[i];
+        if (b.n_planes == 0) continue;
+        s = run_refocus(b.gamma_f32, b.a.height, b.a.width, b.b.height, b.b.width, b.planes, b.n_planes,
+                        b.refocus_out, ws + bp.it[i].rws_off, bp.it[i].rws_bytes, st);
+        if (s != CPI_OK) return s;
+    }
+    return CPI_OK;
+}
+
+uint64_t fnv(uint64_t h, const void* p, size_t n) {
+    const unsigned char* c = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ c[i]) * 1099511628211ull;
+    return h;
+}
+
+// Shape of a batch (what the chunk-split tuning depends on).
+uint64_t batch_shape_key(const cpi_batch_item* items, int n, int dev) {
+    uint64_t h = fnv(1469598103934665603ull, &n, sizeof(n));
+    h = fnv(h, &dev, sizeof(dev));
+    for (int i = 0; i < n; ++i) {
+        const cpi_batch_item& b = items[i];
+        const int64_t f[] = {b.a.bits, b.a.height, b.a.width, b.b.bits, b.b.height, b.b.width, b.n_frames,
+                             b.n_planes};
+        h = fnv(h, f, sizeof(f));
+    }
+    return h;
+}
+
+// Everything a captured graph bakes in: shapes, pointers, plane coefficients,
+// workspace and the chosen split.
+uint64_t batch_graph_key(const cpi_batch_item* items, int n, const void* ws, int split, int dev) {
+    uint64_t h = fnv(1469598103934665603ull, &n, sizeof(n));
+    h = fnv(h, &ws, sizeof(ws));
+    h = fnv(h, &split, sizeof(split));
+    h = fnv(h, &dev, sizeof(dev));
+    h = fnv(h, &g_timeout_ns, sizeof(g_timeout_ns));
+    for (int i = 0; i < n; ++i) {
+        h = fnv(h, &items[i], sizeof(cpi_batch_item));
+        if (items[i].n_planes > 0) h = fnv(h, items[i].planes, sizeof(cpi_plane) * items[i].n_planes);
+    }
+    return h;
+}
+
+struct BatchCache {
+    std::mutex mu;
+    std::unordered_map<uint64_t, int> split;              // shape key -> tuned split
+    std::vector<std::pair<uint64_t, cudaGraphExec_t>> graphs[kMaxDevices];
+    cudaStream_t capture_stream[kMaxDevices] = {};
+};
+BatchCache g_batch;
+constexpr size_t kMaxGraphs = 16;
+
+// Chunk split of the grouped raw-moment launches, tuned on first use of a batch
+// shape by timing the candidates (the launches run on whatever the workspace
+// holds; only their duration is used).
+cpi_status tuned_split(const cpi_batch_item* items, int n, uint8_t* ws, DeviceInfo* dev, int dev_id,
+                       cudaStream_t st, int* split_out) {
+    const uint64_t key = batch_shape_key(items, n, dev_id);
+    {
+        std::lock_guard<std::mutex> lk(g_batch.mu);
+        auto it = g_batch.split.find(key);
+        if (it != g_batch.split.end()) {
+            *split_out = it->second;
+            return CPI_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return CPI_ERR_CUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return CPI_ERR_CUDA;
+    }
+    float best = 1e30f;
+    int best_split = 1;
+    cpi_status s = CPI_OK;
+    for (int c = 0; c < 3 && s == CPI_OK; ++c) {
+        BatchPlan bp;
+        s = make_batch_plan(items, n, dev->sm_count, kSplitCandidates[c], &bp);
+        if (s != CPI_OK) break;
+        s = launch_batch_moments(items, bp, ws, dev, st);                 // warm-up
+        if (s != CPI_OK) break;
+        if (cudaEventRecord(e0, st) != cudaSuccess) { s = CPI_ERR_CUDA; break; }
+        for (int r = 0; r < 2 && s == CPI_OK; ++r) s = launch_batch_moments(items, bp, ws, dev, st);
+        if (s != CPI_OK) break;
+        if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            s = CPI_ERR_CUDA;
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_split = kSplitCandidates[c];
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != CPI_OK) return s;
+    std::lock_guard<std::mutex> lk(g_batch.mu);
+    g_batch.split[key] = best_split;
+    *split_out = best_split;
     return CPI_OK;
 }
 
@@ -351,64 +642,87 @@ cpi_status cpi_correlate_finalize(const int64_t* s_ab, const int64_t* s_a, const
 
 size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb,
                                   int32_t n_planes) {
-    if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || n_planes < 1) return 0;
     DeviceInfo* dev = nullptr;
     int sm = 152;
     if (device_info(&dev) == cudaSuccess) sm = dev->sm_count;
-    const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
-    const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, sm);
-    return round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(float), 256);
+    return refocus_ws_size(ha, wa, hb, wb, n_planes, sm);
 }
 
 cpi_status cpi_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
                        const cpi_plane* planes, int32_t n_planes, float* out, void* workspace,
                        size_t workspace_bytes, cpi_stream stream) {
-    if (!gamma_f32 || !planes || !out || n_planes < 1) return CPI_ERR_INVALID_ARG;
-    if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || wa > 512) return CPI_ERR_INVALID_ARG;
-    if ((int64_t)hb * wb > kMaxPixels) return CPI_ERR_INVALID_ARG;
-    if (refocus_smem_bytes(ha, wa) > 200 * 1024) return CPI_ERR_UNSUPPORTED;
-    if (!aligned(gamma_f32, 16) || !aligned(out, 4)) return CPI_ERR_INVALID_ARG;
-    for (int i = 0; i < n_planes; ++i)
-        if (!std::isfinite(planes[i].alpha) || !std::isfinite(planes[i].beta))
-            return CPI_ERR_INVALID_ARG;
+    return run_refocus(gamma_f32, ha, wa, hb, wb, planes, n_planes, out, workspace, workspace_bytes,
+                       reinterpret_cast<cudaStream_t>(stream));
+}
+
+size_t cpi_batch_workspace_size(const cpi_batch_item* items, int32_t n_items) {
+    DeviceInfo* dev = nullptr;
+    int sm = 152;
+    if (device_info(&dev) == cudaSuccess) sm = dev->sm_count;
+    size_t most = 0;
+    for (int c = 0; c < 3; ++c) {
+        BatchPlan bp;
+        if (make_batch_plan(items, n_items, sm, kSplitCandidates[c], &bp) != CPI_OK) return 0;
+        most = bp.ws_bytes > most ? bp.ws_bytes : most;
+    }
+    return most;
+}
+
+cpi_status cpi_batch_correlate(const cpi_batch_item* items, int32_t n_items, void* workspace,
+                               size_t workspace_bytes, int32_t flags, cpi_stream stream) {
     DeviceInfo* dev = nullptr;
     if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
-    const size_t need = cpi_refocus_workspace_size(ha, wa, hb, wb, n_planes);
-    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return CPI_ERR_WORKSPACE;
+    int dev_id = 0;
+    if (cudaGetDevice(&dev_id) != cudaSuccess) return CPI_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
-    const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, dev->sm_count);
-    float* partial = static_cast<float*>(workspace);
-    CUtensorMap tm;
-    const bool sep = refocus_separable(ha, wa);
-    if (sep && (int64_t)hb * wb * ha >= ((int64_t)1 << 31)) return CPI_ERR_UNSUPPORTED;
-    if (sep && !make_slice_map(&tm, gamma_f32, ha, wa, (int64_t)hb * wb)) return CPI_ERR_CUDA;
-    PlaneBlock pb;
-    for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {
-        const int np = n_planes - p0 < kRefocusMaxPlanesPerLaunch ? n_planes - p0
-                                                                  : kRefocusMaxPlanesPerLaunch;
-        std::memset(&pb, 0, sizeof(pb));
-        for (int i = 0; i < np; ++i) {
-            pb.alpha[i] = planes[p0 + i].alpha;
-            pb.beta[i] = planes[p0 + i].beta;
-        }
-        RefocusGeom g{};
-        g.ha = ha;
-        g.wa = wa;
-        g.hb = hb;
-        g.wb = wb;
-        g.n_ranges = ranges;
-        g.b_per_range = refocus_range_size(ha, wa, hb, wb, ranges);
-        g.n_planes = np;
-        g.plane_offset = p0;
-        g.total_planes = n_planes;
-        g.status = dev->status;
-        g.timeout_ns = g_timeout_ns;
-        cudaError_t e = launch_refocus(gamma_f32, sep ? &tm : nullptr, g, pb, partial, st);
-        if (e != cudaSuccess) return CPI_ERR_CUDA;
+    BatchPlan probe;
+    cpi_status s = make_batch_plan(items, n_items, dev->sm_count, 1, &probe);   // validates the items
+    if (s != CPI_OK) return s;
+    if (!workspace || !aligned(workspace, 256) || workspace_bytes < cpi_batch_workspace_size(items, n_items))
+        return CPI_ERR_WORKSPACE;
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    int split = 1;
+    if (flags & CPI_BATCH_TUNE) {
+        s = tuned_split(items, n_items, ws, dev, dev_id, st, &split);
+        if (s != CPI_OK) return s;
     }
-    return cuda_status(
-        launch_refocus_reduce(partial, ranges, (int64_t)n_planes * ha * wa, out, st));
+    BatchPlan bp;
+    s = make_batch_plan(items, n_items, dev->sm_count, split, &bp);
+    if (s != CPI_OK) return s;
+    if (!(flags & CPI_BATCH_GRAPH)) return run_batch(items, bp, ws, dev, st);
+
+    const uint64_t key = batch_graph_key(items, n_items, workspace, split, dev_id);
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_batch.mu);
+        for (auto& g : g_batch.graphs[dev_id])
+            if (g.first == key) exec = g.second;
+        if (exec == nullptr && g_batch.capture_stream[dev_id] == nullptr &&
+            cudaStreamCreateWithFlags(&g_batch.capture_stream[dev_id], cudaStreamNonBlocking) != cudaSuccess)
+            return CPI_ERR_CUDA;
+    }
+    if (exec == nullptr) {
+        cudaStream_t cap = g_batch.capture_stream[dev_id];
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CPI_ERR_CUDA;
+        s = run_batch(items, bp, ws, dev, cap);
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ee = cudaStreamEndCapture(cap, &graph);
+        if (s != CPI_OK || ee != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return s != CPI_OK ? s : CPI_ERR_CUDA;
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ei != cudaSuccess) return CPI_ERR_CUDA;
+        std::lock_guard<std::mutex> lk(g_batch.mu);
+        auto& v = g_batch.graphs[dev_id];
+        if (v.size() >= kMaxGraphs) {
+            cudaGraphExecDestroy(v.front().second);
+            v.erase(v.begin());
+        }
+        v.emplace_back(key, exec);
+    }
+    return cudaGraphLaunch(exec, st) == cudaSuccess ? CPI_OK : CPI_ERR_CUDA;
 }
 
 cpi_status cpi_denoise(const void* model, const float* gamma_in, float* gamma_out, int32_t ha,

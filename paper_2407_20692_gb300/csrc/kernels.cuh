@@ -33,24 +33,30 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
                           int64_t* s_b, cudaStream_t st);
 
 // ------------------------------------------------------------------ moments
-struct MomentsParams {
-    int32_t* partial;        // [n_chunks][M][N] exact partial sums
+// One raw-moment problem: S_ab of one (A, B) pair, split into work units of
+// (frame chunk, 128 x BLOCK_N output tile).
+struct MomentsProblem {
+    int32_t* partial;        // [n_chunks][M][N] exact int32 partial sums
     int32_t M, N;            // A pixels (rows), B pixels (columns)
     int32_t k_blocks;        // K blocks of 128 bytes per operand row
     int32_t kb_per_chunk;    // K blocks per frame chunk (one partial slot each)
     int32_t kb_per_fold;     // K blocks per exact FP32 segment (BF16 path)
-    int32_t n_chunks, tiles_m, tiles_n, n_units;
+    int32_t n_chunks, tiles_m, tiles_n;
+    int32_t unit_begin;      // first unit of this problem in the launch
+};
+
+// A persistent launch over the units of up to K problems (K = 1 for a single
+// correlation, kMaxGroup for a batch).  Passed as a __grid_constant__ kernel
+// parameter, so the TMA descriptors live in parameter space.
+constexpr int kMaxGroup = 64;
+template <int K>
+struct MomentsLaunch {
+    CUtensorMap map_a[K];
+    CUtensorMap map_b[K];
+    MomentsProblem prob[K];
+    int32_t n_problems, n_units;
     unsigned int* status;
     unsigned long long timeout_ns;
-    // Fused fold (single frame chunk, no accumulation): the epilogue writes
-    // S_ab, Gamma and the slice-major FP32 copy directly; partial is unused.
-    int32_t fused;
-    int64_t* s_ab;
-    const int64_t* s_a;
-    const int64_t* s_b;
-    double* gamma;
-    float* gamma_f32;
-    GammaDiv gd;
 };
 
 struct MomentsShape {
@@ -61,8 +67,9 @@ struct MomentsShape {
 };
 MomentsShape moments_shape(bool bf16);
 
-cudaError_t launch_moments(bool bf16, const CUtensorMap& tm_a, const CUtensorMap& tm_b,
-                           const MomentsParams& p, int grid, cudaStream_t st);
+cudaError_t launch_moments(bool bf16, const MomentsLaunch<1>& L, int grid, cudaStream_t st);
+cudaError_t launch_moments_group(bool bf16, const MomentsLaunch<kMaxGroup>& L, int grid,
+                                 cudaStream_t st);
 
 // ------------------------------------------------------------------ fold / finalize
 cudaError_t launch_fold(const int32_t* partial, int n_chunks, int64_t M, int64_t N,

@@ -12,10 +12,13 @@
 //     folded into exact int32 registers every 256 frames
 //     (256 * 65025 = 16,646,400 < 2^24); a chunk of <= 32768 frames keeps the
 //     int32 total below 2^31.
-// Each (frame chunk, 128 x BLOCK_N output tile) is one work unit; its exact
-// int32 partial sum goes to its own slot of the workspace, and the fold step
-// adds the slots into int64.  Integer addition is associative, so the split
-// over chunks and CTAs never changes the result.
+// Each (frame chunk, 128 x BLOCK_N output tile) of a problem is one work unit;
+// its exact int32 partial sum goes to its own slot of the workspace, and the
+// fold step adds the slots into int64.  Integer addition is associative, so the
+// split over chunks and CTAs never changes the result.  One launch serves one
+// problem (a correlation) or up to kMaxGroup problems of uneven shapes (a
+// batch): the persistent CTAs walk one list of units, each unit naming its
+// problem by a binary search over the problems' first units.
 //
 // Persistent, warp-specialised CTA (one per SM, 192 threads):
 //   warp 0  : TMA producer (128-byte swizzled tiles, STAGES-deep ring)
@@ -24,7 +27,6 @@
 // Two TMEM accumulators let the epilogue of one segment overlap the MMAs of the
 // next.  Every barrier wait is bounded; on a time-out the CTA records the error,
 // drains its own copies and MMAs, frees its tensor memory and returns.
-#include "gamma_div.cuh"
 #include "kernels.cuh"
 #include "ptx.cuh"
 
@@ -49,50 +51,59 @@ struct MomentsCfg {
     static constexpr size_t kSmem = 1024 + (size_t)kStages * (kABytes + kBBytes) + 256;
 };
 
-// Write 32 exact sums of output row m, columns nb .. nb+31 (those < N): either
-// to the chunk's int32 partial slot, or -- when the whole frame range is one
-// chunk and nothing is accumulated -- straight to S_ab, Gamma (row-major) and
-// the slice-major FP32 copy (the fused fold of Eq. (1)).  Measured on GB300 the
-// fused form is slower for one tile per CTA: each lane owns a row, so the
-// row-major stores touch 32 lines per instruction and nothing overlaps them;
-// the host keeps it off (MomentsParams::fused = 0) and runs the fold kernel.
-__device__ __forceinline__ void store_row_chunk(const MomentsParams& p, int chunk, int m, int nb,
+// Write 32 exact sums of output row m, columns nb .. nb+31 (those < N), to the
+// chunk's int32 partial slot.  (Folding Gamma straight from here was measured
+// slower on GB300 for one tile per CTA: each lane owns a row, so row-major
+// Gamma stores touch 32 lines per instruction and nothing overlaps them.)
+__device__ __forceinline__ void store_row_chunk(const MomentsProblem& P, int chunk, int m, int nb,
                                                 const int32_t (&v)[32]) {
-    if (m >= p.M) return;
-    if (!p.fused) {
-        int32_t* out = p.partial + ((size_t)chunk * p.M + (size_t)m) * p.N;
-        if ((p.N & 3) == 0 && nb + 32 <= p.N) {
-            int4* o4 = reinterpret_cast<int4*>(out + nb);
+    if (m >= P.M) return;
+    int32_t* out = P.partial + ((size_t)chunk * P.M + (size_t)m) * P.N;
+    if ((P.N & 3) == 0 && nb + 32 <= P.N) {
+        int4* o4 = reinterpret_cast<int4*>(out + nb);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) o4[j] = make_int4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
-        } else {
+        for (int j = 0; j < 8; ++j) o4[j] = make_int4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+    } else {
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (nb + j < p.N) out[nb + j] = v[j];
-        }
-        return;
-    }
-    const int64_t sa = __ldg(p.s_a + m);
-    const size_t rowoff = (size_t)m * p.N;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const int n = nb + j;
-        if (n < p.N) {
-            const int64_t S = v[j];
-            p.s_ab[rowoff + n] = S;
-            if (p.gamma != nullptr || p.gamma_f32 != nullptr) {
-                const double g = gamma_from_num(p.gd.n * S - sa * __ldg(p.s_b + n), p.gd);
-                if (p.gamma) p.gamma[rowoff + n] = g;
-                if (p.gamma_f32) p.gamma_f32[(size_t)n * p.M + m] = double_to_float_rn(g);
-            }
-        }
+        for (int j = 0; j < 32; ++j)
+            if (nb + j < P.N) out[nb + j] = v[j];
     }
 }
 
-template <bool kBf16>
+struct Unit {
+    int prob, chunk, tm, tn, kb0, kb1;
+};
+
+// Unit u of the launch: its problem (binary search over first units), frame
+// chunk, output tile and K-block range.
+template <int K>
+__device__ __forceinline__ Unit decode_unit(const MomentsLaunch<K>& L, int u) {
+    int lo = 0;
+    if constexpr (K > 1) {
+        int hi = L.n_problems - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (L.prob[mid].unit_begin <= u) lo = mid;
+            else hi = mid - 1;
+        }
+    }
+    const MomentsProblem& P = L.prob[lo];
+    const int local = u - P.unit_begin;
+    const int per_chunk = P.tiles_m * P.tiles_n;
+    Unit w;
+    w.prob = lo;
+    w.chunk = local / per_chunk;
+    const int t = local - w.chunk * per_chunk;
+    w.tm = t / P.tiles_n;
+    w.tn = t - w.tm * P.tiles_n;
+    w.kb0 = w.chunk * P.kb_per_chunk;
+    w.kb1 = min(w.kb0 + P.kb_per_chunk, P.k_blocks);
+    return w;
+}
+
+template <bool kBf16, int K>
 __global__ void __launch_bounds__(kThreads, 1)
-    moments_kernel(const __grid_constant__ CUtensorMap tm_a, const __grid_constant__ CUtensorMap tm_b,
-                   const MomentsParams p) {
+    moments_kernel(const __grid_constant__ MomentsLaunch<K> L) {
     using C = MomentsCfg<kBf16>;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -108,7 +119,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint64_t tmo = p.timeout_ns;
+    const uint64_t tmo = L.timeout_ns;
+    unsigned int* const status = L.status;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < C::kStages; ++s) {
@@ -123,8 +135,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         *abort_flag = 0;
         fence_barrier_init();
         fence_proxy_async_smem();
-        tma_prefetch_desc(&tm_a);
-        tma_prefetch_desc(&tm_b);
+        if constexpr (K == 1) {
+            tma_prefetch_desc(&L.map_a[0]);
+            tma_prefetch_desc(&L.map_b[0]);
+        }
     }
     if (warp == 1) {
         tmem_alloc(tmem_slot, C::kTmemCols);
@@ -134,7 +148,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
-    const int units_per_chunk = p.tiles_m * p.tiles_n;
 
     if (warp == 0) {
         if (lane == 0) {
@@ -143,22 +156,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t phase = 0;
             uint32_t issued_mask = 0, issued_phase = 0;   // per stage: loaded at least once / parity
             bool ok = true;
-            for (int u = blockIdx.x; ok && u < p.n_units; u += gridDim.x) {
-                const int chunk = u / units_per_chunk;
-                const int t = u - chunk * units_per_chunk;
-                const int tm = t / p.tiles_n, tn = t - tm * p.tiles_n;
-                const int kb0 = chunk * p.kb_per_chunk;
-                const int kb1 = min(kb0 + p.kb_per_chunk, p.k_blocks);
-                for (int kb = kb0; kb < kb1; ++kb) {
-                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1, abort_flag, p.status, tmo)) {
+            for (int u = blockIdx.x; ok && u < L.n_units; u += gridDim.x) {
+                const Unit w = decode_unit(L, u);
+                const CUtensorMap* ma = &L.map_a[w.prob];
+                const CUtensorMap* mb = &L.map_b[w.prob];
+                for (int kb = w.kb0; kb < w.kb1; ++kb) {
+                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1, abort_flag, status, tmo)) {
                         ok = false;
                         break;
                     }
                     mbar_arrive_expect_tx(&full[stage], C::kABytes + C::kBBytes);
-                    tma_load_2d(sA + stage * C::kABytes, &tm_a, &full[stage], kb * C::kKPerBlock,
-                                tm * kBlockM);
-                    tma_load_2d(sB + stage * C::kBBytes, &tm_b, &full[stage], kb * C::kKPerBlock,
-                                tn * C::kBlockN);
+                    tma_load_2d(sA + stage * C::kABytes, ma, &full[stage], kb * C::kKPerBlock,
+                                w.tm * kBlockM);
+                    tma_load_2d(sB + stage * C::kBBytes, mb, &full[stage], kb * C::kKPerBlock,
+                                w.tn * C::kBlockN);
                     issued_mask |= 1u << stage;
                     issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
                     if (++stage == C::kStages) {
@@ -184,23 +195,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             int acc = 0;
             uint32_t acc_phase = 0;
             bool ok = true, issued_any = false;
-            for (int u = blockIdx.x; ok && u < p.n_units; u += gridDim.x) {
-                const int chunk = u / units_per_chunk;
-                const int kb0 = chunk * p.kb_per_chunk;
-                const int kb1 = min(kb0 + p.kb_per_chunk, p.k_blocks);
+            for (int u = blockIdx.x; ok && u < L.n_units; u += gridDim.x) {
+                const Unit w = decode_unit(L, u);
+                const int kb_per_fold = L.prob[w.prob].kb_per_fold;
+                const int kb0 = w.kb0, kb1 = w.kb1;
                 for (int kb = kb0; kb < kb1; ++kb) {
                     const int local = kb - kb0;
-                    const bool seg_start = kBf16 ? (local % p.kb_per_fold == 0) : (local == 0);
+                    const bool seg_start = kBf16 ? (local % kb_per_fold == 0) : (local == 0);
                     const bool seg_end =
-                        kBf16 ? ((local + 1) % p.kb_per_fold == 0 || kb + 1 == kb1) : (kb + 1 == kb1);
+                        kBf16 ? ((local + 1) % kb_per_fold == 0 || kb + 1 == kb1) : (kb + 1 == kb1);
                     if (seg_start) {
-                        if (!mbar_wait_bounded(&tempty[acc], acc_phase ^ 1, abort_flag, p.status, tmo)) {
+                        if (!mbar_wait_bounded(&tempty[acc], acc_phase ^ 1, abort_flag, status, tmo)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                     }
-                    if (!mbar_wait_bounded(&full[stage], phase, abort_flag, p.status, tmo)) {
+                    if (!mbar_wait_bounded(&full[stage], phase, abort_flag, status, tmo)) {
                         ok = false;
                         break;
                     }
@@ -244,17 +255,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         int acc = 0;
         uint32_t acc_phase = 0;
         bool ok = true;
-        for (int u = blockIdx.x; ok && u < p.n_units; u += gridDim.x) {
-            const int chunk = u / units_per_chunk;
-            const int t = u - chunk * units_per_chunk;
-            const int tm = t / p.tiles_n, tn = t - tm * p.tiles_n;
-            const int kb0 = chunk * p.kb_per_chunk;
-            const int kb1 = min(kb0 + p.kb_per_chunk, p.k_blocks);
-            const int m = tm * kBlockM + row;
-            const int n0 = tn * C::kBlockN + half * kHalf;
+        for (int u = blockIdx.x; ok && u < L.n_units; u += gridDim.x) {
+            const Unit w = decode_unit(L, u);
+            const MomentsProblem& P = L.prob[w.prob];
+            const int chunk = w.chunk;
+            const int kb0 = w.kb0, kb1 = w.kb1;
+            const int m = w.tm * kBlockM + row;
+            const int n0 = w.tn * C::kBlockN + half * kHalf;
             const uint32_t col0 = (uint32_t)(half * kHalf);
             if constexpr (!kBf16) {
-                if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, p.status, tmo)) {
+                if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, status, tmo)) {
                     ok = false;
                     break;
                 }
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     int32_t v[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = __float2int_rn(__uint_as_float(r[j]));
-                    store_row_chunk(p, chunk, m, n0 + c * 32, v);
+                    store_row_chunk(P, chunk, m, n0 + c * 32, v);
                 }
                 tc_fence_before();
                 mbar_arrive(&tempty[acc]);
@@ -277,9 +287,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int32_t sum[kHalf];
 #pragma unroll
                 for (int j = 0; j < kHalf; ++j) sum[j] = 0;
-                const int nseg = (kb1 - kb0 + p.kb_per_fold - 1) / p.kb_per_fold;
+                const int nseg = (kb1 - kb0 + P.kb_per_fold - 1) / P.kb_per_fold;
                 for (int sgm = 0; sgm < nseg; ++sgm) {
-                    if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, p.status, tmo)) {
+                    if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, status, tmo)) {
                         ok = false;
                         break;
                     }
@@ -304,7 +314,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     int32_t v[32];
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = sum[c * 32 + j];
-                    store_row_chunk(p, chunk, m, n0 + c * 32, v);
+                    store_row_chunk(P, chunk, m, n0 + c * 32, v);
                 }
             }
         }
@@ -328,32 +338,32 @@ MomentsShape moments_shape(bool bf16) {
             MomentsCfg<false>::kSmem};
 }
 
-cudaError_t launch_moments(bool bf16, const CUtensorMap& tm_a, const CUtensorMap& tm_b,
-                           const MomentsParams& p, int grid, cudaStream_t st) {
+template <bool kBf16, int K>
+static cudaError_t launch_impl(const MomentsLaunch<K>& L, int grid, cudaStream_t st) {
     // The shared-memory opt-in is a per-device function attribute: set it once per device.
-    static bool attr_set[2][64] = {};
+    static bool attr_set[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    if (bf16) {
-        if (!attr_set[1][dev]) {
-            e = cudaFuncSetAttribute(moments_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)MomentsCfg<true>::kSmem);
-            if (e != cudaSuccess) return e;
-            attr_set[1][dev] = true;
-        }
-        moments_kernel<true><<<grid, kThreads, MomentsCfg<true>::kSmem, st>>>(tm_a, tm_b, p);
-    } else {
-        if (!attr_set[0][dev]) {
-            e = cudaFuncSetAttribute(moments_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)MomentsCfg<false>::kSmem);
-            if (e != cudaSuccess) return e;
-            attr_set[0][dev] = true;
-        }
-        moments_kernel<false><<<grid, kThreads, MomentsCfg<false>::kSmem, st>>>(tm_a, tm_b, p);
+    using C = MomentsCfg<kBf16>;
+    if (!attr_set[dev]) {
+        e = cudaFuncSetAttribute(moments_kernel<kBf16, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::kSmem);
+        if (e != cudaSuccess) return e;
+        attr_set[dev] = true;
     }
+    moments_kernel<kBf16, K><<<grid, kThreads, C::kSmem, st>>>(L);
     return cudaGetLastError();
+}
+
+cudaError_t launch_moments(bool bf16, const MomentsLaunch<1>& L, int grid, cudaStream_t st) {
+    return bf16 ? launch_impl<true, 1>(L, grid, st) : launch_impl<false, 1>(L, grid, st);
+}
+
+cudaError_t launch_moments_group(bool bf16, const MomentsLaunch<kMaxGroup>& L, int grid,
+                                 cudaStream_t st) {
+    return bf16 ? launch_impl<true, kMaxGroup>(L, grid, st) : launch_impl<false, kMaxGroup>(L, grid, st);
 }
 
 }  // namespace cpi

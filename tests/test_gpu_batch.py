@@ -1,0 +1,107 @@
+"""Batches: many uneven acquisitions (binary and counts) in grouped persistent
+launches replayed from a CUDA graph must give, item by item, exactly what the
+single-acquisition entry points give (which the other GPU tests pin to the
+oracle), on the first call and on replays after the inputs change."""
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2407_20692_gb300 as cpi
+import synth
+from gpu_util import assert_exact, desc, oracle_correlate
+
+pytestmark = pytest.mark.gpu
+
+SPECS = [(40, 20, 3000, "poisson8", 1.5), (33, 17, 1500, "poisson8", 3.0), (64, 32, 5000, "bernoulli", 0.3),
+         (24, 12, 800, "bernoulli", 0.3), (96, 48, 2500, "poisson8", 1.0), (50, 30, 4100, "poisson8", 2.0),
+         (32, 16, 700, "bernoulli", 0.5)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ready(cuda_ready, oracle_mod):
+    yield
+
+
+def _make(seed_base):
+    items, keep = [], []
+    for k, (sa, sb, n, counts, mu) in enumerate(SPECS):
+        acq = synth.Acquisition(sa, sb, n, mu, counts, seed=seed_base + k)
+        A, B = synth.generate(acq, "cuda")
+        fr, lay = synth.pack_side_by_side(A, B, acq.bits)
+        ma, mb = sa * sa, sb * sb
+        alpha, beta = synth.uniform_planes(6)
+        e = dict(a=desc(fr, lay["a"]), b=desc(fr, lay["b"]), n_frames=n,
+                 s_ab=torch.empty((ma, mb), dtype=torch.int64, device="cuda"),
+                 s_a=torch.empty(ma, dtype=torch.int64, device="cuda"),
+                 s_b=torch.empty(mb, dtype=torch.int64, device="cuda"),
+                 gamma=torch.empty((ma, mb), dtype=torch.float64, device="cuda"),
+                 gamma_f32=torch.empty((mb, ma), dtype=torch.float32, device="cuda"),
+                 planes=cpi.plane_array(alpha, beta),
+                 refocus_out=torch.empty((6, sa, sa), dtype=torch.float32, device="cuda"))
+        items.append(e)
+        keep.append((fr, lay, acq))
+    return items, keep
+
+
+def _individual(e, lay):
+    a, b, n = e["a"], e["b"], e["n_frames"]
+    ws = torch.empty(cpi.cpi_correlate_workspace_size(a, b, n), dtype=torch.uint8, device="cuda")
+    out = {k: torch.empty_like(e[k]) for k in ("s_ab", "s_a", "s_b", "gamma", "gamma_f32", "refocus_out")}
+    cpi.cpi_correlate(a, b, n, out["s_ab"], out["s_a"], out["s_b"], out["gamma"], out["gamma_f32"], ws)
+    ha, wa, hb, wb = lay["a"]["height"], lay["a"]["width"], lay["b"]["height"], lay["b"]["width"]
+    rws = torch.empty(cpi.cpi_refocus_workspace_size(ha, wa, hb, wb, len(e["planes"])), dtype=torch.uint8,
+                      device="cuda")
+    cpi.cpi_refocus(out["gamma_f32"], ha, wa, hb, wb, e["planes"], out["refocus_out"], rws)
+    return out
+
+
+def _check(items, keep):
+    torch.cuda.synchronize()
+    assert cpi.cpi_device_status() == 0
+    for e, (fr, lay, acq) in zip(items, keep):
+        ref = _individual(e, lay)
+        torch.cuda.synchronize()
+        for k in ("s_ab", "s_a", "s_b", "gamma", "gamma_f32", "refocus_out"):
+            assert torch.equal(ref[k], e[k]), (acq, k)
+
+
+def test_batch_equals_individual_calls_and_replays():
+    items, keep = _make(100)
+    arr = cpi.batch_items(items)
+    ws = torch.empty(cpi.cpi_batch_workspace_size(arr), dtype=torch.uint8, device="cuda")
+    cpi.cpi_batch_correlate(arr, ws)                     # tunes, captures and replays
+    _check(items, keep)
+    # new frames in the same buffers: the cached graph must see them
+    for k, (fr, lay, acq) in enumerate(keep):
+        A, B = synth.generate(synth.frames.replace(acq, seed=acq.seed + 50), "cuda")
+        fr2, _ = synth.pack_side_by_side(A, B, acq.bits)
+        fr.copy_(fr2)
+    cpi.cpi_batch_correlate(arr, ws)
+    _check(items, keep)
+    # without the graph and the tuner
+    for e in items:
+        e["s_ab"].zero_()
+    cpi.cpi_batch_correlate(arr, ws, flags=0)
+    _check(items, keep)
+
+
+def test_batch_item_against_oracle():
+    items, keep = _make(300)
+    arr = cpi.batch_items(items)
+    ws = torch.empty(cpi.cpi_batch_workspace_size(arr), dtype=torch.uint8, device="cuda")
+    cpi.cpi_batch_correlate(arr, ws)
+    torch.cuda.synchronize()
+    for e, (fr, lay, acq) in list(zip(items, keep))[:3]:
+        want = oracle_correlate(fr.cpu().numpy(), lay["a"], lay["b"], acq.n_frames)
+        got = {k: e[k].cpu() for k in ("s_ab", "s_a", "s_b", "gamma")}
+        assert_exact(got, want)
+
+
+def test_batch_rejects_bad_items():
+    items, keep = _make(500)
+    items[2]["s_ab"] = None
+    arr = cpi.batch_items(items)
+    with pytest.raises(cpi.CpiError) as e:
+        cpi.cpi_batch_correlate(arr, torch.empty(1024, dtype=torch.uint8, device="cuda"))
+    assert e.value.code == 1
