@@ -302,7 +302,7 @@ cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
     if (!gamma_f32 || !planes || !out || n_planes < 1) return CPI_ERR_INVALID_ARG;
     if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || wa > 512) return CPI_ERR_INVALID_ARG;
     if ((int64_t)hb * wb > kMaxPixels) return CPI_ERR_INVALID_ARG;
-    if (refocus_smem_bytes(ha, wa) > 200 * 1024) return CPI_ERR_UNSUPPORTED;
+    if (refocus_smem_bytes(ha, wa) > 220 * 1024) return CPI_ERR_UNSUPPORTED;
     if (!aligned(gamma_f32, 16) || !aligned(out, 4)) return CPI_ERR_INVALID_ARG;
     for (int i = 0; i < n_planes; ++i)
         if (!std::isfinite(planes[i].alpha) || !std::isfinite(planes[i].beta))
@@ -315,7 +315,7 @@ cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
     const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, dev->sm_count);
     float* partial = static_cast<float*>(workspace);
     CUtensorMap tm;
-    const bool sep = refocus_separable(ha, wa);
+    const bool sep = refocus_uses_tma(ha, wa);
     if (sep && (int64_t)hb * wb * ha >= ((int64_t)1 << 31)) return CPI_ERR_UNSUPPORTED;
     if (sep && !make_slice_map(&tm, gamma_f32, ha, wa, (int64_t)hb * wb)) return CPI_ERR_CUDA;
     PlaneBlock pb;
@@ -373,7 +373,7 @@ cpi_status check_batch_item(const cpi_batch_item& b) {
     if (b.n_planes < 0) return CPI_ERR_INVALID_ARG;
     if (b.n_planes > 0) {
         if (!b.planes || !b.refocus_out || !b.gamma_f32) return CPI_ERR_INVALID_ARG;
-        if (b.a.width > 512 || refocus_smem_bytes(b.a.height, b.a.width) > 200 * 1024)
+        if (b.a.width > 512 || refocus_smem_bytes(b.a.height, b.a.width) > 220 * 1024)
             return CPI_ERR_UNSUPPORTED;
         for (int i = 0; i < b.n_planes; ++i)
             if (!std::isfinite(b.planes[i].alpha) || !std::isfinite(b.planes[i].beta))

@@ -94,6 +94,7 @@ struct RefocusGeom {
 };
 size_t refocus_smem_bytes(int ha, int wa);
 bool refocus_separable(int ha, int wa);
+bool refocus_uses_tma(int ha, int wa);     // separable kernel staged by TMA (needs the tensor map)
 // Number of ranges the angular pixels are split into (one partial image each),
 // and the size of one range (angular rows for the separable kernel, angular
 // pixels for the direct one).

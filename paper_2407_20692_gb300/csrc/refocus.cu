@@ -29,6 +29,8 @@
 //
 // This file is compiled without FMA contraction: the double-float and Kahan
 // steps depend on the written rounding order; the products use explicit fmaf.
+#include <cstring>
+
 #include "kernels.cuh"
 #include "ptx.cuh"
 
@@ -114,20 +116,36 @@ __device__ __forceinline__ PlaneCoef plane_coef(const PlaneBlock& pl, int p, int
 
 // ------------------------------------------------------------ separable kernel
 // CTA = (angular row br, block of PB planes).  Thread t owns column c = t % wa
-// and rows rp + R*k (R = 512 / wa row phases).  Each slice (br, bc) is staged by
-// one 2-D TMA copy of a (wa + 8) x ha box starting at column -4: the columns
-// outside the image come back as zeros, which are exactly the out-of-grid taps.
-// Every staged slice is interpolated along x for all PB planes; after the last
-// bc the row's U images are interpolated along y and this angular row's
-// contribution to each output pixel is written to partial[br][plane][pixel].
-// The reduce kernel adds the angular rows in a fixed order (compensated FP32).
+// and rows rp + R*k (R = 512 / wa row phases).  Each slice (br, bc) is staged
+// into shared memory with 4 zero columns on both sides: by one 2-D TMA copy of
+// a (wa + 8) x ha box starting at column -4 (the columns outside the image come
+// back as zeros, exactly the out-of-grid taps), or, for widths TMA cannot
+// describe, by 4-byte cp.async copies of each thread's own pixels.  Every
+// staged slice is interpolated along x for all PB planes; after the last bc the
+// row's U images are interpolated along y and this angular row's contribution
+// to each output pixel is written to partial[br][plane][pixel].  The reduce
+// kernel adds the angular rows in a fixed order (compensated FP32).
+//
+// Variants: PB = 2 planes, <= 8 rows per thread, 2 CTAs per SM (small images);
+// PB = 1 plane, <= 32 rows per thread, 1 CTA per SM (images up to ~128 x 128).
 // kWA > 0 fixes the image width (and kHA the height) at compile time, so every
-// row offset of the inner loop is an immediate; kWA == 0 is the general form.
-template <int KR, int PB, int kWA, int kHA>
-__global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_constant__ CUtensorMap tm,
-                                                                  const RefocusGeom geo,
-                                                                  const PlaneBlock pl,
-                                                                  float* __restrict__ partial) {
+// row offset of the inner loop is an immediate.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int KR, int PB, int kWA, int kHA, bool kTma, int kStages, int kMinBlocks>
+__global__ void __launch_bounds__(kThreads, kMinBlocks) refocus_sep_kernel(const __grid_constant__ CUtensorMap tm,
+                                                                           const float* __restrict__ gamma,
+                                                                           const RefocusGeom geo,
+                                                                           const PlaneBlock pl,
+                                                                           float* __restrict__ partial) {
     extern __shared__ __align__(128) float sm_raw[];
     const int ha = kWA ? kHA : geo.ha, wa = kWA ? kWA : geo.wa, hb = geo.hb, wb = geo.wb;
     const int WS = wa + kPadL + kPadR;                 // staged slice row stride (TMA box width)
@@ -135,11 +153,11 @@ __global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_c
     // 128-byte aligned start, computed on the shared-window offset so that the
     // pointers stay shared-space (the loads below compile to shared loads)
     float* const buf0 = sm_raw + (((128u - (static_cast<uint32_t>(__cvta_generic_to_shared(sm_raw)) & 127u)) & 127u) >> 2);
-    float* const U = buf0 + kSepStages * slice_f;      // PB x (ha + 2) x wa, zero rows -1 and ha
-    Tap* const xt = reinterpret_cast<Tap*>(U + PB * (ha + 2) * wa);   // [kSepStages][PB][wa]
-    Tap* const yt = xt + kSepStages * PB * wa;                        // [PB][ha]
+    float* const U = buf0 + kStages * slice_f;         // PB x (ha + 2) x wa, zero rows -1 and ha
+    Tap* const xt = reinterpret_cast<Tap*>(U + PB * (ha + 2) * wa);   // [kStages][PB][wa]
+    Tap* const yt = xt + kStages * PB * wa;                           // [PB][ha]
     __shared__ PlaneCoef coef[PB];                     // per-plane coefficients, computed once
-    __shared__ __align__(8) uint64_t full[kSepStages]; // TMA completion of each slice buffer
+    __shared__ __align__(8) uint64_t full[kStages];    // TMA completion of each slice buffer
     __shared__ int abort_flag;
 
     const int tid = threadIdx.x;
@@ -156,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_c
     const uint32_t slice_bytes = (uint32_t)(ha * WS * sizeof(float));
 
     if (tid == 0) {
-        for (int i = 0; i < kSepStages; ++i) mbar_init(&full[i], 1);
+        for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
         abort_flag = 0;
         fence_barrier_init();
     }
@@ -166,30 +184,52 @@ __global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_c
         U[j * (ha + 2) * wa + x] = 0.0f;
         U[j * (ha + 2) * wa + (ha + 1) * wa + x] = 0.0f;
     }
-    __syncthreads();   // barriers initialised, coef visible
-    auto issue = [&](int bc) {   // one thread: slice (br, bc) -> buffer bc % kSepStages
-        const int sb = bc % kSepStages;
-        mbar_arrive_expect_tx(&full[sb], slice_bytes);
-        tma_load_2d(buf0 + sb * slice_f, &tm, &full[sb], -kPadL, (br * wb + bc) * ha);
+    if constexpr (!kTma) {   // zero columns of every buffer row (cp.async writes the interior only)
+        for (int i = tid; i < kStages * ha; i += kThreads) {
+            float* row = buf0 + (i / ha) * slice_f + (i % ha) * WS;
+#pragma unroll
+            for (int q = 0; q < kPadL; ++q) row[q] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < kPadR; ++q) row[kPadL + wa + q] = 0.0f;
+        }
+    }
+    __syncthreads();   // barriers initialised, coef and pads visible
+    auto issue = [&](int bc) {   // slice (br, bc) -> buffer bc % kStages
+        const int sb = bc % kStages;
+        if constexpr (kTma) {
+            if (tid == 0) {
+                mbar_arrive_expect_tx(&full[sb], slice_bytes);
+                tma_load_2d(buf0 + sb * slice_f, &tm, &full[sb], -kPadL, (br * wb + bc) * ha);
+            }
+        } else {
+            if (active) {
+                const float* src = gamma + ((int64_t)br * wb + bc) * Ma + (int64_t)rp * wa + c;
+                float* dst = buf0 + sb * slice_f + rp * WS + kPadL + c;
+                for (int k = 0; k < nk; ++k) cp_async4(dst + k * R * WS, src + (int64_t)k * R * wa);
+            }
+            cp_async_commit();   // one group per slice, also when this thread copied nothing
+        }
     };
     auto taps = [&](int bc) {    // x taps of slice bc for every plane
-        const int sb = bc % kSepStages;
+        const int sb = bc % kStages;
         for (int i = tid; i < np * wa; i += kThreads) {
             const int j = i / wa, x = i - j * wa;
             xt[(sb * PB + j) * wa + x] =
                 axis_tap(coef[j].alpha, (float)x - cxa, coef[j].qx, (float)bc - cxb, cxa, wa, kPadL);
         }
     };
-    // prologue: the first kSepStages - 1 slices in flight, their taps ready
-    int last_issue[kSepStages];
+    // prologue: the first kStages - 1 slices in flight, their taps ready
+    int last_issue[kStages];
 #pragma unroll
-    for (int i = 0; i < kSepStages; ++i) last_issue[i] = -1;
-    for (int bc = 0; bc < kSepStages - 1 && bc < wb; ++bc) {
-        if (tid == 0) {
+    for (int i = 0; i < kStages; ++i) last_issue[i] = -1;
+    for (int bc = 0; bc < kStages - 1; ++bc) {
+        if (bc < wb) {
             issue(bc);
-            last_issue[bc % kSepStages] = bc;
+            last_issue[bc % kStages] = bc;
+            taps(bc);
+        } else if constexpr (!kTma) {
+            cp_async_commit();   // keep one group per slot
         }
-        taps(bc);
     }
 
     // U accumulates plainly (two fused multiply-adds per slice) over pairs of
@@ -202,22 +242,27 @@ __global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_c
         for (int k = 0; k < KR; ++k) Ug[j][k] = Ua[j][k] = Uc[j][k] = 0.0f;
 
     for (int bc = 0; bc < wb; ++bc) {
-        const int sb = bc % kSepStages;
-        const uint32_t parity = (uint32_t)((bc / kSepStages) & 1);
-        // one thread waits for the copy; the others sleep in the barrier below
-        if (tid == 0 && !mbar_wait_sleepy(&full[sb], parity, geo.status, geo.timeout_ns)) abort_flag = 1;
+        const int sb = bc % kStages;
+        const uint32_t parity = (uint32_t)((bc / kStages) & 1);
+        if constexpr (kTma) {
+            // one thread waits for the copy; the others sleep in the barrier below
+            if (tid == 0 && !mbar_wait_sleepy(&full[sb], parity, geo.status, geo.timeout_ns)) abort_flag = 1;
+        } else {
+            cp_async_wait<kStages - 2>();   // this thread's copies of slice bc have landed
+        }
         __syncthreads();   // slice bc landed; every thread is done with slice bc - 1
         if (abort_flag) break;
         // refill the buffer slice bc - 1 used, and prepare its taps
-        const int nxt = bc + kSepStages - 1;
+        const int nxt = bc + kStages - 1;
         if (nxt < wb) {
-            if (tid == 0) {
-                issue(nxt);
-                last_issue[nxt % kSepStages] = nxt;
-            }
+            issue(nxt);
+            last_issue[nxt % kStages] = nxt;
             taps(nxt);
+        } else if constexpr (!kTma) {
+            cp_async_commit();
         }
-        mbar_wait_bounded(&full[sb], parity, &abort_flag, geo.status, geo.timeout_ns);   // completes at once
+        if constexpr (kTma)
+            mbar_wait_bounded(&full[sb], parity, &abort_flag, geo.status, geo.timeout_ns);   // completes at once
         if (active) {
             const float* S = buf0 + sb * slice_f + rp * WS;
             const int step = R * WS;
@@ -257,12 +302,13 @@ __global__ void __launch_bounds__(kThreads, 2) refocus_sep_kernel(const __grid_c
                 }
         }
     }
+    if constexpr (!kTma) cp_async_wait<0>();
     if (abort_flag) {
         // drain any copy still in flight before the CTA exits
-        if (tid == 0)
-            for (int i = 0; i < kSepStages; ++i)
+        if (kTma && tid == 0)
+            for (int i = 0; i < kStages; ++i)
                 if (last_issue[i] >= 0)
-                    mbar_wait_bounded(&full[i], (uint32_t)((last_issue[i] / kSepStages) & 1), nullptr,
+                    mbar_wait_bounded(&full[i], (uint32_t)((last_issue[i] / kStages) & 1), nullptr,
                                       nullptr, geo.timeout_ns);
         return;
     }
@@ -394,27 +440,29 @@ __global__ void refocus_reduce_kernel(const float* __restrict__ partial, int n_r
 
 template <typename K>
 cudaError_t set_smem_attr(K kernel, int slot) {
-    static bool done[16][64] = {};
+    static bool done[32][64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!done[slot][dev]) {
-        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (e != cudaSuccess) return e;
         done[slot][dev] = true;
     }
     return cudaSuccess;
 }
 
-template <int KR, int kWA = 0, int kHA = 0>
-cudaError_t launch_sep(const CUtensorMap& tm, const RefocusGeom& geo, const PlaneBlock& pl,
+template <int KR, int PB, bool kTma, int kStages, int kMinBlocks, int kWA = 0, int kHA = 0>
+cudaError_t launch_sep(const CUtensorMap* tm, const float* g, const RefocusGeom& geo, const PlaneBlock& pl,
                        float* partial, size_t smem, cudaStream_t st, int slot) {
-    cudaError_t e = set_smem_attr(refocus_sep_kernel<KR, kSepPlanes, kWA, kHA>, slot);
+    auto kern = refocus_sep_kernel<KR, PB, kWA, kHA, kTma, kStages, kMinBlocks>;
+    cudaError_t e = set_smem_attr(kern, slot);
     if (e != cudaSuccess) return e;
-    const int pblocks = (geo.n_planes + kSepPlanes - 1) / kSepPlanes;
-    refocus_sep_kernel<KR, kSepPlanes, kWA, kHA><<<dim3(geo.hb, pblocks), kThreads, smem, st>>>(tm, geo, pl,
-                                                                                                partial);
+    CUtensorMap dummy;
+    std::memset(&dummy, 0, sizeof(dummy));
+    const int pblocks = (geo.n_planes + PB - 1) / PB;
+    kern<<<dim3(geo.hb, pblocks), kThreads, smem, st>>>(tm ? *tm : dummy, g, geo, pl, partial);
     return cudaGetLastError();
 }
 
@@ -437,24 +485,53 @@ int kr_for(int ha, int wa, int cap) {
 
 }  // namespace
 
-static size_t sep_smem(int ha, int wa) {
+// Separable-kernel variant of an image shape.
+struct SepVariant {
+    bool ok;
+    bool tma;       // TMA staging (width a multiple of 4, box sides <= 256)
+    bool large;     // 1 plane per CTA, up to 32 rows per thread, 1 CTA per SM
+    int kr;         // rows per thread (power of two)
+    int stages;
+};
+
+static size_t sep_smem_for(int ha, int wa, int pb, int stages) {
     const size_t slice_f = ((size_t)ha * (wa + kPadL + kPadR) + 31) & ~(size_t)31;
-    return 128 + sizeof(float) * (kSepStages * slice_f + (size_t)kSepPlanes * (ha + 2) * wa) +
-           sizeof(Tap) * (kSepStages * (size_t)kSepPlanes * wa + (size_t)kSepPlanes * ha);
+    return 128 + sizeof(float) * (stages * slice_f + (size_t)pb * (ha + 2) * wa) +
+           sizeof(Tap) * (stages * (size_t)pb * wa + (size_t)pb * ha);
 }
 
-bool refocus_separable(int ha, int wa) {
-    // TMA staging: the box is (wa + 8) x ha floats, each side <= 256, rows 16-byte multiples
-    if (wa % 4 != 0 || wa + kPadL + kPadR > 256 || ha > 256) return false;
-    if (wa > kThreads) return false;
+static SepVariant sep_variant(int ha, int wa) {
+    SepVariant v{false, false, false, 1, 3};
+    if (wa > kThreads) return v;
+    v.tma = (wa % 4 == 0) && (wa + kPadL + kPadR <= 256) && ha <= 256;
     const int R = kThreads / wa;
-    if ((ha + R - 1) / R > 8) return false;
-    return sep_smem(ha, wa) <= 112 * 1024;
+    const int rows = (ha + R - 1) / R;
+    if (rows <= 8 && sep_smem_for(ha, wa, kSepPlanes, 3) <= 112 * 1024) {
+        v.ok = true;
+        v.kr = kr_for(ha, wa, 8);
+        v.stages = 3;
+        return v;
+    }
+    if (rows <= 32) {
+        v.large = true;
+        v.kr = rows <= 16 ? 16 : 32;
+        v.stages = sep_smem_for(ha, wa, 1, 3) <= 220 * 1024 ? 3 : 2;
+        v.ok = sep_smem_for(ha, wa, 1, v.stages) <= 220 * 1024;
+    }
+    return v;
 }
+
+bool refocus_separable(int ha, int wa) { return sep_variant(ha, wa).ok; }
 
 size_t refocus_smem_bytes(int ha, int wa) {
-    if (refocus_separable(ha, wa)) return sep_smem(ha, wa);
+    const SepVariant v = sep_variant(ha, wa);
+    if (v.ok) return sep_smem_for(ha, wa, v.large ? 1 : kSepPlanes, v.stages);
     return sizeof(float) * (size_t)(ha + 2) * (wa + 2) + sizeof(Tap) * ((size_t)wa + ha);
+}
+
+bool refocus_uses_tma(int ha, int wa) {
+    const SepVariant v = sep_variant(ha, wa);
+    return v.ok && v.tma;
 }
 
 int refocus_ranges(int ha, int wa, int hb, int wb, int n_planes, int sm_count) {
@@ -477,27 +554,54 @@ int refocus_range_size(int ha, int wa, int hb, int wb, int n_ranges) {
 cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const RefocusGeom& geo,
                            const PlaneBlock& pl, float* partial, cudaStream_t st) {
     const size_t smem = refocus_smem_bytes(geo.ha, geo.wa);
-    if (refocus_separable(geo.ha, geo.wa)) {
-        if (tm == nullptr) return cudaErrorInvalidValue;
-        // compile-time shapes of the common square detector sizes
-        if (geo.wa == 64 && geo.ha == 64) return launch_sep<8, 64, 64>(*tm, geo, pl, partial, smem, st, 10);
-        if (geo.wa == 32 && geo.ha == 32) return launch_sep<2, 32, 32>(*tm, geo, pl, partial, smem, st, 11);
-        switch (kr_for(geo.ha, geo.wa, 8)) {
-            case 1: return launch_sep<1>(*tm, geo, pl, partial, smem, st, 0);
-            case 2: return launch_sep<2>(*tm, geo, pl, partial, smem, st, 1);
-            case 4: return launch_sep<4>(*tm, geo, pl, partial, smem, st, 2);
-            default: return launch_sep<8>(*tm, geo, pl, partial, smem, st, 3);
+    const SepVariant v = sep_variant(geo.ha, geo.wa);
+    if (v.ok) {
+        if (v.tma && tm == nullptr) return cudaErrorInvalidValue;
+        const float* g = gamma_f32;
+        if (!v.large) {
+            if (v.tma) {
+                // compile-time shapes of the common square detector sizes
+                if (geo.wa == 64 && geo.ha == 64)
+                    return launch_sep<8, 2, true, 3, 2, 64, 64>(tm, g, geo, pl, partial, smem, st, 10);
+                if (geo.wa == 32 && geo.ha == 32)
+                    return launch_sep<2, 2, true, 3, 2, 32, 32>(tm, g, geo, pl, partial, smem, st, 11);
+                switch (v.kr) {
+                    case 1: return launch_sep<1, 2, true, 3, 2>(tm, g, geo, pl, partial, smem, st, 0);
+                    case 2: return launch_sep<2, 2, true, 3, 2>(tm, g, geo, pl, partial, smem, st, 1);
+                    case 4: return launch_sep<4, 2, true, 3, 2>(tm, g, geo, pl, partial, smem, st, 2);
+                    default: return launch_sep<8, 2, true, 3, 2>(tm, g, geo, pl, partial, smem, st, 3);
+                }
+            }
+            switch (v.kr) {
+                case 1: return launch_sep<1, 2, false, 3, 2>(nullptr, g, geo, pl, partial, smem, st, 4);
+                case 2: return launch_sep<2, 2, false, 3, 2>(nullptr, g, geo, pl, partial, smem, st, 5);
+                case 4: return launch_sep<4, 2, false, 3, 2>(nullptr, g, geo, pl, partial, smem, st, 6);
+                default: return launch_sep<8, 2, false, 3, 2>(nullptr, g, geo, pl, partial, smem, st, 7);
+            }
         }
+        const CUtensorMap* t = v.tma ? tm : nullptr;
+        if (v.stages == 3) {
+            if (v.kr == 16)
+                return v.tma ? launch_sep<16, 1, true, 3, 1>(t, g, geo, pl, partial, smem, st, 12)
+                             : launch_sep<16, 1, false, 3, 1>(t, g, geo, pl, partial, smem, st, 13);
+            return v.tma ? launch_sep<32, 1, true, 3, 1>(t, g, geo, pl, partial, smem, st, 14)
+                         : launch_sep<32, 1, false, 3, 1>(t, g, geo, pl, partial, smem, st, 15);
+        }
+        if (v.kr == 16)
+            return v.tma ? launch_sep<16, 1, true, 2, 1>(t, g, geo, pl, partial, smem, st, 16)
+                         : launch_sep<16, 1, false, 2, 1>(t, g, geo, pl, partial, smem, st, 17);
+        return v.tma ? launch_sep<32, 1, true, 2, 1>(t, g, geo, pl, partial, smem, st, 18)
+                     : launch_sep<32, 1, false, 2, 1>(t, g, geo, pl, partial, smem, st, 19);
     }
     const int R = kThreads / geo.wa;
     const int kr = kr_for(geo.ha, geo.wa, 16);
     const int zchunks = (geo.ha + R * kr - 1) / (R * kr);
     switch (kr) {
-        case 1: return launch_direct<1>(gamma_f32, geo, pl, partial, zchunks, smem, st, 5);
-        case 2: return launch_direct<2>(gamma_f32, geo, pl, partial, zchunks, smem, st, 6);
-        case 4: return launch_direct<4>(gamma_f32, geo, pl, partial, zchunks, smem, st, 7);
-        case 8: return launch_direct<8>(gamma_f32, geo, pl, partial, zchunks, smem, st, 8);
-        default: return launch_direct<16>(gamma_f32, geo, pl, partial, zchunks, smem, st, 9);
+        case 1: return launch_direct<1>(gamma_f32, geo, pl, partial, zchunks, smem, st, 5 + 20);
+        case 2: return launch_direct<2>(gamma_f32, geo, pl, partial, zchunks, smem, st, 6 + 20);
+        case 4: return launch_direct<4>(gamma_f32, geo, pl, partial, zchunks, smem, st, 7 + 20);
+        case 8: return launch_direct<8>(gamma_f32, geo, pl, partial, zchunks, smem, st, 8 + 20);
+        default: return launch_direct<16>(gamma_f32, geo, pl, partial, zchunks, smem, st, 9 + 20);
     }
 }
 

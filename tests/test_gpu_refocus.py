@@ -38,7 +38,17 @@ def test_refocus_hand_worked():
     assert np.array_equal(out, np.array(g["out"]))
 
 
-@pytest.mark.parametrize("ha,wa,hb,wb", [(9, 12, 4, 6), (64, 64, 32, 32), (33, 70, 7, 5), (5, 300, 3, 2)])
+@pytest.mark.parametrize("ha,wa,hb,wb", [
+    (9, 12, 4, 6),        # separable, TMA staging, 2 planes per CTA
+    (64, 64, 32, 32),     # compile-time 64 x 64 shape
+    (33, 70, 7, 5),       # separable, cp.async staging (width not a multiple of 4)
+    (5, 300, 3, 2),       # TMA box too wide: cp.async staging
+    (96, 96, 8, 8),       # one plane per CTA, 32 rows per thread, TMA
+    (72, 72, 6, 6),       # one plane per CTA, 16 rows per thread
+    (100, 90, 3, 3),      # one plane per CTA, cp.async staging
+    (128, 128, 4, 4),     # one plane per CTA, two staged slices
+    (200, 120, 2, 2),     # 50 rows per thread: direct kernel
+])
 def test_refocus_random_gamma(ha, wa, hb, wb):
     rng = np.random.default_rng(ha * 1000 + wa)
     gamma = rng.standard_normal((ha * wa, hb * wb))
