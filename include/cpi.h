@@ -166,11 +166,15 @@ CPI_API cpi_status cpi_correlate_stage(int32_t stage, const cpi_frames *a, const
  * (alpha, beta) = (1, 0) is the plane the spatial detector is focused on.
  *
  *   gamma_f32 : float [hb*wb][ha*wa], slice-major (cpi_correlate's gamma_f32)
- *   planes    : HOST array of n_planes (alpha, beta), finite
+ *   planes    : HOST array of n_planes (alpha, beta), |alpha|, |beta| <= 1e6
+ *               (else CPI_ERR_INVALID_ARG)
  *   out       : float [n_planes][ha][wa]
  * Sums use compensated FP32 accumulation; coordinates are computed on the fly
- * with ~48-bit (double-float) precision.  Requires ha, wa, hb, wb >= 1,
- * wa <= 512, (ha + 2) * (wa + 2) * 4 bytes <= 200 KiB, gamma_f32 16-byte aligned.
+ * in 32.32 fixed point from FP64 products, and each interpolation fraction is
+ * rounded to 24 bits (the two weights are exact and sum to 1).  Requires
+ * ha, wa, hb, wb >= 1, wa <= 512, (ha + 4) * (wa + 4) * 4 bytes <= 200 KiB,
+ * hb*wb*ha*wa < 2^31 - 1024, gamma_f32 16-byte aligned; Gamma values must be
+ * finite (a non-finite value may reach outputs through zero-weight taps).
  * -------------------------------------------------------------------------- */
 CPI_API size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb,
                                   int32_t n_planes);

@@ -111,6 +111,19 @@ bool make_slice_map(CUtensorMap* m, const float* g, int ha, int wa, int64_t mb) 
     return r == CUDA_SUCCESS;
 }
 
+bool make_gamma_map(CUtensorMap* m, const float* g, int64_t elements) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    cuuint64_t dims[1] = {(cuuint64_t)elements};
+    cuuint64_t strides[1] = {0};
+    cuuint32_t box[1] = {256};
+    cuuint32_t estr[1] = {1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<float*>(g), dims, strides, box,
+                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -302,10 +315,10 @@ cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
     if (!gamma_f32 || !planes || !out || n_planes < 1) return CPI_ERR_INVALID_ARG;
     if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || wa > 512) return CPI_ERR_INVALID_ARG;
     if ((int64_t)hb * wb > kMaxPixels) return CPI_ERR_INVALID_ARG;
-    if (refocus_smem_bytes(ha, wa) > 220 * 1024) return CPI_ERR_UNSUPPORTED;
+    if (refocus_smem_bytes(ha, wa, wb) > 220 * 1024) return CPI_ERR_UNSUPPORTED;
     if (!aligned(gamma_f32, 16) || !aligned(out, 4)) return CPI_ERR_INVALID_ARG;
     for (int i = 0; i < n_planes; ++i)
-        if (!std::isfinite(planes[i].alpha) || !std::isfinite(planes[i].beta))
+        if (!(std::fabs(planes[i].alpha) <= kRefocusMaxCoef) || !(std::fabs(planes[i].beta) <= kRefocusMaxCoef))
             return CPI_ERR_INVALID_ARG;
     DeviceInfo* dev = nullptr;
     if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
@@ -315,9 +328,12 @@ cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
     const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, dev->sm_count);
     float* partial = static_cast<float*>(workspace);
     CUtensorMap tm;
-    const bool sep = refocus_uses_tma(ha, wa);
-    if (sep && (int64_t)hb * wb * ha >= ((int64_t)1 << 31)) return CPI_ERR_UNSUPPORTED;
-    if (sep && !make_slice_map(&tm, gamma_f32, ha, wa, (int64_t)hb * wb)) return CPI_ERR_CUDA;
+    const int staging = refocus_staging(ha, wa, wb);
+    const bool pipe = staging != 0;
+    const int64_t elements = (int64_t)hb * wb * ha * wa;
+    if (pipe && elements >= ((int64_t)1 << 31) - 1024) return CPI_ERR_UNSUPPORTED;
+    if (staging == 1 && !make_gamma_map(&tm, gamma_f32, elements)) return CPI_ERR_CUDA;
+    if (staging == 2 && !make_slice_map(&tm, gamma_f32, ha, wa, (int64_t)hb * wb)) return CPI_ERR_CUDA;
     PlaneBlock pb;
     for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {
         const int np = n_planes - p0 < kRefocusMaxPlanesPerLaunch ? n_planes - p0
@@ -339,7 +355,7 @@ cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
         g.total_planes = n_planes;
         g.status = dev->status;
         g.timeout_ns = g_timeout_ns;
-        cudaError_t e = launch_refocus(gamma_f32, sep ? &tm : nullptr, g, pb, partial, st);
+        cudaError_t e = launch_refocus(gamma_f32, pipe ? &tm : nullptr, g, pb, partial, dev->sm_count, st);
         if (e != cudaSuccess) return CPI_ERR_CUDA;
     }
     return cuda_status(
@@ -373,10 +389,10 @@ cpi_status check_batch_item(const cpi_batch_item& b) {
     if (b.n_planes < 0) return CPI_ERR_INVALID_ARG;
     if (b.n_planes > 0) {
         if (!b.planes || !b.refocus_out || !b.gamma_f32) return CPI_ERR_INVALID_ARG;
-        if (b.a.width > 512 || refocus_smem_bytes(b.a.height, b.a.width) > 220 * 1024)
+        if (b.a.width > 512 || refocus_smem_bytes(b.a.height, b.a.width, b.b.width) > 220 * 1024)
             return CPI_ERR_UNSUPPORTED;
         for (int i = 0; i < b.n_planes; ++i)
-            if (!std::isfinite(b.planes[i].alpha) || !std::isfinite(b.planes[i].beta))
+            if (!(std::fabs(b.planes[i].alpha) <= kRefocusMaxCoef) || !(std::fabs(b.planes[i].beta) <= kRefocusMaxCoef))
                 return CPI_ERR_INVALID_ARG;
     }
     return CPI_OK;

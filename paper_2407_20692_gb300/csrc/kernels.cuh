@@ -89,21 +89,28 @@ struct RefocusGeom {
     int32_t n_planes;        // planes in this launch
     int32_t plane_offset;    // index of this launch's first plane in the partial buffer
     int32_t total_planes;
+    int32_t boxes;           // 256-element boxes per slice, 1-D staging (set by launch_refocus)
+    int32_t slice_f;         // floats per shared-memory stage buffer (set by launch_refocus)
     unsigned int* status;           // device status word (bounded waits)
     unsigned long long timeout_ns;
 };
-size_t refocus_smem_bytes(int ha, int wa);
-bool refocus_separable(int ha, int wa);
-bool refocus_uses_tma(int ha, int wa);     // separable kernel staged by TMA (needs the tensor map)
+// Planes with |alpha| or |beta| above this are rejected (coordinates are formed
+// in 32.32 fixed point).
+constexpr double kRefocusMaxCoef = 1.0e6;
+size_t refocus_smem_bytes(int ha, int wa, int wb);
+// Pipelined kernel (TMA-staged slices).  refocus_staging: 0 = direct kernel (no
+// tensor map), 1 = 1-D tensor map over all Mb*ha*wa elements with a 256-element
+// box, 2 = 2-D map over [Mb*ha rows][wa columns] with a (wa + 8) x ha box.
+bool refocus_pipelined(int ha, int wa, int wb);
+int refocus_staging(int ha, int wa, int wb);
 // Number of ranges the angular pixels are split into (one partial image each),
-// and the size of one range (angular rows for the separable kernel, angular
+// and the size of one range (angular rows for the pipelined kernel, angular
 // pixels for the direct one).
 int refocus_ranges(int ha, int wa, int hb, int wb, int n_planes, int sm_count);
 int refocus_range_size(int ha, int wa, int hb, int wb, int n_ranges);
-// tm: 2-D tensor map over gamma_f32 viewed as [Mb * ha rows][wa columns] with a
-// (wa + 8) x ha box, required when refocus_separable(ha, wa).
+// tm: the tensor map refocus_staging() asks for (unused by the direct kernel).
 cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const RefocusGeom& g,
-                           const PlaneBlock& pl, float* partial, cudaStream_t st);
+                           const PlaneBlock& pl, float* partial, int sm_count, cudaStream_t st);
 cudaError_t launch_refocus_reduce(const float* partial, int n_ranges, int64_t per_range,
                                   float* out, cudaStream_t st);
 

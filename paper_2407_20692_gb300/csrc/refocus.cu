@@ -15,20 +15,22 @@
 //     out(r, c) += wy0(r,br) U(yo, c) + wy1(r,br) U(yo+1, c),
 // which reads each staged slice value twice instead of four times.
 //
-// Interpolation coordinates are computed on the fly inside the kernel (the
-// point of Section 4.1), per slice for the W_a columns and per angular row for
-// the H_a rows, in double-float arithmetic on the FP32 pipe (~48-bit
-// significands; GB300's FP64 pipe is a small fraction of its FP32 rate).  All
-// sums are Kahan-compensated FP32; the partial image of each angular row is
-// written in FP32 and the rows are added in a fixed order (Kahan-compensated)
-// by a second kernel, so the result is deterministic.
+// Coordinates are computed on the fly inside the kernel (the point of Section
+// 4.1) in 32.32 fixed point: u = A + B with A = alpha*(j - c_a) + c_a per
+// output column (row) and B = beta*s*(b - c_b) per angular column (row), each
+// rounded once from FP64.  The fraction is rounded to 24 bits, so both weights
+// (1 - f, f) are exact FP32 numbers and sum to exactly 1.  Sums are FP32 with
+// Kahan compensation across pairs of angular columns; the partial image of each
+// angular row is written in FP32 and the rows are added in a fixed order
+// (Kahan-compensated) by a second kernel, so the result is deterministic.
 //
 // Layout: Gamma arrives slice-major, float [Mb][Ma]; slice b is one contiguous
-// spatial image, staged into shared memory with cp.async (double-buffered),
-// with zero columns on both sides so that out-of-grid taps read 0.
+// spatial image.  It is staged into shared memory by 1-D TMA boxes of 256
+// elements, starting at the 16-byte boundary at or below the slice (the slice
+// then sits 0-3 elements into the buffer).
 //
-// This file is compiled without FMA contraction: the double-float and Kahan
-// steps depend on the written rounding order; the products use explicit fmaf.
+// This file is compiled without FMA contraction: the Kahan steps depend on the
+// written rounding order; the products use explicit fmaf.
 #include <cstring>
 
 #include "kernels.cuh"
@@ -37,64 +39,47 @@
 namespace cpi {
 namespace {
 
-constexpr int kThreads = 512;
-constexpr int kPadL = 4;      // zero columns left of the interior (keeps 16-byte alignment)
-constexpr int kPadR = 4;
-constexpr int kSepPlanes = 2;  // planes per CTA of the separable kernel
-constexpr int kSepStages = 3;  // staged slices (TMA pipeline depth)
+constexpr int kBox = 256;        // elements per 1-D TMA box
+constexpr int kUPad = 2;         // zero rows above and below each U image
 
-// ------------------------------------------------------------ double-float helpers
-struct DF {
-    float hi, lo;
+// ------------------------------------------------------------ coordinates
+__device__ __forceinline__ long long fix32(double v) { return __double2ll_rn(v * 4294967296.0); }
+
+struct Frac {
+    int i;      // floor of the coordinate
+    float f;    // fraction, a multiple of 2^-24 in [0, 1)
 };
-__device__ __forceinline__ DF two_sum(float a, float b) {
-    const float s = a + b;
-    const float bb = s - a;
-    const float e = (a - (s - bb)) + (b - bb);
-    return {s, e};
-}
-__device__ __forceinline__ DF df_split(double v) {
-    const float h = __double2float_rn(v);
-    return {h, __double2float_rn(v - (double)h)};
-}
-// (a.hi + a.lo) * x for a small exactly representable x
-__device__ __forceinline__ DF df_mul(DF a, float x) {
-    const float p = a.hi * x;
-    float e = __fmaf_rn(a.hi, x, -p);
-    e = __fmaf_rn(a.lo, x, e);
-    return two_sum(p, e);
-}
-__device__ __forceinline__ DF df_add(DF a, DF b) {
-    const DF s = two_sum(a.hi, b.hi);
-    return two_sum(s.hi, s.lo + (a.lo + b.lo));
+__device__ __forceinline__ Frac split_fix(long long u) {
+    const long long u24 = (u + 128) >> 8;      // round the 32-bit fraction to 24 bits
+    return {(int)(u24 >> 24), (float)(int)(u24 & 0xFFFFFF) * 0x1p-24f};
 }
 
-// Bilinear tap of one axis: u = (scale * j_centred + shift * b_centred) + centre.
-// Returns the padded offset of the first tap and both weights (zero weights when
-// neither tap lies inside [0, n)).
-struct Tap {
+// Taps of one axis in an unpadded row of n values: read columns off and off+1
+// with weights w0, w1.  Taps outside [0, n) get weight 0 and are moved onto
+// in-grid columns, so no read leaves the staged slice.
+struct __align__(16) STap {
+    int off;
+    float w0, w1;
+    int unused;
+};
+__device__ __forceinline__ STap slice_tap(long long u, int n) {
+    const Frac q = split_fix(u);
+    const float w1 = q.f, w0 = 1.0f - q.f;
+    if (q.i >= 0 && q.i <= n - 2) return {q.i, w0, w1, 0};
+    if (q.i == -1) return {0, w1, 0.0f, 0};                       // only column 0 inside
+    if (q.i == n - 1) return n >= 2 ? STap{n - 2, 0.0f, w0, 0} : STap{0, w0, 0.0f, 0};
+    return {0, 0.0f, 0.0f, 0};
+}
+
+// Taps of one axis in a buffer with kUPad zero rows (columns) on both sides:
+// out-of-grid taps read the zero border.
+struct PTap {
     int off;
     float w0, w1;
 };
-__device__ __forceinline__ Tap axis_tap(DF scale, float jc, DF shift, float bcen, float centre,
-                                        int n, int pad) {
-    const DF u = df_add(df_add(df_mul(scale, jc), df_mul(shift, bcen)), DF{centre, 0.0f});
-    float f0 = floorf(u.hi);
-    float fr = (u.hi - f0) + u.lo;
-    if (fr < 0.0f) {
-        f0 -= 1.0f;
-        fr += 1.0f;
-    } else if (fr >= 1.0f) {
-        f0 += 1.0f;
-        fr -= 1.0f;
-    }
-    Tap t{pad - 1, 0.0f, 0.0f};
-    if (f0 >= -1.0f && f0 <= (float)(n - 1)) {
-        t.off = (int)f0 + pad;
-        t.w0 = 1.0f - fr;
-        t.w1 = fr;
-    }
-    return t;
+__device__ __forceinline__ PTap padded_tap(long long u, int n) {
+    const Frac q = split_fix(u);
+    return {min(max(q.i, -kUPad), n) + kUPad, 1.0f - q.f, q.f};
 }
 
 __device__ __forceinline__ void kahan_add(float& acc, float& cmp, float v) {
@@ -104,245 +89,304 @@ __device__ __forceinline__ void kahan_add(float& acc, float& cmp, float v) {
     acc = t;
 }
 
-struct PlaneCoef {
-    DF alpha, qx, qy;     // alpha, beta*sx, beta*sy
-};
-__device__ __forceinline__ PlaneCoef plane_coef(const PlaneBlock& pl, int p, int ha, int wa, int hb,
-                                                int wb) {
-    const double al = pl.alpha[p], be = pl.beta[p];
-    const double sx = (double)wa / (double)wb, sy = (double)ha / (double)hb;
-    return {df_split(al), df_split(be * sx), df_split(be * sy)};
+__device__ __forceinline__ void named_bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
-// ------------------------------------------------------------ separable kernel
-// CTA = (angular row br, block of PB planes).  Thread t owns column c = t % wa
-// and rows rp + R*k (R = 512 / wa row phases).  Each slice (br, bc) is staged
-// into shared memory with 4 zero columns on both sides: by one 2-D TMA copy of
-// a (wa + 8) x ha box starting at column -4 (the columns outside the image come
-// back as zeros, exactly the out-of-grid taps), or, for widths TMA cannot
-// describe, by 4-byte cp.async copies of each thread's own pixels.  Every
-// staged slice is interpolated along x for all PB planes; after the last bc the
-// row's U images are interpolated along y and this angular row's contribution
-// to each output pixel is written to partial[br][plane][pixel].  The reduce
-// kernel adds the angular rows in a fixed order (compensated FP32).
-//
-// Variants: PB = 2 planes, <= 8 rows per thread, 2 CTAs per SM (small images);
-// PB = 1 plane, <= 32 rows per thread, 1 CTA per SM (images up to ~128 x 128).
-// kWA > 0 fixes the image width (and kHA the height) at compile time, so every
-// row offset of the inner loop is an immediate.
-__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
-                     static_cast<uint32_t>(__cvta_generic_to_shared(dst))),
-                 "l"(src)
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
 
-template <int KR, int PB, int kWA, int kHA, bool kTma, int kStages, int kMinBlocks>
-__global__ void __launch_bounds__(kThreads, kMinBlocks) refocus_sep_kernel(const __grid_constant__ CUtensorMap tm,
-                                                                           const float* __restrict__ gamma,
-                                                                           const RefocusGeom geo,
-                                                                           const PlaneBlock pl,
-                                                                           float* __restrict__ partial) {
+__device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* m, uint64_t* bar, int32_t x) {
+    asm volatile(
+        "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(x)
+        : "memory");
+}
+
+// ------------------------------------------------------------ pipelined kernel
+// Persistent: one CTA of kThreads per SM walks the work units blockIdx.x,
+// blockIdx.x + gridDim.x, ...  A unit is (angular row br, block of PB planes);
+// units are ordered br-major, so CTAs running at the same time stage the same
+// slices (L2 reuse) and, as the grid is a multiple of the plane-block count in
+// the common case, a CTA keeps its plane block from unit to unit.
+//
+// Slices (br, bc) of the CTA's units stream through kStages shared-memory
+// buffers, one TMA copy (group) each, completion counted on full[stage].  The
+// last warp to finish with a buffer (a shared counter per stage) issues the copy
+// of the slice kStages further on into it, so no thread ever waits for a free
+// buffer.  Staging: a 2-D box of (wa + 8) x ha from column -4 when wa % 4 == 0
+// (the 4 columns on each side come back as zeros, the out-of-grid taps), else
+// 1-D boxes of 256 elements from the 16-byte boundary at or below the slice.
+//
+// Thread t owns column c = t % wa and rows rp + R*k (R = kThreads / wa).  For
+// each staged slice and each plane of the unit it reads its x taps (from a
+// per-plane-block table when it fits in shared memory, else computes them),
+// adds NSTEP slices with fused multiply-adds and Kahan-adds the step's sum into
+// its U values.  After the unit's last slice the U images go to shared memory
+// and are interpolated along y; this angular row's contribution to each output
+// pixel is written to partial[br][plane][pixel].
+//
+// Every wait is bounded (the device status word records a time out).  A slice
+// that never arrives stops every thread at that same slice, so no barrier is
+// left half-entered.
+constexpr int kThreads = 512;
+constexpr int kPadL = 4;         // zero columns left of a 2-D staged row (TMA x start -4)
+constexpr int kPadR = 4;
+
+template <bool kPad>
+struct XTab;
+template <>
+struct XTab<true> {    // 2-D staged rows with zero borders: w0 = 1 - w1
+    int off;
+    float w1;
+};
+template <>
+struct XTab<false> {   // unpadded rows: both weights (edge taps moved in-grid)
+    STap t;
+};
+
+template <bool kPad>
+__device__ __forceinline__ XTab<kPad> make_xtab(long long u, int wa, int sh) {
+    if constexpr (kPad) {
+        const Frac q = split_fix(u);
+        return {min(max(q.i, -2), wa) + kPadL, q.f};
+    } else {
+        STap t = slice_tap(u, wa);
+        t.off += sh;
+        return {t};
+    }
+}
+
+template <bool kPad>
+__device__ __forceinline__ void read_xtab(const XTab<kPad>* e, int& off, float& w0, float& w1) {
+    if constexpr (kPad) {
+        const float2 v = *reinterpret_cast<const float2*>(e);
+        off = __float_as_int(v.x);
+        w1 = v.y;
+        w0 = 1.0f - v.y;
+    } else {
+        const float4 v = *reinterpret_cast<const float4*>(e);
+        off = __float_as_int(v.x);
+        w0 = v.y;
+        w1 = v.z;
+    }
+}
+
+template <int KR, int PB, int NSTEP, int kStages, bool kPad, bool kTable, int kWA, int kHA>
+__global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_constant__ CUtensorMap tm,
+                                                                   const RefocusGeom geo, const PlaneBlock pl,
+                                                                   float* __restrict__ partial) {
+    static_assert(NSTEP == 1 || NSTEP == 2, "one or two slices per step");
+    static_assert(kStages >= NSTEP + 1, "a step must not hold every stage");
+    constexpr int NW = kThreads / 32;
     extern __shared__ __align__(128) float sm_raw[];
     const int ha = kWA ? kHA : geo.ha, wa = kWA ? kWA : geo.wa, hb = geo.hb, wb = geo.wb;
-    const int WS = wa + kPadL + kPadR;                 // staged slice row stride (TMA box width)
-    const int slice_f = (ha * WS + 31) & ~31;          // buffer stride: 128-byte multiples
-    // 128-byte aligned start, computed on the shared-window offset so that the
-    // pointers stay shared-space (the loads below compile to shared loads)
-    float* const buf0 = sm_raw + (((128u - (static_cast<uint32_t>(__cvta_generic_to_shared(sm_raw)) & 127u)) & 127u) >> 2);
-    float* const U = buf0 + kStages * slice_f;         // PB x (ha + 2) x wa, zero rows -1 and ha
-    Tap* const xt = reinterpret_cast<Tap*>(U + PB * (ha + 2) * wa);   // [kStages][PB][wa]
-    Tap* const yt = xt + kStages * PB * wa;                           // [PB][ha]
-    __shared__ PlaneCoef coef[PB];                     // per-plane coefficients, computed once
-    __shared__ __align__(8) uint64_t full[kStages];    // TMA completion of each slice buffer
-    __shared__ int abort_flag;
+    const int Ma = ha * wa;
+    const int WS = kPad ? wa + kPadL + kPadR : wa;     // staged row stride
+    const int slice_f = geo.slice_f;                   // floats per stage buffer (multiple of 32)
+    uint8_t* p = reinterpret_cast<uint8_t*>(
+        sm_raw + (((128u - (static_cast<uint32_t>(__cvta_generic_to_shared(sm_raw)) & 127u)) & 127u) >> 2));
+    float* const buf0 = reinterpret_cast<float*>(p);
+    p += sizeof(float) * (size_t)kStages * slice_f;
+    XTab<kPad>* const xtab = reinterpret_cast<XTab<kPad>*>(p);   // [PB][wb][wa] when kTable
+    if (kTable) p += sizeof(XTab<kPad>) * (size_t)PB * wb * wa;
+    PTap* const yt = reinterpret_cast<PTap*>(p);                  // [PB][ha]
+    p += (sizeof(PTap) * (size_t)PB * ha + 15) & ~(size_t)15;
+    long long* const ax = reinterpret_cast<long long*>(p);        // [PB][wa]
+    p += sizeof(long long) * (size_t)PB * wa;
+    long long* const bx = reinterpret_cast<long long*>(p);        // [PB][wb]
+    p += sizeof(long long) * (size_t)PB * wb;
+    float* const U = reinterpret_cast<float*>(p);                 // [PB][ha + 2*kUPad][wa]
+    __shared__ __align__(8) uint64_t full[kStages];
+    __shared__ unsigned int relcnt[kStages];
 
-    const int tid = threadIdx.x;
-    const int R = kThreads / wa;
-    const int c = tid % wa, rp = tid / wa;
-    const bool active = rp < R;
-    const int nk = active ? (ha - rp + R - 1) / R : 0;      // rows of this thread
-    const int br = blockIdx.x;
-    const int pbase = blockIdx.y * PB;                  // first plane of this CTA (in this launch)
-    const int np = min(PB, geo.n_planes - pbase);
-    const float cxa = 0.5f * (float)(wa - 1), cya = 0.5f * (float)(ha - 1);
-    const float cxb = 0.5f * (float)(wb - 1), cyb = 0.5f * (float)(hb - 1);
-    const int64_t Ma = (int64_t)ha * wa;
-    const uint32_t slice_bytes = (uint32_t)(ha * WS * sizeof(float));
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int UH = ha + 2 * kUPad;
+    const int n_pb = (geo.n_planes + PB - 1) / PB;
+    const int n_units = hb * n_pb;
+    const int n_mine = blockIdx.x < n_units ? (n_units - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+    const uint32_t total_sl = (uint32_t)n_mine * (uint32_t)wb;
+    const double cxa = 0.5 * (double)(wa - 1), cya = 0.5 * (double)(ha - 1);
+    const double cxb = 0.5 * (double)(wb - 1), cyb = 0.5 * (double)(hb - 1);
+    const double sx = (double)wa / (double)wb, sy = (double)ha / (double)hb;
+    const uint32_t stage_bytes = (uint32_t)(kPad ? ha * WS * sizeof(float) : geo.boxes * kBox * sizeof(float));
+
+    // slice q of this CTA (q-th slice of its unit sequence) -> stage q % kStages
+    auto issue = [&](uint32_t q) {
+        const int s = (int)(q % kStages);
+        const int k = (int)(q / (uint32_t)wb), bc = (int)(q - (uint32_t)k * wb);
+        const int u = blockIdx.x + k * gridDim.x;
+        const int br = u / n_pb;
+        mbar_arrive_expect_tx(&full[s], stage_bytes);
+        float* dst = buf0 + (size_t)s * slice_f;
+        if constexpr (kPad) {
+            tma_load_2d(dst, &tm, &full[s], -kPadL, (br * wb + bc) * ha);
+        } else {
+            const long long e = (long long)(br * wb + bc) * Ma;
+            const int32_t x0 = (int32_t)(e & ~3ll);
+            for (int b = 0; b < geo.boxes; ++b) tma_load_1d(dst + b * kBox, &tm, &full[s], x0 + b * kBox);
+        }
+    };
 
     if (tid == 0) {
-        for (int i = 0; i < kStages; ++i) mbar_init(&full[i], 1);
-        abort_flag = 0;
+        for (int i = 0; i < kStages; ++i) {
+            mbar_init(&full[i], 1);
+            relcnt[i] = 0;
+        }
         fence_barrier_init();
     }
-    if (tid < np) coef[tid] = plane_coef(pl, pbase + tid, ha, wa, hb, wb);
-    for (int i = tid; i < PB * wa; i += kThreads) {
-        const int j = i / wa, x = i - j * wa;
-        U[j * (ha + 2) * wa + x] = 0.0f;
-        U[j * (ha + 2) * wa + (ha + 1) * wa + x] = 0.0f;
+    for (int i = tid; i < PB * 2 * kUPad * wa; i += kThreads) {   // zero border rows of U
+        const int j = i / (2 * kUPad * wa), rem = i - j * 2 * kUPad * wa;
+        const int row = rem / wa, x = rem - row * wa;
+        U[(j * UH + (row < kUPad ? row : ha + row)) * wa + x] = 0.0f;
     }
-    if constexpr (!kTma) {   // zero columns of every buffer row (cp.async writes the interior only)
-        for (int i = tid; i < kStages * ha; i += kThreads) {
-            float* row = buf0 + (i / ha) * slice_f + (i % ha) * WS;
-#pragma unroll
-            for (int q = 0; q < kPadL; ++q) row[q] = 0.0f;
-#pragma unroll
-            for (int q = 0; q < kPadR; ++q) row[kPadL + wa + q] = 0.0f;
-        }
-    }
-    __syncthreads();   // barriers initialised, coef and pads visible
-    auto issue = [&](int bc) {   // slice (br, bc) -> buffer bc % kStages
-        const int sb = bc % kStages;
-        if constexpr (kTma) {
-            if (tid == 0) {
-                mbar_arrive_expect_tx(&full[sb], slice_bytes);
-                tma_load_2d(buf0 + sb * slice_f, &tm, &full[sb], -kPadL, (br * wb + bc) * ha);
-            }
-        } else {
-            if (active) {
-                const float* src = gamma + ((int64_t)br * wb + bc) * Ma + (int64_t)rp * wa + c;
-                float* dst = buf0 + sb * slice_f + rp * WS + kPadL + c;
-                for (int k = 0; k < nk; ++k) cp_async4(dst + k * R * WS, src + (int64_t)k * R * wa);
-            }
-            cp_async_commit();   // one group per slice, also when this thread copied nothing
-        }
-    };
-    auto taps = [&](int bc) {    // x taps of slice bc for every plane
-        const int sb = bc % kStages;
-        for (int i = tid; i < np * wa; i += kThreads) {
-            const int j = i / wa, x = i - j * wa;
-            xt[(sb * PB + j) * wa + x] =
-                axis_tap(coef[j].alpha, (float)x - cxa, coef[j].qx, (float)bc - cxb, cxa, wa, kPadL);
-        }
-    };
-    // prologue: the first kStages - 1 slices in flight, their taps ready
-    int last_issue[kStages];
-#pragma unroll
-    for (int i = 0; i < kStages; ++i) last_issue[i] = -1;
-    for (int bc = 0; bc < kStages - 1; ++bc) {
-        if (bc < wb) {
-            issue(bc);
-            last_issue[bc % kStages] = bc;
-            taps(bc);
-        } else if constexpr (!kTma) {
-            cp_async_commit();   // keep one group per slot
-        }
-    }
+    __syncthreads();
+    if (tid == 0)
+        for (uint32_t q = 0; q < (uint32_t)kStages && q < total_sl; ++q) issue(q);
 
-    // U accumulates plainly (two fused multiply-adds per slice) over pairs of
-    // slices (Ug); the pair sums are Kahan-added (Ua, Uc): error <= (4 + 2) 2^-24
-    // of the summed magnitudes, to first order.
-    float Ug[PB][KR], Ua[PB][KR], Uc[PB][KR];
-#pragma unroll
-    for (int j = 0; j < PB; ++j)
-#pragma unroll
-        for (int k = 0; k < KR; ++k) Ug[j][k] = Ua[j][k] = Uc[j][k] = 0.0f;
-
-    for (int bc = 0; bc < wb; ++bc) {
-        const int sb = bc % kStages;
-        const uint32_t parity = (uint32_t)((bc / kStages) & 1);
-        if constexpr (kTma) {
-            // one thread waits for the copy; the others sleep in the barrier below
-            if (tid == 0 && !mbar_wait_sleepy(&full[sb], parity, geo.status, geo.timeout_ns)) abort_flag = 1;
-        } else {
-            cp_async_wait<kStages - 2>();   // this thread's copies of slice bc have landed
+    const int R = kThreads / wa;
+    constexpr int kWdiv = kWA > 0 ? kWA : 1;
+    constexpr bool kFull = kWA > 0 && kThreads % kWdiv == 0 && kHA == KR * (kThreads / kWdiv);
+    constexpr int kRStep = (kThreads / kWdiv) * (kWA + (kPad ? kPadL + kPadR : 0));
+    const int c = tid % wa, rp = tid / wa;
+    const bool active = kFull || rp < R;
+    const int nk = kFull ? KR : (active ? max(0, min(KR, (ha - rp + R - 1) / R)) : 0);
+    const int rstep = R * WS;
+    uint32_t g = 0;
+    int cur_pb = -1;
+    for (int k = 0; k < n_mine; ++k) {
+        const int u = blockIdx.x + k * gridDim.x;
+        const int br = u / n_pb, pblk = u - br * n_pb, p0 = pblk * PB;
+        const int np = min(PB, geo.n_planes - p0);
+        if (pblk != cur_pb) {   // uniform: fixed-point x coordinates of this plane block
+            for (int i = tid; i < np * wa; i += kThreads) {
+                const int j = i / wa, x = i - j * wa;
+                ax[i] = fix32(pl.alpha[p0 + j] * ((double)x - cxa) + cxa);
+            }
+            for (int i = tid; i < np * wb; i += kThreads) {
+                const int j = i / wb, b = i - j * wb;
+                bx[i] = fix32((pl.beta[p0 + j] * sx) * ((double)b - cxb));
+            }
+            __syncthreads();
+            if constexpr (kTable) {
+                for (int i = tid; i < np * wb * wa; i += kThreads) {
+                    const int j = i / (wb * wa), rem = i - j * wb * wa;
+                    const int b = rem / wa, x = rem - b * wa;
+                    xtab[i] = make_xtab<kPad>(ax[j * wa + x] + bx[j * wb + b], wa, 0);
+                }
+                __syncthreads();
+            }
+            cur_pb = pblk;
         }
-        __syncthreads();   // slice bc landed; every thread is done with slice bc - 1
-        if (abort_flag) break;
-        // refill the buffer slice bc - 1 used, and prepare its taps
-        const int nxt = bc + kStages - 1;
-        if (nxt < wb) {
-            issue(nxt);
-            last_issue[nxt % kStages] = nxt;
-            taps(nxt);
-        } else if constexpr (!kTma) {
-            cp_async_commit();
-        }
-        if constexpr (kTma)
-            mbar_wait_bounded(&full[sb], parity, &abort_flag, geo.status, geo.timeout_ns);   // completes at once
-        if (active) {
-            const float* S = buf0 + sb * slice_f + rp * WS;
-            const int step = R * WS;
+        float Ua[PB][KR], Uc[PB][KR];
 #pragma unroll
-            for (int j = 0; j < PB; ++j) {
-                if (j < np) {
-                    const Tap tx = xt[(sb * PB + j) * wa + c];
-                    const float* q = S + tx.off;
-                    if constexpr (kWA > 0 && kHA % (kThreads / kWA) == 0) {
-                        constexpr int kStep = (kThreads / kWA) * (kWA + kPadL + kPadR);
+        for (int j = 0; j < PB; ++j)
 #pragma unroll
-                        for (int k = 0; k < KR; ++k)
-                            Ug[j][k] = __fmaf_rn(tx.w1, q[k * kStep + 1], __fmaf_rn(tx.w0, q[k * kStep], Ug[j][k]));
-                    } else if (nk == KR) {
+            for (int kk = 0; kk < KR; ++kk) Ua[j][kk] = Uc[j][kk] = 0.0f;
+        for (int bc0 = 0; bc0 < wb; bc0 += NSTEP) {
+            const int nsl = min(NSTEP, wb - bc0);
+            bool ok = true;
 #pragma unroll
-                        for (int k = 0; k < KR; ++k) {
-                            Ug[j][k] = __fmaf_rn(tx.w1, q[1], __fmaf_rn(tx.w0, q[0], Ug[j][k]));
-                            q += step;
+            for (int i = 0; i < NSTEP; ++i)
+                if (i < nsl)
+                    ok = ok && mbar_wait_bounded(&full[(g + i) % kStages], ((g + i) / kStages) & 1u, nullptr,
+                                                 geo.status, geo.timeout_ns);
+            if (!ok) {   // every thread stops at this same slice
+                if (tid == 0)
+                    for (uint32_t q = g; q < g + kStages && q < total_sl; ++q)
+                        mbar_wait_bounded(&full[q % kStages], (q / kStages) & 1u, nullptr, nullptr, geo.timeout_ns);
+                return;
+            }
+            if (nk > 0) {
+                const int s0 = (int)(g % kStages), s1 = (int)((g + 1) % kStages);
+                // 1-D staging: the slice starts sh elements into its buffer
+                const int sh0 = kPad ? 0 : (int)(((long long)(br * wb + bc0) * Ma) & 3);
+                const int sh1 = kPad ? 0 : (int)(((long long)(br * wb + bc0 + 1) * Ma) & 3);
+                const float* S0 = buf0 + (size_t)s0 * slice_f + rp * WS + sh0;
+                const float* S1 = buf0 + (size_t)s1 * slice_f + rp * WS + sh1;
+#pragma unroll
+                for (int j = 0; j < PB; ++j) {
+                    if (j < np) {
+                        int oa, ob = 0;
+                        float a0, a1, b0 = 0.0f, b1 = 0.0f;
+                        if constexpr (kTable) {
+                            read_xtab<kPad>(&xtab[(j * wb + bc0) * wa + c], oa, a0, a1);
+                            if (NSTEP == 2 && nsl == 2)
+                                read_xtab<kPad>(&xtab[(j * wb + bc0 + 1) * wa + c], ob, b0, b1);
+                        } else {
+                            const XTab<kPad> ta = make_xtab<kPad>(ax[j * wa + c] + bx[j * wb + bc0], wa, 0);
+                            read_xtab<kPad>(&ta, oa, a0, a1);
+                            if (NSTEP == 2 && nsl == 2) {
+                                const XTab<kPad> tb = make_xtab<kPad>(ax[j * wa + c] + bx[j * wb + bc0 + 1], wa, 0);
+                                read_xtab<kPad>(&tb, ob, b0, b1);
+                            }
                         }
-                    } else {
+                        const float* qa = S0 + oa;
+                        const float* qb = S1 + ob;
 #pragma unroll
-                        for (int k = 0; k < KR; ++k) {
-                            if (k < nk) Ug[j][k] = __fmaf_rn(tx.w1, q[1], __fmaf_rn(tx.w0, q[0], Ug[j][k]));
-                            q += step;
+                        for (int kk = 0; kk < KR; ++kk) {
+                            if (kFull || kk < nk) {
+                                const int o = kWA ? kk * kRStep : kk * rstep;
+                                float t = __fmaf_rn(a1, qa[o + 1], a0 * qa[o]);
+                                if (NSTEP == 2 && nsl == 2)
+                                    t = __fmaf_rn(b1, qb[o + 1], __fmaf_rn(b0, qb[o], t));
+                                kahan_add(Ua[j][kk], Uc[j][kk], t);
+                            }
                         }
                     }
                 }
             }
-        }
-        if ((bc & 1) == 1 || bc == wb - 1) {   // uniform: every thread takes it together
-#pragma unroll
-            for (int j = 0; j < PB; ++j)
-#pragma unroll
-                for (int k = 0; k < KR; ++k) {
-                    kahan_add(Ua[j][k], Uc[j][k], Ug[j][k]);
-                    Ug[j][k] = 0.0f;
+            // release the step's buffers; the last warp to do so refills them
+            __syncwarp();
+            if (lane == 0) {
+                for (int i = 0; i < nsl; ++i) {
+                    const uint32_t q = g + i;
+                    const int s = (int)(q % kStages);
+                    __threadfence_block();
+                    if (atomicAdd(&relcnt[s], 1u) == NW - 1) {
+                        relcnt[s] = 0;
+                        __threadfence_block();
+                        if (q + kStages < total_sl) {
+                            fence_proxy_async_smem();
+                            issue(q + kStages);
+                        }
+                    }
                 }
+            }
+            g += nsl;
         }
-    }
-    if constexpr (!kTma) cp_async_wait<0>();
-    if (abort_flag) {
-        // drain any copy still in flight before the CTA exits
-        if (kTma && tid == 0)
-            for (int i = 0; i < kStages; ++i)
-                if (last_issue[i] >= 0)
-                    mbar_wait_bounded(&full[i], (uint32_t)((last_issue[i] / kStages) & 1), nullptr,
-                                      nullptr, geo.timeout_ns);
-        return;
-    }
-    __syncthreads();   // all slices consumed before U is written
 
-    // y-interpolation of this angular row
-    if (active) {
+        // y-interpolation of this angular row
+        __syncthreads();   // the previous unit's U and y taps are no longer read
 #pragma unroll
         for (int j = 0; j < PB; ++j)
 #pragma unroll
-            for (int k = 0; k < KR; ++k) {
-                const int y = rp + R * k;
-                if (k < nk) U[(j * (ha + 2) + y + 1) * wa + c] = Ua[j][k] - Uc[j][k];
-            }
-    }
-    for (int i = tid; i < np * ha; i += kThreads) {
-        const int j = i / ha, y = i - j * ha;
-        Tap t = axis_tap(coef[j].alpha, (float)y - cya, coef[j].qy, (float)br - cyb, cya, ha, 1);
-        t.off = (j * (ha + 2) + t.off) * wa;
-        yt[j * ha + y] = t;
-    }
-    __syncthreads();
-    if (!active) return;
+            for (int kk = 0; kk < KR; ++kk)
+                if (j < np && (kFull || kk < nk)) U[(j * UH + rp + R * kk + kUPad) * wa + c] = Ua[j][kk] - Uc[j][kk];
+        for (int i = tid; i < np * ha; i += kThreads) {
+            const int j = i / ha, r = i - j * ha;
+            const long long uy = fix32(pl.alpha[p0 + j] * ((double)r - cya) + cya) +
+                                 fix32((pl.beta[p0 + j] * sy) * ((double)br - cyb));
+            PTap t = padded_tap(uy, ha);
+            t.off = (j * UH + t.off) * wa;
+            yt[i] = t;
+        }
+        __syncthreads();
 #pragma unroll
-    for (int j = 0; j < PB; ++j) {
-        if (j < np) {
-            float* dst = partial + ((int64_t)br * geo.total_planes + geo.plane_offset + pbase + j) * Ma;
+        for (int j = 0; j < PB; ++j) {
+            if (j < np) {
+                float* dst = partial + ((int64_t)br * geo.total_planes + geo.plane_offset + p0 + j) * Ma;
 #pragma unroll
-            for (int k = 0; k < KR; ++k) {
-                const int r = rp + R * k;
-                if (k < nk) {
-                    const Tap ty = yt[j * ha + r];
-                    const float v0 = U[ty.off + c], v1 = U[ty.off + wa + c];
-                    dst[(int64_t)r * wa + c] = __fmaf_rn(ty.w1, v1, ty.w0 * v0);
+                for (int kk = 0; kk < KR; ++kk) {
+                    if (kFull || kk < nk) {
+                        const int r = rp + R * kk;
+                        const PTap ty = yt[j * ha + r];
+                        const float v0 = U[ty.off + c], v1 = U[ty.off + wa + c];
+                        dst[(int64_t)r * wa + c] = __fmaf_rn(ty.w1, v1, ty.w0 * v0);
+                    }
                 }
             }
         }
@@ -350,63 +394,64 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks) refocus_sep_kernel(const
 }
 
 // ------------------------------------------------------------ direct kernel
-// Fallback for spatial images too large for the separable kernel's registers:
+// Fallback for spatial images too large for the pipelined kernel's registers:
 // CTA = (range of angular pixels, plane, band of output rows); each angular
 // pixel's slice is staged with a zero border and its 4 taps read per output.
+constexpr int kDirectThreads = 512;
 template <int KR>
-__global__ void __launch_bounds__(kThreads) refocus_direct_kernel(const float* __restrict__ gamma,
-                                                                  const RefocusGeom geo,
-                                                                  const PlaneBlock pl,
-                                                                  float* __restrict__ partial) {
+__global__ void __launch_bounds__(kDirectThreads) refocus_direct_kernel(const float* __restrict__ gamma,
+                                                                        const RefocusGeom geo,
+                                                                        const PlaneBlock pl,
+                                                                        float* __restrict__ partial) {
     extern __shared__ __align__(16) float sm[];
     const int ha = geo.ha, wa = geo.wa, hb = geo.hb, wb = geo.wb;
-    const int W2 = wa + 2;
+    const int W2 = wa + 2 * kUPad;
     const int64_t Ma = (int64_t)ha * wa;
-    float* slice = sm;                                                // (ha + 2) x (wa + 2)
-    Tap* xt = reinterpret_cast<Tap*>(slice + (ha + 2) * W2);          // [wa]
-    Tap* yt = xt + wa;                                                // [ha]
+    float* slice = sm;                                                   // (ha + 4) x (wa + 4)
+    PTap* xt = reinterpret_cast<PTap*>(slice + (ha + 2 * kUPad) * W2);   // [wa]
+    PTap* yt = xt + wa;                                                  // [ha]
     const int tid = threadIdx.x;
-    const int R = kThreads / wa;
+    const int R = kDirectThreads / wa;
     const int c = tid % wa, rp = tid / wa;
     const bool active = rp < R;
     const int row0 = blockIdx.z * (R * KR);
     const int p = blockIdx.y;
-    const PlaneCoef pc = plane_coef(pl, p, ha, wa, hb, wb);
-    const float cxa = 0.5f * (float)(wa - 1), cya = 0.5f * (float)(ha - 1);
-    const float cxb = 0.5f * (float)(wb - 1), cyb = 0.5f * (float)(hb - 1);
+    const double al = pl.alpha[p], be = pl.beta[p];
+    const double sx = (double)wa / (double)wb, sy = (double)ha / (double)hb;
+    const double cxa = 0.5 * (double)(wa - 1), cya = 0.5 * (double)(ha - 1);
+    const double cxb = 0.5 * (double)(wb - 1), cyb = 0.5 * (double)(hb - 1);
 
-    for (int i = tid; i < (ha + 2) * W2; i += kThreads) slice[i] = 0.0f;
+    for (int i = tid; i < (ha + 2 * kUPad) * W2; i += kDirectThreads) slice[i] = 0.0f;
     float acc[KR], cmp[KR];
 #pragma unroll
     for (int k = 0; k < KR; ++k) acc[k] = cmp[k] = 0.0f;
     const int nb = hb * wb;
     const int b_begin = blockIdx.x * geo.b_per_range;
     const int b_end = min(b_begin + geo.b_per_range, nb);
-    const int rows_per_pass = kThreads / wa;
     for (int b = b_begin; b < b_end; ++b) {
         __syncthreads();
         const float* src = gamma + (int64_t)b * Ma;
         if (active)
-            for (int r = rp; r < ha; r += rows_per_pass)
-                slice[(r + 1) * W2 + c + 1] = __ldg(src + (int64_t)r * wa + c);
+            for (int r = rp; r < ha; r += R) slice[(r + kUPad) * W2 + c + kUPad] = __ldg(src + (int64_t)r * wa + c);
         const int br = b / wb, bc = b - br * wb;
-        for (int j = tid; j < wa + ha; j += kThreads) {
+        for (int j = tid; j < wa + ha; j += kDirectThreads) {
             if (j < wa) {
-                xt[j] = axis_tap(pc.alpha, (float)j - cxa, pc.qx, (float)bc - cxb, cxa, wa, 1);
+                xt[j] = padded_tap(fix32(al * ((double)j - cxa) + cxa) + fix32((be * sx) * ((double)bc - cxb)), wa);
             } else {
-                Tap t = axis_tap(pc.alpha, (float)(j - wa) - cya, pc.qy, (float)br - cyb, cya, ha, 1);
+                const int r = j - wa;
+                PTap t = padded_tap(fix32(al * ((double)r - cya) + cya) + fix32((be * sy) * ((double)br - cyb)), ha);
                 t.off *= W2;
-                yt[j - wa] = t;
+                yt[r] = t;
             }
         }
         __syncthreads();
         if (active) {
-            const Tap tx = xt[c];
+            const PTap tx = xt[c];
 #pragma unroll
             for (int k = 0; k < KR; ++k) {
                 const int r = row0 + rp + R * k;
                 if (r < ha) {
-                    const Tap ty = yt[r];
+                    const PTap ty = yt[r];
                     const int base = ty.off + tx.off;
                     const float v00 = slice[base], v01 = slice[base + 1];
                     const float v10 = slice[base + W2], v11 = slice[base + W2 + 1];
@@ -440,11 +485,11 @@ __global__ void refocus_reduce_kernel(const float* __restrict__ partial, int n_r
 
 template <typename K>
 cudaError_t set_smem_attr(K kernel, int slot) {
-    static bool done[32][64] = {};
+    static bool done[64][64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (dev < 0 || dev >= 64 || slot < 0 || slot >= 64) return cudaErrorInvalidValue;
     if (!done[slot][dev]) {
         e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024);
         if (e != cudaSuccess) return e;
@@ -453,16 +498,56 @@ cudaError_t set_smem_attr(K kernel, int slot) {
     return cudaSuccess;
 }
 
-template <int KR, int PB, bool kTma, int kStages, int kMinBlocks, int kWA = 0, int kHA = 0>
-cudaError_t launch_sep(const CUtensorMap* tm, const float* g, const RefocusGeom& geo, const PlaneBlock& pl,
-                       float* partial, size_t smem, cudaStream_t st, int slot) {
-    auto kern = refocus_sep_kernel<KR, PB, kWA, kHA, kTma, kStages, kMinBlocks>;
+constexpr size_t kSmemCap = 220 * 1024;
+
+// 1-D staging: 256-element boxes covering the slice from the 16-byte boundary
+// at or below its start (and one value past it when wa == 1).
+int pipe_boxes(int ha, int wa) {
+    const int64_t ma = (int64_t)ha * wa;
+    const int64_t lead = (ma % 4 == 0) ? 0 : 3;
+    const int64_t tail = (wa == 1) ? 1 : 0;
+    return (int)((lead + ma + tail + kBox - 1) / kBox);
+}
+
+struct PipeCfg {
+    bool pad;      // 2-D padded staging (else 1-D boxes)
+    bool table;    // per-plane-block x-tap table in shared memory
+    int pb, nstep, stages, kr;
+};
+
+bool pad_staging(int ha, int wa) { return wa % 4 == 0 && wa + kPadL + kPadR <= 256 && ha <= 256; }
+
+int slice_floats(int ha, int wa, bool pad) {
+    return pad ? ((ha * (wa + kPadL + kPadR) + 31) & ~31) : pipe_boxes(ha, wa) * kBox;
+}
+
+size_t pipe_smem(int ha, int wa, int wb, const PipeCfg& c) {
+    size_t b = 128 + sizeof(float) * (size_t)c.stages * slice_floats(ha, wa, c.pad);
+    if (c.table) b += (c.pad ? sizeof(XTab<true>) : sizeof(XTab<false>)) * (size_t)c.pb * wb * wa;
+    b += (sizeof(PTap) * (size_t)c.pb * ha + 15) & ~(size_t)15;
+    b += sizeof(long long) * (size_t)c.pb * (wa + wb);
+    b += sizeof(float) * (size_t)c.pb * (ha + 2 * kUPad) * wa;
+    return b;
+}
+
+int rows_per_thread(int ha, int wa) {
+    const int R = kThreads / wa;
+    return R > 0 ? (ha + R - 1) / R : 1 << 30;
+}
+
+int pow2_at_least(int v, int lo) {
+    int k = lo;
+    while (k < v) k *= 2;
+    return k;
+}
+
+template <int KR, int PB, int NSTEP, int kStages, bool kPad, bool kTable, int kWA = 0, int kHA = 0>
+cudaError_t launch_pipe(const CUtensorMap* tm, const RefocusGeom& geo, const PlaneBlock& pl, float* partial,
+                        size_t smem, int grid, cudaStream_t st, int slot) {
+    auto kern = refocus_pipe_kernel<KR, PB, NSTEP, kStages, kPad, kTable, kWA, kHA>;
     cudaError_t e = set_smem_attr(kern, slot);
     if (e != cudaSuccess) return e;
-    CUtensorMap dummy;
-    std::memset(&dummy, 0, sizeof(dummy));
-    const int pblocks = (geo.n_planes + PB - 1) / PB;
-    kern<<<dim3(geo.hb, pblocks), kThreads, smem, st>>>(tm ? *tm : dummy, g, geo, pl, partial);
+    kern<<<grid, kThreads, smem, st>>>(*tm, geo, pl, partial);
     return cudaGetLastError();
 }
 
@@ -472,72 +557,85 @@ cudaError_t launch_direct(const float* g, const RefocusGeom& geo, const PlaneBlo
     cudaError_t e = set_smem_attr(refocus_direct_kernel<KR>, slot);
     if (e != cudaSuccess) return e;
     dim3 grid((unsigned)geo.n_ranges, (unsigned)geo.n_planes, (unsigned)zchunks);
-    refocus_direct_kernel<KR><<<grid, kThreads, smem, st>>>(g, geo, pl, partial);
+    refocus_direct_kernel<KR><<<grid, kDirectThreads, smem, st>>>(g, geo, pl, partial);
     return cudaGetLastError();
 }
 
-int kr_for(int ha, int wa, int cap) {
-    const int R = kThreads / wa;
-    int kr = 1;
-    while (kr < cap && R * kr < ha) kr *= 2;
-    return kr;
-}
-
-}  // namespace
-
-// Separable-kernel variant of an image shape.
-struct SepVariant {
-    bool ok;
-    bool tma;       // TMA staging (width a multiple of 4, box sides <= 256)
-    bool large;     // 1 plane per CTA, up to 32 rows per thread, 1 CTA per SM
-    int kr;         // rows per thread (power of two)
-    int stages;
+// Kernel choice for an image shape.
+struct RefocusVariant {
+    bool pipe;     // pipelined kernel (else direct)
+    PipeCfg cfg;
 };
 
-static size_t sep_smem_for(int ha, int wa, int pb, int stages) {
-    const size_t slice_f = ((size_t)ha * (wa + kPadL + kPadR) + 31) & ~(size_t)31;
-    return 128 + sizeof(float) * (stages * slice_f + (size_t)pb * (ha + 2) * wa) +
-           sizeof(Tap) * (stages * (size_t)pb * wa + (size_t)pb * ha);
-}
-
-static SepVariant sep_variant(int ha, int wa) {
-    SepVariant v{false, false, false, 1, 3};
+RefocusVariant refocus_variant(int ha, int wa, int wb) {
+    RefocusVariant v{false, {false, false, 1, 1, 2, 1}};
     if (wa > kThreads) return v;
-    v.tma = (wa % 4 == 0) && (wa + kPadL + kPadR <= 256) && ha <= 256;
-    const int R = kThreads / wa;
-    const int rows = (ha + R - 1) / R;
-    if (rows <= 8 && sep_smem_for(ha, wa, kSepPlanes, 3) <= 112 * 1024) {
-        v.ok = true;
-        v.kr = kr_for(ha, wa, 8);
-        v.stages = 3;
-        return v;
+    const bool pad = pad_staging(ha, wa);
+    const int rows = rows_per_thread(ha, wa);
+    if (rows <= 8) {   // four planes per unit, two slices per step, x-tap table
+        const PipeCfg c{pad, true, 4, 2, 4, pow2_at_least(rows, 1)};
+        if (pipe_smem(ha, wa, wb, c) <= kSmemCap) return {true, c};
     }
-    if (rows <= 32) {
-        v.large = true;
-        v.kr = rows <= 16 ? 16 : 32;
-        v.stages = sep_smem_for(ha, wa, 1, 3) <= 220 * 1024 ? 3 : 2;
-        v.ok = sep_smem_for(ha, wa, 1, v.stages) <= 220 * 1024;
+    if (rows <= 32) {  // one plane per unit, one slice per step, taps computed in place
+        PipeCfg c{pad, false, 1, 1, 3, pow2_at_least(rows, 8)};
+        if (pipe_smem(ha, wa, wb, c) > kSmemCap) c.stages = 2;
+        if (pipe_smem(ha, wa, wb, c) <= kSmemCap) return {true, c};
     }
     return v;
 }
 
-bool refocus_separable(int ha, int wa) { return sep_variant(ha, wa).ok; }
-
-size_t refocus_smem_bytes(int ha, int wa) {
-    const SepVariant v = sep_variant(ha, wa);
-    if (v.ok) return sep_smem_for(ha, wa, v.large ? 1 : kSepPlanes, v.stages);
-    return sizeof(float) * (size_t)(ha + 2) * (wa + 2) + sizeof(Tap) * ((size_t)wa + ha);
+template <bool kPad>
+cudaError_t launch_pipe_cfg(const PipeCfg& c, const CUtensorMap* tm, const RefocusGeom& geo, const PlaneBlock& pl,
+                            float* partial, size_t smem, int grid, cudaStream_t st) {
+    const int base = kPad ? 0 : 20;
+    if (c.table) {
+        if constexpr (kPad) {   // compile-time shapes of the common square detector sizes
+            if (geo.wa == 64 && geo.ha == 64)
+                return launch_pipe<8, 4, 2, 4, true, true, 64, 64>(tm, geo, pl, partial, smem, grid, st, base + 0);
+            if (geo.wa == 32 && geo.ha == 32)
+                return launch_pipe<2, 4, 2, 4, true, true, 32, 32>(tm, geo, pl, partial, smem, grid, st, base + 1);
+        }
+        switch (c.kr) {
+            case 1: return launch_pipe<1, 4, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 2);
+            case 2: return launch_pipe<2, 4, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 3);
+            case 4: return launch_pipe<4, 4, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 4);
+            default: return launch_pipe<8, 4, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 5);
+        }
+    }
+    if (c.stages == 3) {
+        switch (c.kr) {
+            case 8: return launch_pipe<8, 1, 1, 3, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 6);
+            case 16: return launch_pipe<16, 1, 1, 3, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 7);
+            default: return launch_pipe<32, 1, 1, 3, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 8);
+        }
+    }
+    switch (c.kr) {
+        case 8: return launch_pipe<8, 1, 1, 2, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 9);
+        case 16: return launch_pipe<16, 1, 1, 2, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 10);
+        default: return launch_pipe<32, 1, 1, 2, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 11);
+    }
 }
 
-bool refocus_uses_tma(int ha, int wa) {
-    const SepVariant v = sep_variant(ha, wa);
-    return v.ok && v.tma;
+}  // namespace
+
+bool refocus_pipelined(int ha, int wa, int wb) { return refocus_variant(ha, wa, wb).pipe; }
+
+int refocus_staging(int ha, int wa, int wb) {
+    const RefocusVariant v = refocus_variant(ha, wa, wb);
+    if (!v.pipe) return 0;
+    return v.cfg.pad ? 2 : 1;
+}
+
+size_t refocus_smem_bytes(int ha, int wa, int wb) {
+    const RefocusVariant v = refocus_variant(ha, wa, wb);
+    if (v.pipe) return pipe_smem(ha, wa, wb, v.cfg);
+    return sizeof(float) * (size_t)(ha + 2 * kUPad) * (wa + 2 * kUPad) + sizeof(PTap) * ((size_t)wa + ha);
 }
 
 int refocus_ranges(int ha, int wa, int hb, int wb, int n_planes, int sm_count) {
-    // separable kernel: one range per angular row; direct kernel: ranges of
+    // pipelined kernel: one range per angular row; direct kernel: ranges of
     // angular pixels sized to fill the GPU
-    if (refocus_separable(ha, wa)) return hb;
+    if (refocus_pipelined(ha, wa, wb)) return hb;
     const int units = hb * wb;
     int target = (4 * sm_count + n_planes - 1) / (n_planes > 0 ? n_planes : 1);
     if (target < 1) target = 1;
@@ -547,61 +645,34 @@ int refocus_ranges(int ha, int wa, int hb, int wb, int n_planes, int sm_count) {
 }
 
 int refocus_range_size(int ha, int wa, int hb, int wb, int n_ranges) {
-    if (refocus_separable(ha, wa)) return 1;
+    if (refocus_pipelined(ha, wa, wb)) return 1;
     return (hb * wb + n_ranges - 1) / n_ranges;
 }
 
-cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const RefocusGeom& geo,
-                           const PlaneBlock& pl, float* partial, cudaStream_t st) {
-    const size_t smem = refocus_smem_bytes(geo.ha, geo.wa);
-    const SepVariant v = sep_variant(geo.ha, geo.wa);
-    if (v.ok) {
-        if (v.tma && tm == nullptr) return cudaErrorInvalidValue;
-        const float* g = gamma_f32;
-        if (!v.large) {
-            if (v.tma) {
-                // compile-time shapes of the common square detector sizes
-                if (geo.wa == 64 && geo.ha == 64)
-                    return launch_sep<8, 2, true, 3, 2, 64, 64>(tm, g, geo, pl, partial, smem, st, 10);
-                if (geo.wa == 32 && geo.ha == 32)
-                    return launch_sep<2, 2, true, 3, 2, 32, 32>(tm, g, geo, pl, partial, smem, st, 11);
-                switch (v.kr) {
-                    case 1: return launch_sep<1, 2, true, 3, 2>(tm, g, geo, pl, partial, smem, st, 0);
-                    case 2: return launch_sep<2, 2, true, 3, 2>(tm, g, geo, pl, partial, smem, st, 1);
-                    case 4: return launch_sep<4, 2, true, 3, 2>(tm, g, geo, pl, partial, smem, st, 2);
-                    default: return launch_sep<8, 2, true, 3, 2>(tm, g, geo, pl, partial, smem, st, 3);
-                }
-            }
-            switch (v.kr) {
-                case 1: return launch_sep<1, 2, false, 3, 2>(nullptr, g, geo, pl, partial, smem, st, 4);
-                case 2: return launch_sep<2, 2, false, 3, 2>(nullptr, g, geo, pl, partial, smem, st, 5);
-                case 4: return launch_sep<4, 2, false, 3, 2>(nullptr, g, geo, pl, partial, smem, st, 6);
-                default: return launch_sep<8, 2, false, 3, 2>(nullptr, g, geo, pl, partial, smem, st, 7);
-            }
-        }
-        const CUtensorMap* t = v.tma ? tm : nullptr;
-        if (v.stages == 3) {
-            if (v.kr == 16)
-                return v.tma ? launch_sep<16, 1, true, 3, 1>(t, g, geo, pl, partial, smem, st, 12)
-                             : launch_sep<16, 1, false, 3, 1>(t, g, geo, pl, partial, smem, st, 13);
-            return v.tma ? launch_sep<32, 1, true, 3, 1>(t, g, geo, pl, partial, smem, st, 14)
-                         : launch_sep<32, 1, false, 3, 1>(t, g, geo, pl, partial, smem, st, 15);
-        }
-        if (v.kr == 16)
-            return v.tma ? launch_sep<16, 1, true, 2, 1>(t, g, geo, pl, partial, smem, st, 16)
-                         : launch_sep<16, 1, false, 2, 1>(t, g, geo, pl, partial, smem, st, 17);
-        return v.tma ? launch_sep<32, 1, true, 2, 1>(t, g, geo, pl, partial, smem, st, 18)
-                     : launch_sep<32, 1, false, 2, 1>(t, g, geo, pl, partial, smem, st, 19);
+cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const RefocusGeom& geo_in,
+                           const PlaneBlock& pl, float* partial, int sm_count, cudaStream_t st) {
+    const size_t smem = refocus_smem_bytes(geo_in.ha, geo_in.wa, geo_in.wb);
+    const RefocusVariant v = refocus_variant(geo_in.ha, geo_in.wa, geo_in.wb);
+    RefocusGeom geo = geo_in;
+    if (v.pipe) {
+        if (tm == nullptr) return cudaErrorInvalidValue;
+        geo.boxes = pipe_boxes(geo.ha, geo.wa);
+        geo.slice_f = slice_floats(geo.ha, geo.wa, v.cfg.pad);
+        const int units = geo.hb * ((geo.n_planes + v.cfg.pb - 1) / v.cfg.pb);
+        const int grid = units < sm_count ? units : sm_count;
+        return v.cfg.pad ? launch_pipe_cfg<true>(v.cfg, tm, geo, pl, partial, smem, grid, st)
+                         : launch_pipe_cfg<false>(v.cfg, tm, geo, pl, partial, smem, grid, st);
     }
-    const int R = kThreads / geo.wa;
-    const int kr = kr_for(geo.ha, geo.wa, 16);
+    const int R = kDirectThreads / geo.wa;
+    int kr = 1;
+    while (kr < 16 && R * kr < geo.ha) kr *= 2;
     const int zchunks = (geo.ha + R * kr - 1) / (R * kr);
     switch (kr) {
-        case 1: return launch_direct<1>(gamma_f32, geo, pl, partial, zchunks, smem, st, 5 + 20);
-        case 2: return launch_direct<2>(gamma_f32, geo, pl, partial, zchunks, smem, st, 6 + 20);
-        case 4: return launch_direct<4>(gamma_f32, geo, pl, partial, zchunks, smem, st, 7 + 20);
-        case 8: return launch_direct<8>(gamma_f32, geo, pl, partial, zchunks, smem, st, 8 + 20);
-        default: return launch_direct<16>(gamma_f32, geo, pl, partial, zchunks, smem, st, 9 + 20);
+        case 1: return launch_direct<1>(gamma_f32, geo, pl, partial, zchunks, smem, st, 40);
+        case 2: return launch_direct<2>(gamma_f32, geo, pl, partial, zchunks, smem, st, 41);
+        case 4: return launch_direct<4>(gamma_f32, geo, pl, partial, zchunks, smem, st, 42);
+        case 8: return launch_direct<8>(gamma_f32, geo, pl, partial, zchunks, smem, st, 43);
+        default: return launch_direct<16>(gamma_f32, geo, pl, partial, zchunks, smem, st, 44);
     }
 }
 
