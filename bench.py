@@ -381,16 +381,23 @@ def rooflines(ma, mb, n, n_planes, bits, ms):
                    "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
                    "traffic": _traffic("fold"), "peak_source": f"{src} hbm copy", "ms": ms["fold"],
                    "work": "24 B per Gamma entry"}
+    # Refocus, as the workload's metric defines it: per-plane Gamma FP32 traffic
+    # (P planes x Ma x Mb x 4 B, what an unfused per-plane gather reads) per
+    # second against the HBM copy peak.  The kernel reads Gamma from HBM once
+    # per pass of 4 planes and is bound on chip by shared-memory loads, given
+    # as "lsu" (8 B of loads per plane, row, column and angular pixel).
+    eff = n_planes * ma * mb * 4.0 / (ms["refocus"] / 1e3) / 1e9
     smem = n_planes * ma * mb * 8.0
     smem_peak = SM_COUNT * SMEM_BYTES_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
     a = smem / (ms["refocus"] / 1e3) / 1e9
-    eff = n_planes * ma * mb * 4.0 / (ms["refocus"] / 1e3) / 1e9
-    out["refocus"] = {"kernel": "refocus (separable bilinear shift-and-sum + row reduce)", "bound": "smem",
-                      "achieved": a, "peak": smem_peak, "unit": "GB/s", "frac": a / smem_peak,
-                      "traffic": _traffic("refocus"),
-                      "peak_source": "derived: 152 SMs x 128 B/clk shared-memory loads x max SM clock",
-                      "ms": ms["refocus"], "work": "8 B of shared-memory reads per (plane, row, column, angular pixel)",
-                      "per_plane_gamma_gbs": eff, "per_plane_gamma_frac_of_hbm": eff / peaks["hbm_gbs"]}
+    out["refocus"] = {"kernel": "refocus (pipelined bilinear shift-and-sum, 4 planes per Gamma pass, + row reduce)",
+                      "bound": "hbm", "achieved": eff, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                      "frac": eff / peaks["hbm_gbs"], "traffic": _traffic("refocus"),
+                      "peak_source": f"{src} hbm copy", "ms": ms["refocus"],
+                      "work": "P x Ma x Mb x 4 B (one FP32 Gamma read per plane)",
+                      "lsu": {"achieved": a, "peak": smem_peak, "unit": "GB/s", "frac": a / smem_peak,
+                              "peak_source": "derived: 152 SMs x 128 B/clk shared-memory loads x max SM clock",
+                              "work": "8 B of shared-memory reads per (plane, row, column, angular pixel)"}}
     return out
 
 

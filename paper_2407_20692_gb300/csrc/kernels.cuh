@@ -91,6 +91,7 @@ struct RefocusGeom {
     int32_t total_planes;
     int32_t boxes;           // 256-element boxes per slice, 1-D staging (set by launch_refocus)
     int32_t slice_f;         // floats per shared-memory stage buffer (set by launch_refocus)
+    int32_t stages;          // shared-memory stage buffers (set by launch_refocus)
     unsigned int* status;           // device status word (bounded waits)
     unsigned long long timeout_ns;
 };

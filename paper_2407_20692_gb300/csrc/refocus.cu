@@ -133,6 +133,7 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* m, uin
 // that never arrives stops every thread at that same slice, so no barrier is
 // left half-entered.
 constexpr int kThreads = 512;
+constexpr int kMaxStages = 4;
 constexpr int kPadL = 4;         // zero columns left of a 2-D staged row (TMA x start -4)
 constexpr int kPadR = 4;
 
@@ -175,13 +176,13 @@ __device__ __forceinline__ void read_xtab(const XTab<kPad>* e, int& off, float& 
     }
 }
 
-template <int KR, int PB, int NSTEP, int kStages, bool kPad, bool kTable, int kWA, int kHA>
+template <int KR, int PB, int NSTEP, int kST, bool kPad, bool kTable, int kWA, int kHA>
 __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_constant__ CUtensorMap tm,
                                                                    const RefocusGeom geo, const PlaneBlock pl,
                                                                    float* __restrict__ partial) {
     static_assert(NSTEP == 1 || NSTEP == 2, "one or two slices per step");
-    static_assert(kStages >= NSTEP + 1, "a step must not hold every stage");
     constexpr int NW = kThreads / 32;
+    const int kStages = kST ? kST : geo.stages;        // 2..kMaxStages, > NSTEP
     extern __shared__ __align__(128) float sm_raw[];
     const int ha = kWA ? kHA : geo.ha, wa = kWA ? kWA : geo.wa, hb = geo.hb, wb = geo.wb;
     const int Ma = ha * wa;
@@ -200,8 +201,8 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
     long long* const bx = reinterpret_cast<long long*>(p);        // [PB][wb]
     p += sizeof(long long) * (size_t)PB * wb;
     float* const U = reinterpret_cast<float*>(p);                 // [PB][ha + 2*kUPad][wa]
-    __shared__ __align__(8) uint64_t full[kStages];
-    __shared__ unsigned int relcnt[kStages];
+    __shared__ __align__(8) uint64_t full[kMaxStages];
+    __shared__ unsigned int relcnt[kMaxStages];
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int UH = ha + 2 * kUPad;
@@ -255,7 +256,9 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
     const bool active = kFull || rp < R;
     const int nk = kFull ? KR : (active ? max(0, min(KR, (ha - rp + R - 1) / R)) : 0);
     const int rstep = R * WS;
-    uint32_t g = 0;
+    uint32_t g = 0;          // slices of this CTA consumed so far
+    int cs = 0;              // stage of slice g
+    uint32_t cp = 0;         // phase parity of slice g in its stage
     int cur_pb = -1;
     for (int k = 0; k < n_mine; ++k) {
         const int u = blockIdx.x + k * gridDim.x;
@@ -281,6 +284,8 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
             }
             cur_pb = pblk;
         }
+        // Two slices per step: the step's sum (four fused multiply-adds) is
+        // Kahan-added into U.  One slice per step: each slice's sum is.
         float Ua[PB][KR], Uc[PB][KR];
 #pragma unroll
         for (int j = 0; j < PB; ++j)
@@ -288,12 +293,12 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
             for (int kk = 0; kk < KR; ++kk) Ua[j][kk] = Uc[j][kk] = 0.0f;
         for (int bc0 = 0; bc0 < wb; bc0 += NSTEP) {
             const int nsl = min(NSTEP, wb - bc0);
-            bool ok = true;
-#pragma unroll
-            for (int i = 0; i < NSTEP; ++i)
-                if (i < nsl)
-                    ok = ok && mbar_wait_bounded(&full[(g + i) % kStages], ((g + i) / kStages) & 1u, nullptr,
-                                                 geo.status, geo.timeout_ns);
+            // stages and phase parities of this step's slices g and g + 1
+            const int s0 = cs, s1 = cs + 1 == kStages ? 0 : cs + 1;
+            const uint32_t p1 = s1 == 0 ? cp ^ 1u : cp;
+            bool ok = mbar_wait_bounded(&full[s0], cp, nullptr, geo.status, geo.timeout_ns);
+            if (NSTEP == 2 && nsl == 2)
+                ok = ok && mbar_wait_bounded(&full[s1], p1, nullptr, geo.status, geo.timeout_ns);
             if (!ok) {   // every thread stops at this same slice
                 if (tid == 0)
                     for (uint32_t q = g; q < g + kStages && q < total_sl; ++q)
@@ -301,7 +306,6 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
                 return;
             }
             if (nk > 0) {
-                const int s0 = (int)(g % kStages), s1 = (int)((g + 1) % kStages);
                 // 1-D staging: the slice starts sh elements into its buffer
                 const int sh0 = kPad ? 0 : (int)(((long long)(br * wb + bc0) * Ma) & 3);
                 const int sh1 = kPad ? 0 : (int)(((long long)(br * wb + bc0 + 1) * Ma) & 3);
@@ -331,8 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
                             if (kFull || kk < nk) {
                                 const int o = kWA ? kk * kRStep : kk * rstep;
                                 float t = __fmaf_rn(a1, qa[o + 1], a0 * qa[o]);
-                                if (NSTEP == 2 && nsl == 2)
-                                    t = __fmaf_rn(b1, qb[o + 1], __fmaf_rn(b0, qb[o], t));
+                                if (NSTEP == 2 && nsl == 2) t = __fmaf_rn(b1, qb[o + 1], __fmaf_rn(b0, qb[o], t));
                                 kahan_add(Ua[j][kk], Uc[j][kk], t);
                             }
                         }
@@ -344,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
             if (lane == 0) {
                 for (int i = 0; i < nsl; ++i) {
                     const uint32_t q = g + i;
-                    const int s = (int)(q % kStages);
+                    const int s = i == 0 ? s0 : s1;
                     __threadfence_block();
                     if (atomicAdd(&relcnt[s], 1u) == NW - 1) {
                         relcnt[s] = 0;
@@ -357,6 +360,12 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
                 }
             }
             g += nsl;
+            cs = nsl == 2 ? s1 : s0;
+            cp = nsl == 2 ? p1 : cp;
+            if (++cs == kStages) {
+                cs = 0;
+                cp ^= 1u;
+            }
         }
 
         // y-interpolation of this angular row
@@ -478,7 +487,15 @@ __global__ void refocus_reduce_kernel(const float* __restrict__ partial, int n_r
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < per_range;
          i += (int64_t)gridDim.x * blockDim.x) {
         float acc = 0.0f, cmp = 0.0f;
-        for (int r = 0; r < n_ranges; ++r) kahan_add(acc, cmp, __ldg(partial + (int64_t)r * per_range + i));
+        int r = 0;
+        for (; r + 8 <= n_ranges; r += 8) {   // 8 loads in flight, then the adds in order
+            float v[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] = __ldg(partial + (int64_t)(r + k) * per_range + i);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) kahan_add(acc, cmp, v[k]);
+        }
+        for (; r < n_ranges; ++r) kahan_add(acc, cmp, __ldg(partial + (int64_t)r * per_range + i));
         out[i] = acc - cmp;
     }
 }
@@ -541,10 +558,10 @@ int pow2_at_least(int v, int lo) {
     return k;
 }
 
-template <int KR, int PB, int NSTEP, int kStages, bool kPad, bool kTable, int kWA = 0, int kHA = 0>
+template <int KR, int PB, int NSTEP, int kST, bool kPad, bool kTable, int kWA = 0, int kHA = 0>
 cudaError_t launch_pipe(const CUtensorMap* tm, const RefocusGeom& geo, const PlaneBlock& pl, float* partial,
                         size_t smem, int grid, cudaStream_t st, int slot) {
-    auto kern = refocus_pipe_kernel<KR, PB, NSTEP, kStages, kPad, kTable, kWA, kHA>;
+    auto kern = refocus_pipe_kernel<KR, PB, NSTEP, kST, kPad, kTable, kWA, kHA>;
     cudaError_t e = set_smem_attr(kern, slot);
     if (e != cudaSuccess) return e;
     kern<<<grid, kThreads, smem, st>>>(*tm, geo, pl, partial);
@@ -572,13 +589,21 @@ RefocusVariant refocus_variant(int ha, int wa, int wb) {
     if (wa > kThreads) return v;
     const bool pad = pad_staging(ha, wa);
     const int rows = rows_per_thread(ha, wa);
-    if (rows <= 8) {   // four planes per unit, two slices per step, x-tap table
-        const PipeCfg c{pad, true, 4, 2, 4, pow2_at_least(rows, 1)};
-        if (pipe_smem(ha, wa, wb, c) <= kSmemCap) return {true, c};
-    }
-    if (rows <= 32) {  // one plane per unit, one slice per step, taps computed in place
-        PipeCfg c{pad, false, 1, 1, 3, pow2_at_least(rows, 8)};
-        if (pipe_smem(ha, wa, wb, c) > kSmemCap) c.stages = 2;
+    // candidates in order of preference; the first whose rows per thread and
+    // shared memory fit is used
+    const int kr8 = rows <= 1 ? 1 : rows <= 2 ? 2 : 4;
+    const PipeCfg cands[] = {
+        {pad, true, 8, 2, 4, kr8},                                  // <= 4 rows: 8 planes per unit
+        {pad, true, 4, 2, 4, 8},                                    // <= 8 rows: 4 planes per unit
+        {pad, true, 2, 2, 4, 16}, {pad, false, 2, 2, 4, 16},        // <= 16 rows: 2 planes per unit
+        {pad, true, 2, 2, 3, 16}, {pad, false, 2, 2, 3, 16},
+        {pad, true, 1, 2, 4, 32}, {pad, false, 1, 2, 4, 32},        // <= 32 rows: 1 plane per unit
+        {pad, true, 1, 2, 3, 32}, {pad, false, 1, 2, 3, 32},
+        {pad, false, 1, 1, 2, 32},                                  // one slice per step, 2 stages
+    };
+    for (const PipeCfg& c : cands) {
+        if (rows > c.kr) continue;
+        if (c.pb == 8 && rows > 4) continue;
         if (pipe_smem(ha, wa, wb, c) <= kSmemCap) return {true, c};
     }
     return v;
@@ -588,32 +613,31 @@ template <bool kPad>
 cudaError_t launch_pipe_cfg(const PipeCfg& c, const CUtensorMap* tm, const RefocusGeom& geo, const PlaneBlock& pl,
                             float* partial, size_t smem, int grid, cudaStream_t st) {
     const int base = kPad ? 0 : 20;
-    if (c.table) {
-        if constexpr (kPad) {   // compile-time shapes of the common square detector sizes
-            if (geo.wa == 64 && geo.ha == 64)
-                return launch_pipe<8, 4, 2, 4, true, true, 64, 64>(tm, geo, pl, partial, smem, grid, st, base + 0);
+    if (c.pb == 8) {
+        if constexpr (kPad) {   // compile-time shape of a common square detector size
             if (geo.wa == 32 && geo.ha == 32)
-                return launch_pipe<2, 4, 2, 4, true, true, 32, 32>(tm, geo, pl, partial, smem, grid, st, base + 1);
+                return launch_pipe<2, 8, 2, 4, true, true, 32, 32>(tm, geo, pl, partial, smem, grid, st, base + 0);
         }
         switch (c.kr) {
-            case 1: return launch_pipe<1, 4, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 2);
-            case 2: return launch_pipe<2, 4, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 3);
-            case 4: return launch_pipe<4, 4, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 4);
-            default: return launch_pipe<8, 4, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 5);
+            case 1: return launch_pipe<1, 8, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 1);
+            case 2: return launch_pipe<2, 8, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 2);
+            default: return launch_pipe<4, 8, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 3);
         }
     }
-    if (c.stages == 3) {
-        switch (c.kr) {
-            case 8: return launch_pipe<8, 1, 1, 3, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 6);
-            case 16: return launch_pipe<16, 1, 1, 3, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 7);
-            default: return launch_pipe<32, 1, 1, 3, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 8);
+    if (c.pb == 4) {
+        if constexpr (kPad) {
+            if (geo.wa == 64 && geo.ha == 64)
+                return launch_pipe<8, 4, 2, 4, true, true, 64, 64>(tm, geo, pl, partial, smem, grid, st, base + 4);
         }
+        return launch_pipe<8, 4, 2, 4, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 5);
     }
-    switch (c.kr) {
-        case 8: return launch_pipe<8, 1, 1, 2, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 9);
-        case 16: return launch_pipe<16, 1, 1, 2, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 10);
-        default: return launch_pipe<32, 1, 1, 2, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 11);
-    }
+    if (c.pb == 2)
+        return c.table ? launch_pipe<16, 2, 2, 0, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 6)
+                       : launch_pipe<16, 2, 2, 0, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 7);
+    if (c.nstep == 2)
+        return c.table ? launch_pipe<32, 1, 2, 0, kPad, true>(tm, geo, pl, partial, smem, grid, st, base + 8)
+                       : launch_pipe<32, 1, 2, 0, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 9);
+    return launch_pipe<32, 1, 1, 2, kPad, false>(tm, geo, pl, partial, smem, grid, st, base + 10);
 }
 
 }  // namespace
@@ -658,6 +682,7 @@ cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const 
         if (tm == nullptr) return cudaErrorInvalidValue;
         geo.boxes = pipe_boxes(geo.ha, geo.wa);
         geo.slice_f = slice_floats(geo.ha, geo.wa, v.cfg.pad);
+        geo.stages = v.cfg.stages;
         const int units = geo.hb * ((geo.n_planes + v.cfg.pb - 1) / v.cfg.pb);
         const int grid = units < sm_count ? units : sm_count;
         return v.cfg.pad ? launch_pipe_cfg<true>(v.cfg, tm, geo, pl, partial, smem, grid, st)
