@@ -162,9 +162,9 @@ struct CorrPlan {
     bool bf16;                 // BF16 operands (any 8-bit input) or FP8 (both binary)
     int64_t Ma, Mb, n;
     int64_t kstride_bytes;     // operand row length in bytes (frames padded to the ingest tile)
-    int k_blocks, kb_per_chunk, kb_per_fold, n_chunks;
+    int k_blocks, kb_per_chunk, n_chunks;
     int block_n, tiles_m, tiles_n, n_units;
-    size_t off_a, off_b, off_part, ws_bytes;
+    size_t off_a, off_b, off_part, off_vmax, ws_bytes;
 };
 
 // split == 0: single correlation (more frame chunks when the tiles alone cannot
@@ -193,24 +193,21 @@ cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm
     p.tiles_m = (int)((p.Ma + 127) / 128);
     p.tiles_n = (int)((p.Mb + p.block_n - 1) / p.block_n);
     const int max_kb_chunk = kChunkFrames / sh.k_per_block;
-    p.kb_per_fold = p.bf16 ? 256 / sh.k_per_block : max_kb_chunk;
     const int64_t tiles = (int64_t)p.tiles_m * p.tiles_n;
     int n_chunks = (p.k_blocks + max_kb_chunk - 1) / max_kb_chunk;
     if (split >= 1) {
-        const int max_by_len = p.k_blocks / (p.bf16 ? p.kb_per_fold : 8) > 0
-                                   ? p.k_blocks / (p.bf16 ? p.kb_per_fold : 8) : 1;
+        const int max_by_len = p.k_blocks / 8 > 0 ? p.k_blocks / 8 : 1;
         n_chunks = n_chunks * split < max_by_len ? n_chunks * split : (max_by_len > n_chunks ? max_by_len : n_chunks);
     } else if (tiles < sm_count) {
         // small outputs: split the frames further so every SM gets work, but keep
-        // each chunk at least one exact-fold segment long
+        // each chunk at least 8 K blocks long
         int want = (int)(sm_count / tiles);
-        int max_by_len = p.k_blocks / (p.bf16 ? p.kb_per_fold : 8);
+        int max_by_len = p.k_blocks / 8;
         if (max_by_len < 1) max_by_len = 1;
         if (want > max_by_len) want = max_by_len;
         if (want > n_chunks) n_chunks = want;
     }
     p.kb_per_chunk = (p.k_blocks + n_chunks - 1) / n_chunks;
-    if (p.bf16) p.kb_per_chunk = (int)round_up((size_t)p.kb_per_chunk, (size_t)p.kb_per_fold);
     if (p.kb_per_chunk > max_kb_chunk) p.kb_per_chunk = max_kb_chunk;
     p.n_chunks = (p.k_blocks + p.kb_per_chunk - 1) / p.kb_per_chunk;
     const int64_t units = tiles * p.n_chunks;
@@ -219,24 +216,28 @@ cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm
     p.off_a = 0;
     p.off_b = round_up(p.off_a + (size_t)p.Ma * (size_t)p.kstride_bytes, 1024);
     p.off_part = round_up(p.off_b + (size_t)p.Mb * (size_t)p.kstride_bytes, 1024);
-    p.ws_bytes = round_up(p.off_part + (size_t)p.n_chunks * (size_t)p.Ma * (size_t)p.Mb * 4, 1024);
+    p.off_vmax = round_up(p.off_part + (size_t)p.n_chunks * (size_t)p.Ma * (size_t)p.Mb * 4, 256);
+    p.ws_bytes = round_up(p.off_vmax + 2 * sizeof(uint32_t), 1024);
     *pl = p;
     return CPI_OK;
 }
 
 cpi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CPI_OK : CPI_ERR_CUDA; }
 
-void fill_problem(const CorrPlan& pl, int32_t* part, int unit_begin, MomentsProblem* P) {
+
+// vmax: the ingest's value maxima (BF16 path), which set the exact FP32
+// segment length on the device.
+void fill_problem(const CorrPlan& pl, int32_t* part, int unit_begin, MomentsProblem* P, const uint32_t* vmax) {
     P->partial = part;
     P->M = (int32_t)pl.Ma;
     P->N = (int32_t)pl.Mb;
     P->k_blocks = pl.k_blocks;
     P->kb_per_chunk = pl.kb_per_chunk;
-    P->kb_per_fold = pl.kb_per_fold;
     P->n_chunks = pl.n_chunks;
     P->tiles_m = pl.tiles_m;
     P->tiles_n = pl.tiles_n;
     P->unit_begin = unit_begin;
+    P->vmax = pl.bf16 ? vmax : nullptr;
 }
 
 cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const cpi_frames* b,
@@ -246,14 +247,16 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
     uint8_t* op_a = w + pl.off_a;
     uint8_t* op_b = w + pl.off_b;
     int32_t* part = reinterpret_cast<int32_t*>(w + pl.off_part);
+    uint32_t* vmax = reinterpret_cast<uint32_t*>(w + pl.off_vmax);
     if (stage == CPI_STAGE_INGEST) {
         if (!accumulate) {
             cudaError_t e = cudaMemsetAsync(s_a, 0, (size_t)pl.Ma * 8, st);
             if (e == cudaSuccess) e = cudaMemsetAsync(s_b, 0, (size_t)pl.Mb * 8, st);
             if (e != cudaSuccess) return CPI_ERR_CUDA;
         }
+        if (pl.bf16 && cudaMemsetAsync(vmax, 0, 2 * sizeof(uint32_t), st) != cudaSuccess) return CPI_ERR_CUDA;
         return cuda_status(launch_ingest(pl.bf16, to_dev(a), to_dev(b), pl.n, pl.kstride_bytes,
-                                         op_a, op_b, s_a, s_b, st));
+                                         op_a, op_b, s_a, s_b, pl.bf16 ? vmax : nullptr, st));
     }
     if (stage == CPI_STAGE_MOMENTS) {
         CUtensorMap tm_a, tm_b;
@@ -264,13 +267,12 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
         std::memset(&L, 0, sizeof(L));
         L.map_a[0] = tm_a;
         L.map_b[0] = tm_b;
-        fill_problem(pl, part, 0, &L.prob[0]);
+        fill_problem(pl, part, 0, &L.prob[0], vmax);
         L.n_problems = 1;
         L.n_units = pl.n_units;
         L.status = dev->status;
         L.timeout_ns = g_timeout_ns;
-        const int grid = pl.n_units < dev->sm_count ? pl.n_units : dev->sm_count;
-        return cuda_status(launch_moments(pl.bf16, L, grid, st));
+        return cuda_status(launch_moments(pl.bf16, L, dev->sm_count, st));
     }
     if (stage == CPI_STAGE_FOLD) {
         return cuda_status(launch_fold(part, pl.n_chunks, pl.Ma, pl.Mb, s_ab, accumulate, 1, s_a,
@@ -427,9 +429,10 @@ cpi_status launch_batch_moments(const cpi_batch_item* items, const BatchPlan& bp
                                 DeviceInfo* dev, cudaStream_t st) {
     std::unique_ptr<MomentsLaunch<kMaxGroup>> L(new MomentsLaunch<kMaxGroup>);
     for (int kind = 0; kind < 2; ++kind) {
+        const bool bf16 = kind == 1;
         std::vector<int> idx;
         for (int i = 0; i < (int)bp.it.size(); ++i)
-            if ((int)bp.it[i].pl.bf16 == kind) idx.push_back(i);
+            if (bp.it[i].pl.bf16 == bf16) idx.push_back(i);
         std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
             const CorrPlan &p = bp.it[x].pl, &q = bp.it[y].pl;
             if (p.kb_per_chunk != q.kb_per_chunk) return p.kb_per_chunk > q.kb_per_chunk;
@@ -437,7 +440,8 @@ cpi_status launch_batch_moments(const cpi_batch_item* items, const BatchPlan& bp
         });
         for (size_t g0 = 0; g0 < idx.size(); g0 += kMaxGroup) {
             std::memset(L.get(), 0, sizeof(*L));
-            int units = 0, np = 0;
+            int64_t units = 0;
+            int np = 0;
             for (size_t g = g0; g < idx.size() && g < g0 + kMaxGroup; ++g, ++np) {
                 const BatchItemPlan& ip = bp.it[idx[g]];
                 uint8_t* w = ws + ip.ws_off;
@@ -446,16 +450,16 @@ cpi_status launch_batch_moments(const cpi_batch_item* items, const BatchPlan& bp
                     !make_operand_map(&L->map_b[np], w + ip.pl.off_b, ip.pl.bf16, ip.pl.Mb,
                                       ip.pl.kstride_bytes, ip.pl.block_n))
                     return CPI_ERR_CUDA;
-                fill_problem(ip.pl, reinterpret_cast<int32_t*>(w + ip.pl.off_part), units, &L->prob[np]);
-                if ((int64_t)units + ip.pl.n_units > 0x7fffffff) return CPI_ERR_UNSUPPORTED;
+                fill_problem(ip.pl, reinterpret_cast<int32_t*>(w + ip.pl.off_part), (int)units, &L->prob[np],
+                             reinterpret_cast<const uint32_t*>(w + ip.pl.off_vmax));
                 units += ip.pl.n_units;
+                if (units > 0x7fffffff) return CPI_ERR_UNSUPPORTED;
             }
             L->n_problems = np;
-            L->n_units = units;
+            L->n_units = (int)units;
             L->status = dev->status;
             L->timeout_ns = g_timeout_ns;
-            const int grid = units < dev->sm_count ? units : dev->sm_count;
-            if (launch_moments_group(kind == 1, *L, grid, st) != cudaSuccess) return CPI_ERR_CUDA;
+            if (launch_moments_group(bf16, *L, dev->sm_count, st) != cudaSuccess) return CPI_ERR_CUDA;
         }
     }
     (void)items;
@@ -558,6 +562,13 @@ cpi_status tuned_split(const cpi_batch_item* items, int n, uint8_t* ws, DeviceIn
     for (int c = 0; c < 3 && s == CPI_OK; ++c) {
         BatchPlan bp;
         s = make_batch_plan(items, n, dev->sm_count, kSplitCandidates[c], &bp);
+        if (s != CPI_OK) break;
+        // real operands and value maxima in this candidate's layout, so that the
+        // timed launches run the GEMM variant the batch will run
+        for (int i = 0; i < n && s == CPI_OK; ++i)
+            s = run_stage(CPI_STAGE_INGEST, bp.it[i].pl, &items[i].a, &items[i].b, 0, items[i].s_ab,
+                          items[i].s_a, items[i].s_b, items[i].gamma, items[i].gamma_f32,
+                          ws + bp.it[i].ws_off, dev, st);
         if (s != CPI_OK) break;
         s = launch_batch_moments(items, bp, ws, dev, st);                 // warm-up
         if (s != CPI_OK) break;

@@ -27,7 +27,7 @@ template <bool kBf16>
 __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, int64_t n_frames,
                                                      int64_t kstride_bytes, uint8_t* op_a,
                                                      uint8_t* op_b, int64_t* s_a, int64_t* s_b,
-                                                     int tiles_a) {
+                                                     int tiles_a, uint32_t* vmax) {
     constexpr int kFramesPerWarp = kBf16 ? 16 : 32;   // 32 operand bytes per pixel per warp
     const bool is_a = (int)blockIdx.x < tiles_a;
     const FramesDev d = is_a ? A : B;
@@ -39,6 +39,7 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
 
     __shared__ __align__(16) uint8_t tile_s[kIngestPixels][kIngestRowBytes + 16];
     __shared__ long long part[8][32];
+    __shared__ uint32_t wmax[8];
 
     const int64_t p = (int64_t)tile * kIngestPixels + lane;
     const bool valid = p < M;
@@ -54,6 +55,7 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
     const int64_t f0 = (int64_t)blockIdx.y * (kFramesPerWarp * 8) + warp * kFramesPerWarp;
     long long sum = 0;
     uint32_t w[8];
+    uint32_t mx = 0;
     if constexpr (kBf16) {
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
@@ -62,6 +64,7 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
             if (valid && f < n_frames) lo = load_pixel(d, base, sh, f);
             if (valid && f + 1 < n_frames) hi = load_pixel(d, base, sh, f + 1);
             sum += lo + hi;
+            mx = max(mx, max(lo, hi));
             const uint32_t blo = __bfloat16_as_ushort(__float2bfloat16_rn((float)lo));
             const uint32_t bhi = __bfloat16_as_ushort(__float2bfloat16_rn((float)hi));
             w[j] = blo | (bhi << 16);
@@ -85,7 +88,19 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
     dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
     dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
     part[warp][lane] = sum;
+    if constexpr (kBf16) {
+        mx = __reduce_max_sync(0xffffffffu, mx);
+        if (lane == 0) wmax[warp] = mx;
+    }
     __syncthreads();
+    if (kBf16 && vmax != nullptr && threadIdx.x == 0) {
+        uint32_t m = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) m = max(m, wmax[k]);
+        uint32_t* slot = vmax + (is_a ? 0 : 1);
+        // read first: the atomic is needed only while the recorded maximum grows
+        if (m > *reinterpret_cast<volatile uint32_t*>(slot)) atomicMax(slot, m);
+    }
 
     // 32 rows x 256 bytes = 512 chunks of 16 bytes; consecutive threads write
     // consecutive chunks of one operand row.
@@ -232,7 +247,7 @@ static bool bits_fast_ok(const FramesDev& d) {
 }
 cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int64_t n_frames,
                           int64_t kstride_bytes, uint8_t* op_a, uint8_t* op_b, int64_t* s_a,
-                          int64_t* s_b, cudaStream_t st) {
+                          int64_t* s_b, uint32_t* vmax, cudaStream_t st) {
     const int64_t Ma = (int64_t)a.height * a.width, Mb = (int64_t)b.height * b.width;
     const int tiles_a = (int)((Ma + kIngestPixels - 1) / kIngestPixels);
     const int tiles_b = (int)((Mb + kIngestPixels - 1) / kIngestPixels);
@@ -251,12 +266,12 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
                 ingest_kernel<true><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes,
                                                           op_a + t0 * kIngestRowBytes,
                                                           op_b + t0 * kIngestRowBytes, s_a, s_b,
-                                                          tiles_a);
+                                                          tiles_a, vmax);
             else
                 ingest_kernel<false><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes,
                                                            op_a + t0 * kIngestRowBytes,
                                                            op_b + t0 * kIngestRowBytes, s_a, s_b,
-                                                           tiles_a);
+                                                           tiles_a, nullptr);
         }
         return cudaGetLastError();
     }
@@ -270,10 +285,10 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
     }
     if (bf16)
         ingest_kernel<true><<<grid, 256, 0, st>>>(a, b, n_frames, kstride_bytes, op_a, op_b, s_a,
-                                                  s_b, tiles_a);
+                                                  s_b, tiles_a, vmax);
     else
         ingest_kernel<false><<<grid, 256, 0, st>>>(a, b, n_frames, kstride_bytes, op_a, op_b, s_a,
-                                                   s_b, tiles_a);
+                                                   s_b, tiles_a, nullptr);
     return cudaGetLastError();
 }
 

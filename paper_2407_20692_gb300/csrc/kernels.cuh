@@ -28,9 +28,11 @@ constexpr int kIngestPixels = 32;                 // pixels per CTA
 constexpr int kIngestRowBytes = 256;              // operand bytes per pixel per CTA
 inline int ingest_frames_per_cta(bool bf16) { return bf16 ? 128 : 256; }
 
+// vmax (BF16 path, may be null): the largest A and B value seen is raised into
+// vmax[0] and vmax[1] (the caller zeroes them first).
 cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int64_t n_frames,
                           int64_t kstride_bytes, uint8_t* op_a, uint8_t* op_b, int64_t* s_a,
-                          int64_t* s_b, cudaStream_t st);
+                          int64_t* s_b, uint32_t* vmax, cudaStream_t st);
 
 // ------------------------------------------------------------------ moments
 // One raw-moment problem: S_ab of one (A, B) pair, split into work units of
@@ -40,9 +42,10 @@ struct MomentsProblem {
     int32_t M, N;            // A pixels (rows), B pixels (columns)
     int32_t k_blocks;        // K blocks of 128 bytes per operand row
     int32_t kb_per_chunk;    // K blocks per frame chunk (one partial slot each)
-    int32_t kb_per_fold;     // K blocks per exact FP32 segment (BF16 path)
     int32_t n_chunks, tiles_m, tiles_n;
     int32_t unit_begin;      // first unit of this problem in the launch
+    const uint32_t* vmax;    // BF16 path: largest A and B value of the call's frames (written by
+                             // ingest), which set the exact FP32 segment length
 };
 
 // A persistent launch over the units of up to K problems (K = 1 for a single
@@ -67,8 +70,8 @@ struct MomentsShape {
 };
 MomentsShape moments_shape(bool bf16);
 
-cudaError_t launch_moments(bool bf16, const MomentsLaunch<1>& L, int grid, cudaStream_t st);
-cudaError_t launch_moments_group(bool bf16, const MomentsLaunch<kMaxGroup>& L, int grid,
+cudaError_t launch_moments(bool bf16, const MomentsLaunch<1>& L, int sm_count, cudaStream_t st);
+cudaError_t launch_moments_group(bool bf16, const MomentsLaunch<kMaxGroup>& L, int sm_count,
                                  cudaStream_t st);
 
 // ------------------------------------------------------------------ fold / finalize

@@ -8,25 +8,31 @@
 // 2^24, and the schedule guarantees that:
 //   - binary frames: a frame chunk has at most 32768 frames, so every sum is
 //     <= 32768;
-//   - 8-bit values: products are <= 255^2 = 65025, and the accumulator is
-//     folded into exact int32 registers every 256 frames
-//     (256 * 65025 = 16,646,400 < 2^24); a chunk of <= 32768 frames keeps the
-//     int32 total below 2^31.
-// Each (frame chunk, 128 x BLOCK_N output tile) of a problem is one work unit;
-// its exact int32 partial sum goes to its own slot of the workspace, and the
-// fold step adds the slots into int64.  Integer addition is associative, so the
-// split over chunks and CTAs never changes the result.  One launch serves one
-// problem (a correlation) or up to kMaxGroup problems of uneven shapes (a
-// batch): the persistent CTAs walk one list of units, each unit naming its
-// problem by a binary search over the problems' first units.
+//   - 8-bit values: the FP32 accumulator is folded into exact int32 running
+//     sums (kept in tensor memory beside it) every S frames, S the largest
+//     multiple of 64 with S x max A x max B < 2^23 (at least 128 frames, since
+//     128 x 255^2 < 2^23).  The maxima are the ones the ingest records for the
+//     call's frames, read on the device, so photon counts far below 255 fold
+//     rarely or never.  Below 2^23 the fold needs no float-to-integer
+//     conversion: f + 2^23 is exact with bit pattern 0x4B000000 + f.  A chunk of
+//     <= 32768 frames keeps each int32 total below 2^31.
+// Each (frame chunk, 128 x 256 output tile) of a problem is one work unit; its
+// exact int32 partial sum goes to its own slot of the workspace, and the fold
+// step adds the slots into int64.  Integer addition is associative, so the
+// split over chunks, segments and CTAs never changes the result.  One launch
+// serves one problem (a correlation) or up to kMaxGroup problems of uneven
+// shapes (a batch): the persistent CTAs walk one list of units, each unit naming
+// its problem by a binary search over the problems' first units.
 //
-// Persistent, warp-specialised CTA (one per SM, 192 threads):
-//   warp 0  : TMA producer (128-byte swizzled tiles, STAGES-deep ring)
-//   warp 1  : tensor-memory allocator and single-thread MMA issuer
-//   warps 2-5: epilogue, tensor memory -> registers -> global (TMEM lanes 32*(w%4)..)
-// Two TMEM accumulators let the epilogue of one segment overlap the MMAs of the
-// next.  Every barrier wait is bounded; on a time-out the CTA records the error,
-// drains its own copies and MMAs, frees its tensor memory and returns.
+// Persistent, warp-specialised CTA (one per SM, 320 threads):
+//   warp 0   : TMA producer (128-byte swizzled tiles, 4-deep ring)
+//   warp 1   : tensor-memory allocator and single-thread MMA issuer
+//   warps 2-9: epilogue, tensor memory -> registers -> global (TMEM lanes 32*(w%4)..)
+// Binary frames: two TMEM accumulators let the epilogue of one unit overlap the
+// MMAs of the next.  8-bit frames: one FP32 accumulator (256 columns) and the
+// int32 running sums (256 columns).  Every barrier wait is bounded; on a
+// time-out the CTA records the error, drains its own copies and MMAs, frees its
+// tensor memory and returns.
 #include "kernels.cuh"
 #include "ptx.cuh"
 
@@ -40,14 +46,18 @@ constexpr int kEpiThreads = 256;
 
 template <bool kBf16>
 struct MomentsCfg {
-    static constexpr int kBlockN = kBf16 ? 128 : 256;
-    static constexpr int kStages = kBf16 ? 6 : 4;
+    static constexpr int kBlockN = 256;
+    static constexpr int kStages = 4;
     static constexpr int kElem = kBf16 ? 2 : 1;
     static constexpr int kKPerBlock = kRowBytes / kElem;     // 64 / 128 elements
     static constexpr int kMmaK = 32 / kElem;                  // 16 / 32 elements per MMA
     static constexpr int kABytes = kBlockM * kRowBytes;       // 16 KiB
-    static constexpr int kBBytes = kBlockN * kRowBytes;       // 16 / 32 KiB
-    static constexpr uint32_t kTmemCols = 2 * kBlockN;        // two accumulators
+    static constexpr int kBBytes = kBlockN * kRowBytes;       // 32 KiB
+    // tensor memory (512 columns): FP8, two FP32 accumulators; BF16, one FP32
+    // accumulator and the int32 running sums at column 256
+    static constexpr int kAcc = kBf16 ? 1 : 2;
+    static constexpr uint32_t kSumCol = 256;
+    static constexpr uint32_t kTmemCols = 512;
     static constexpr size_t kSmem = 1024 + (size_t)kStages * (kABytes + kBBytes) + 256;
 };
 
@@ -101,10 +111,25 @@ __device__ __forceinline__ Unit decode_unit(const MomentsLaunch<K>& L, int u) {
     return w;
 }
 
+// K blocks (64 frames) per exact FP32 segment of a BF16 problem: the largest S
+// with S x 64 x max A x max B < 2^23, from the ingest's maxima (worst case
+// 255 x 255 when they are missing).
+__device__ __forceinline__ int segment_kblocks(const MomentsProblem& P) {
+    uint64_t prod = 255u * 255u;
+    if (P.vmax != nullptr) prod = (uint64_t)__ldcg(P.vmax) * (uint64_t)__ldcg(P.vmax + 1);
+    if (prod < 1) prod = 1;
+    const uint64_t frames = ((1ull << 23) - 1) / prod;
+    const uint64_t kb = frames / 64;
+    return kb < 1 ? 1 : (kb > 0x40000000ull ? 0x40000000 : (int)kb);
+}
+
 template <bool kBf16, int K>
 __global__ void __launch_bounds__(kThreads, 1)
     moments_kernel(const __grid_constant__ MomentsLaunch<K> L) {
     using C = MomentsCfg<kBf16>;
+    __shared__ int seg_kb[K];   // BF16: K blocks per exact FP32 segment, per problem
+    if constexpr (kBf16)
+        for (int p = threadIdx.x; p < L.n_problems; p += blockDim.x) seg_kb[p] = segment_kblocks(L.prob[p]);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                ~static_cast<uintptr_t>(1023));
@@ -112,9 +137,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t* sB = sA + C::kStages * C::kABytes;
     uint64_t* full = reinterpret_cast<uint64_t*>(sB + C::kStages * C::kBBytes);
     uint64_t* empty = full + C::kStages;
-    uint64_t* tfull = empty + C::kStages;      // [2] accumulator ready for the epilogue
-    uint64_t* tempty = tfull + 2;              // [2] accumulator drained by the epilogue
-    uint64_t* drain = tempty + 2;              // MMA drain on abort
+    uint64_t* tfull = empty + C::kStages;      // [kAcc] accumulator ready for the epilogue
+    uint64_t* tempty = tfull + C::kAcc;        // [kAcc] accumulator drained by the epilogue
+    uint64_t* drain = tempty + C::kAcc;        // MMA drain on abort
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -127,7 +152,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        for (int s = 0; s < 2; ++s) {
+        for (int s = 0; s < C::kAcc; ++s) {
             mbar_init(&tfull[s], 1);
             mbar_init(&tempty[s], kEpiThreads);
         }
@@ -157,7 +182,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t issued_mask = 0, issued_phase = 0;   // per stage: loaded at least once / parity
             bool ok = true;
             for (int u = blockIdx.x; ok && u < L.n_units; u += gridDim.x) {
-                const Unit w = decode_unit(L, u);
+                const Unit w = decode_unit<K>(L, u);
                 const CUtensorMap* ma = &L.map_a[w.prob];
                 const CUtensorMap* mb = &L.map_b[w.prob];
                 for (int kb = w.kb0; kb < w.kb1; ++kb) {
@@ -196,8 +221,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t acc_phase = 0;
             bool ok = true, issued_any = false;
             for (int u = blockIdx.x; ok && u < L.n_units; u += gridDim.x) {
-                const Unit w = decode_unit(L, u);
-                const int kb_per_fold = L.prob[w.prob].kb_per_fold;
+                const Unit w = decode_unit<K>(L, u);
+                const int kb_per_fold = kBf16 ? seg_kb[w.prob] : 0;
                 const int kb0 = w.kb0, kb1 = w.kb1;
                 for (int kb = kb0; kb < kb1; ++kb) {
                     const int local = kb - kb0;
@@ -233,8 +258,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     if (seg_end) {
                         umma_commit(&tfull[acc]);
-                        acc ^= 1;
-                        if (acc == 0) acc_phase ^= 1;
+                        if (++acc == C::kAcc) {
+                            acc = 0;
+                            acc_phase ^= 1;
+                        }
                     }
                 }
             }
@@ -256,7 +283,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t acc_phase = 0;
         bool ok = true;
         for (int u = blockIdx.x; ok && u < L.n_units; u += gridDim.x) {
-            const Unit w = decode_unit(L, u);
+            const Unit w = decode_unit<K>(L, u);
             const MomentsProblem& P = L.prob[w.prob];
             const int chunk = w.chunk;
             const int kb0 = w.kb0, kb1 = w.kb1;
@@ -281,41 +308,51 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_before();
                 mbar_arrive(&tempty[acc]);
-                acc ^= 1;
-                if (acc == 0) acc_phase ^= 1;
+                if (++acc == C::kAcc) {
+                    acc = 0;
+                    acc_phase ^= 1;
+                }
             } else {
-                int32_t sum[kHalf];
-#pragma unroll
-                for (int j = 0; j < kHalf; ++j) sum[j] = 0;
-                const int nseg = (kb1 - kb0 + P.kb_per_fold - 1) / P.kb_per_fold;
+                // Every segment: running sum (TMEM columns kSumCol..) += FP32
+                // segment sum (< 2^23, converted through its bit pattern); the
+                // last segment's totals go to the partial slot instead.
+                const int seg = seg_kb[w.prob];
+                const int nseg = (kb1 - kb0 + seg - 1) / seg;
                 for (int sgm = 0; sgm < nseg; ++sgm) {
-                    if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, status, tmo)) {
+                    if (!mbar_wait_bounded(&tfull[0], acc_phase, abort_flag, status, tmo)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-#pragma unroll
+                    const bool last = sgm + 1 == nseg;
+#pragma unroll 1
                     for (int c = 0; c < kHalf / 32; ++c) {
-                        uint32_t r[32];
-                        tmem_ld_32x32b_x32(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN) + col0 + c * 32,
-                                           r);
+                        const uint32_t col = lane_addr + col0 + (uint32_t)(c * 32);
+                        uint32_t r[32], run[32];
+                        tmem_ld_32x32b_x32(tmem_base + col, r);
+                        if (sgm > 0) tmem_ld_32x32b_x32(tmem_base + C::kSumCol + col, run);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) sum[c * 32 + j] += __float2int_rn(__uint_as_float(r[j]));
+                        for (int j = 0; j < 32; ++j) {
+                            const uint32_t f = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), 8388608.0f)) -
+                                               0x4B000000u;
+                            run[j] = (sgm > 0 ? run[j] : 0u) + f;
+                        }
+                        if (last) {
+                            int32_t v[32];
+#pragma unroll
+                            for (int j = 0; j < 32; ++j) v[j] = (int32_t)run[j];
+                            store_row_chunk(P, chunk, m, n0 + c * 32, v);
+                        } else {
+                            tmem_st_32x32b_x32(tmem_base + C::kSumCol + col, run);
+                        }
                     }
+                    if (!last) tmem_st_wait();
                     tc_fence_before();
-                    mbar_arrive(&tempty[acc]);
-                    acc ^= 1;
-                    if (acc == 0) acc_phase ^= 1;
+                    mbar_arrive(&tempty[0]);
+                    acc_phase ^= 1;
                 }
                 if (!ok) break;
-#pragma unroll
-                for (int c = 0; c < kHalf / 32; ++c) {
-                    int32_t v[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = sum[c * 32 + j];
-                    store_row_chunk(P, chunk, m, n0 + c * 32, v);
-                }
             }
         }
     }
@@ -339,7 +376,7 @@ MomentsShape moments_shape(bool bf16) {
 }
 
 template <bool kBf16, int K>
-static cudaError_t launch_impl(const MomentsLaunch<K>& L, int grid, cudaStream_t st) {
+static cudaError_t launch_impl(const MomentsLaunch<K>& L, int sm_count, cudaStream_t st) {
     // The shared-memory opt-in is a per-device function attribute: set it once per device.
     static bool attr_set[64] = {};
     int dev = 0;
@@ -353,17 +390,18 @@ static cudaError_t launch_impl(const MomentsLaunch<K>& L, int grid, cudaStream_t
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
+    const int grid = L.n_units < sm_count ? L.n_units : sm_count;
     moments_kernel<kBf16, K><<<grid, kThreads, C::kSmem, st>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(bool bf16, const MomentsLaunch<1>& L, int grid, cudaStream_t st) {
-    return bf16 ? launch_impl<true, 1>(L, grid, st) : launch_impl<false, 1>(L, grid, st);
+cudaError_t launch_moments(bool bf16, const MomentsLaunch<1>& L, int sm_count, cudaStream_t st) {
+    return bf16 ? launch_impl<true, 1>(L, sm_count, st) : launch_impl<false, 1>(L, sm_count, st);
 }
 
-cudaError_t launch_moments_group(bool bf16, const MomentsLaunch<kMaxGroup>& L, int grid,
+cudaError_t launch_moments_group(bool bf16, const MomentsLaunch<kMaxGroup>& L, int sm_count,
                                  cudaStream_t st) {
-    return bf16 ? launch_impl<true, kMaxGroup>(L, grid, st) : launch_impl<false, kMaxGroup>(L, grid, st);
+    return bf16 ? launch_impl<true, kMaxGroup>(L, sm_count, st) : launch_impl<false, kMaxGroup>(L, sm_count, st);
 }
 
 }  // namespace cpi

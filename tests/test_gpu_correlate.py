@@ -101,6 +101,30 @@ def test_exactness_adversarial_all_ones_and_max_counts():
     assert_exact(got, want)
 
 
+@pytest.mark.parametrize("top", [23, 91, 255])
+def test_segment_length_follows_the_recorded_value_range(top):
+    """8-bit frames: the FP32 tensor-memory accumulator is folded into int32
+    every S frames, S the largest multiple of 64 with S x max A x max B < 2^23
+    (from the maxima the ingest records).  Constant A = top and B = top except
+    in every 16th frame (top - 1) make every tensor-core K step add an odd
+    increment, so a segment that overran 2^23 would lose low bits in the
+    conversion and the sums would be wrong.  2048 x 1280 outputs keep the frame
+    chunk at the full 32768 frames (several segments per unit for every top)."""
+    n = 32768
+    ha, wa, hb, wb = 32, 64, 20, 64
+    W = wa + wb
+    fr = torch.full((n, ha, W), top, dtype=torch.uint8, device="cuda")
+    low = torch.arange(n, device="cuda") % 16 == 0
+    fr[low, :hb, wa:] = top - 1
+    la = dict(bits=8, height=ha, width=wa, x0=0, y0=0, row_stride=W, frame_stride_bytes=ha * W)
+    lb = dict(la, height=hb, width=wb, x0=wa)
+    got = gpu_correlate(fr, la, lb, n)
+    n_low = int(low.sum().item())
+    assert (got["s_a"] == top * n).all()
+    assert (got["s_b"] == top * n - n_low).all()
+    assert (got["s_ab"] == top * (top * n - n_low)).all()
+
+
 def test_mixed_bit_depths():
     """A binary, B uint8 from different buffers."""
     acq = synth.Acquisition(20, 10, 2500, 1.0, "poisson8", seed=3)
