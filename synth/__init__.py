@@ -12,6 +12,7 @@ from .frames import (  # noqa: F401
     batched_acquisitions,
     generate,
     model_maps,
+    expected_gamma_counts,
     pack_bits_lsb,
     pack_side_by_side,
     uniform_planes,

@@ -47,6 +47,7 @@ class Acquisition:
     sigma: float = 1.5
     radius: int = 5
     seed: int = 0
+    mask_seed: Optional[int] = None  # None: the fixed three-bar object; else a seeded bar pattern
 
     @property
     def S(self) -> int:
@@ -106,6 +107,25 @@ def _bar_mask(S: int) -> np.ndarray:
     return m
 
 
+def _random_bar_mask(S: int, mask_seed: int) -> np.ndarray:
+    """2 to 4 transmissive bars, each vertical or horizontal, width S/16 .. S/6,
+    at seeded positions (the union of them)."""
+    rng = np.random.Generator(np.random.Philox(int(mask_seed)))
+    m = np.zeros((S, S), dtype=np.float64)
+    for _ in range(int(rng.integers(2, 5))):
+        width = int(rng.integers(max(1, S // 16), max(2, S // 6) + 1))
+        lo = int(rng.integers(0, S - width + 1))
+        if rng.random() < 0.5:
+            m[:, lo:lo + width] = 1.0
+        else:
+            m[lo:lo + width, :] = 1.0
+    return m
+
+
+def _mask(acq: "Acquisition") -> np.ndarray:
+    return _bar_mask(acq.S) if acq.mask_seed is None else _random_bar_mask(acq.S, acq.mask_seed)
+
+
 def _gauss1d(sigma: float, radius: int) -> np.ndarray:
     x = np.arange(-radius, radius + 1, dtype=np.float64)
     g = np.exp(-0.5 * (x / sigma) ** 2)
@@ -125,7 +145,7 @@ def _scales(acq: Acquisition):
     """Photon-number scale factors s_a, s_b from the analytic mean intensities."""
     S = acq.S
     g = _gauss1d(acq.sigma, acq.radius)
-    M = _bar_mask(S)
+    M = _mask(acq)
     # E|F_a(u)|^2 = sum_v h(u - v)^2 M(v): zero-padded correlation of M with h^2
     g2 = g ** 2
     mean_grid = _conv_same_np(M, g2)
@@ -165,7 +185,7 @@ def model_maps(acq: Acquisition):
         raise ValueError("model_maps is meant for small source grids")
     g = _gauss1d(acq.sigma, acq.radius)
     r = acq.radius
-    M = _bar_mask(S).reshape(-1)
+    M = _mask(acq).reshape(-1)
     yy, xx = np.meshgrid(np.arange(S), np.arange(S), indexing="ij")
     uy, ux = yy.reshape(-1), xx.reshape(-1)
     dy = uy[:, None] - uy[None, :]
@@ -179,6 +199,45 @@ def model_maps(acq: Acquisition):
     L_b = np.exp(phase)
     s_a, s_b = _scales(acq)
     return L_a, L_b, _bin_matrix(acq.side_a, S), _bin_matrix(acq.side_b, S), s_a, s_b
+
+
+def expected_gamma_counts(acq: Acquisition, device="cpu", n_frames: Optional[int] = None) -> torch.Tensor:
+    """Expected value of Eq. (1) for Poisson counts, E[Gamma] = (1 - 1/N) Cov(A_a, B_b),
+    as a float64 [side_a^2, side_b^2] tensor (the clip at 255 is ignored).
+
+    For circular complex Gaussian E, Cov(|Psi_a(u)|^2, |Psi_b(v)|^2) = |K(u, v)|^2
+    with K(u, v) = E[Psi_a(u) conj(Psi_b(v))] = (h * (M . exp(+2 pi i f_v . w / S)))(u):
+    the blurred object modulated by the conjugate DFT basis vector of frequency v.
+    Poisson noise adds no covariance between the two detectors.  Computed per band
+    of frequency rows with the same separable blur as the generator, then binned."""
+    if acq.counts != "poisson8":
+        raise ValueError("closed form implemented for Poisson counts")
+    device = torch.device(device)
+    n = acq.n_frames if n_frames is None else n_frames
+    S = acq.S
+    s_a, s_b = _scales(acq)
+    g = torch.tensor(_gauss1d(acq.sigma, acq.radius), dtype=torch.float32, device=device)
+    M = torch.tensor(_mask(acq), dtype=torch.float32, device=device)
+    Pa = torch.tensor(_bin_matrix(acq.side_a, S), dtype=torch.float64, device=device)
+    Pb = torch.tensor(_bin_matrix(acq.side_b, S), dtype=torch.float64, device=device)
+    w = torch.arange(S, dtype=torch.float64, device=device)
+    f = torch.arange(S, dtype=torch.float64, device=device) - S // 2
+    cov = torch.zeros((acq.side_a * acq.side_a, acq.side_b * acq.side_b), dtype=torch.float64, device=device)
+    ey = torch.exp(2j * math.pi * f[:, None] * w[None, :] / S)          # [fy, wy]
+    ex = ey                                                              # [fx, wx]
+    for fy0 in range(0, S, 8):
+        fys = slice(fy0, min(fy0 + 8, S))
+        ny = fys.stop - fys.start
+        # modulated object for every (fy, fx) of the band: [ny, S(fx), S(wy), S(wx)]
+        mod = (ey[fys][:, None, :, None] * ex[None, :, None, :]).to(torch.complex64) * M
+        K = _blur_complex(mod.reshape(ny * S, S, S), g, acq.radius)
+        P2 = (K.real.double() ** 2 + K.imag.double() ** 2).reshape(ny, S, S, S)   # [fy, fx, uy, ux]
+        Ia = torch.einsum("au,yxuv,bv->yxab", Pa, P2, Pa).reshape(ny, S, -1)    # [fy, fx, a]
+        by = (torch.arange(fys.start, fys.stop, device=device) * acq.side_b) // S
+        Ib = torch.einsum("yxa,cx->yac", Ia, Pb)                                 # [fy, a, bx]
+        for k in range(ny):
+            cov[:, int(by[k]) * acq.side_b:(int(by[k]) + 1) * acq.side_b] += Ib[k]
+    return cov * (s_a * s_b) * (1.0 - 1.0 / n)
 
 
 # ----------------------------------------------------------------------------- sampling
@@ -202,7 +261,7 @@ def generate(acq: Acquisition, device="cpu", n_frames: Optional[int] = None):
     s_a, s_b = _scales(acq)
     dt = torch.float32
     g = torch.tensor(_gauss1d(acq.sigma, acq.radius), dtype=dt, device=device)
-    M = torch.tensor(_bar_mask(S), dtype=dt, device=device)
+    M = torch.tensor(_mask(acq), dtype=dt, device=device)
     Pa = torch.tensor(_bin_matrix(acq.side_a, S), dtype=dt, device=device)
     Pb = torch.tensor(_bin_matrix(acq.side_b, S), dtype=dt, device=device)
     gen = torch.Generator(device=device)
