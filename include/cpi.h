@@ -251,12 +251,48 @@ CPI_API cpi_status cpi_correlate_noalloc(const cpi_frames *a, const cpi_frames *
                                          float *gamma_f32, cpi_stream stream);
 
 /* --------------------------------------------------------------------------
- * Learned denoiser of Gamma (a small convolutional network mapping Gamma from
- * few frames to Gamma from many).  Not part of the paper's method; not
- * implemented in this build: always returns CPI_ERR_UNSUPPORTED.
+ * Learned denoiser of Gamma.  The paper has no counterpart: this is the
+ * project's "learned denoiser" row, a small convolutional network that maps
+ * Gamma of Eq. (1) measured from few frames to Gamma of many frames, trained on
+ * pairs the method generates; the plain Gamma stays the fallback and the judge
+ * of its error.
+ *
+ * Network, per angular slice b = (br, bc) of Gamma (float [hb*wb][ha*wa],
+ * slice-major: cpi_correlate's gamma_f32):
+ *   x  = 9 channels, the slices of the 3 x 3 angular neighbourhood
+ *        (br + dy, bc + dx), channel 3 (dy + 1) + (dx + 1), zero outside the
+ *        angular grid; the whole Gamma scaled by s = 1 / rms(gamma_in);
+ *   a1 = relu(conv(x; 9 -> 32)), a2 = relu(conv(a1; 32 -> 32)),
+ *   a3 = relu(conv(a2; 32 -> 32)), y = x[4] + conv(a3; 32 -> 1)
+ *   (3 x 3 kernels, zero padding 1, with biases); gamma_out = y / s.
+ * x, a1..a3 and the weights in use are rounded to bfloat16; sums are float32.
+ *
+ * model: DEVICE float [CPI_DENOISER_PARAMS], float32 master weights, per layer
+ *   l = 0..3 the weights W_l [Cout][Cin][3][3] then the biases b_l [Cout].
+ * workspace: DEVICE, 256-byte aligned, cpi_denoise_workspace_size bytes
+ *   (training != 0 for cpi_denoise_grad; about 3.2 GB for 64x64 vs 32x32).
+ * Requires ha, wa, hb, wb >= 1 and hb * wb <= 65535; errors are reported before
+ * any launch.
+ *
+ * cpi_denoise      : gamma_out = denoised gamma_in (same layout).
+ * cpi_denoise_grad : training loss L = mean over all outputs of
+ *                    (y - s * gamma_target)^2 into *loss (DEVICE float) and
+ *                    dL/d(model) into grad (DEVICE float [CPI_DENOISER_PARAMS]).
+ * cpi_denoise_adam : one Adam step (beta1 0.9, beta2 0.999, eps 1e-8,
+ *                    bias-corrected; step counts from 1) of model with moment
+ *                    buffers m, v (DEVICE float [CPI_DENOISER_PARAMS], zero
+ *                    before the first step).
  * -------------------------------------------------------------------------- */
-CPI_API cpi_status cpi_denoise(const void *model, const float *gamma_in, float *gamma_out, int32_t ha,
-                       int32_t wa, int32_t hb, int32_t wb, cpi_stream stream);
+#define CPI_DENOISER_PARAMS 21409
+CPI_API size_t cpi_denoise_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb, int32_t training);
+CPI_API cpi_status cpi_denoise(const float *model, const float *gamma_in, float *gamma_out, int32_t ha,
+                               int32_t wa, int32_t hb, int32_t wb, void *workspace, size_t workspace_bytes,
+                               cpi_stream stream);
+CPI_API cpi_status cpi_denoise_grad(const float *model, const float *gamma_in, const float *gamma_target,
+                                    int32_t ha, int32_t wa, int32_t hb, int32_t wb, float *grad, float *loss,
+                                    void *workspace, size_t workspace_bytes, cpi_stream stream);
+CPI_API cpi_status cpi_denoise_adam(float *model, float *m, float *v, const float *grad, int64_t step,
+                                    float lr, cpi_stream stream);
 
 /* --------------------------------------------------------------------------
  * Device status.  Kernels record failures (a wait on a pipeline barrier that

@@ -20,9 +20,11 @@ __all__ = [
     "cpi_denoise", "cpi_device_status", "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout",
     "CPI_STAGE_INGEST", "CPI_STAGE_MOMENTS", "CPI_STAGE_FOLD", "EXPORTED", "cpi_correlate_noalloc",
     "NOALLOC_SCRATCH_BYTES", "cpi_batch_item", "batch_items", "CPI_BATCH_GRAPH", "CPI_BATCH_TUNE",
-    "cpi_batch_workspace_size", "cpi_batch_correlate",
+    "cpi_batch_workspace_size", "cpi_batch_correlate", "cpi_denoise_workspace_size", "cpi_denoise_grad",
+    "cpi_denoise_adam", "DENOISER_PARAMS",
 ]
 CPI_BATCH_GRAPH, CPI_BATCH_TUNE = 1, 2
+DENOISER_PARAMS = 21409
 
 CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD = 1, 2, 3
 STATUS = {0: "CPI_OK", 1: "CPI_ERR_INVALID_ARG", 2: "CPI_ERR_OVERFLOW", 3: "CPI_ERR_WORKSPACE",
@@ -34,7 +36,8 @@ EXPORTED = [
     "cpi_correlate_accumulate", "cpi_correlate_finalize", "cpi_correlate_stage",
     "cpi_refocus_workspace_size", "cpi_refocus", "cpi_denoise", "cpi_device_status",
     "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout", "cpi_correlate_noalloc",
-    "cpi_batch_workspace_size", "cpi_batch_correlate",
+    "cpi_batch_workspace_size", "cpi_batch_correlate", "cpi_denoise_workspace_size", "cpi_denoise_grad",
+    "cpi_denoise_adam",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -109,7 +112,10 @@ def load(path: str | None = None):
         "cpi_correlate_stage": ([i32, _F, _F, i64, i32, _P, _P, _P, _P, _P, _P, sz, _P], st),
         "cpi_refocus_workspace_size": ([i32, i32, i32, i32, i32], sz),
         "cpi_refocus": ([_P, i32, i32, i32, i32, ctypes.POINTER(cpi_plane), i32, _P, _P, sz, _P], st),
-        "cpi_denoise": ([_P, _P, _P, i32, i32, i32, i32, _P], st),
+        "cpi_denoise_workspace_size": ([i32, i32, i32, i32, i32], sz),
+        "cpi_denoise": ([_P, _P, _P, i32, i32, i32, i32, _P, sz, _P], st),
+        "cpi_denoise_grad": ([_P, _P, _P, i32, i32, i32, i32, _P, _P, _P, sz, _P], st),
+        "cpi_denoise_adam": ([_P, _P, _P, _P, i64, ctypes.c_float, _P], st),
         "cpi_device_status": ([_P, i32], st),
         "cpi_set_wait_timeout_ns": ([i64], None),
         "cpi_selftest_wait_timeout": ([i64, _P], st),
@@ -220,9 +226,25 @@ def cpi_refocus(gamma_f32, ha, wa, hb, wb, planes, out, workspace, stream=None):
                               _stream(stream)), "cpi_refocus")
 
 
-def cpi_denoise(model, gamma_in, gamma_out, ha, wa, hb, wb, stream=None):
-    _check(load().cpi_denoise(None if model is None else ctypes.c_void_p(model), _ptr(gamma_in),
-                              _ptr(gamma_out), ha, wa, hb, wb, _stream(stream)), "cpi_denoise")
+def cpi_denoise_workspace_size(ha, wa, hb, wb, training=False) -> int:
+    return load().cpi_denoise_workspace_size(ha, wa, hb, wb, 1 if training else 0)
+
+
+def cpi_denoise(model, gamma_in, gamma_out, ha, wa, hb, wb, workspace, stream=None):
+    """model: float32 device tensor [DENOISER_PARAMS]; gamma_in/out: float32 [hb*wb][ha*wa]."""
+    _check(load().cpi_denoise(_ptr(model), _ptr(gamma_in), _ptr(gamma_out), ha, wa, hb, wb, _ptr(workspace),
+                              workspace.numel() * workspace.element_size(), _stream(stream)), "cpi_denoise")
+
+
+def cpi_denoise_grad(model, gamma_in, gamma_target, ha, wa, hb, wb, grad, loss, workspace, stream=None):
+    _check(load().cpi_denoise_grad(_ptr(model), _ptr(gamma_in), _ptr(gamma_target), ha, wa, hb, wb, _ptr(grad),
+                                   _ptr(loss), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                                   _stream(stream)), "cpi_denoise_grad")
+
+
+def cpi_denoise_adam(model, m, v, grad, step, lr, stream=None):
+    _check(load().cpi_denoise_adam(_ptr(model), _ptr(m), _ptr(v), _ptr(grad), int(step), float(lr),
+                                   _stream(stream)), "cpi_denoise_adam")
 
 
 def cpi_device_status(stream=None, clear: bool = True) -> int:

@@ -752,11 +752,52 @@ cpi_status cpi_batch_correlate(const cpi_batch_item* items, int32_t n_items, voi
     return cudaGraphLaunch(exec, st) == cudaSuccess ? CPI_OK : CPI_ERR_CUDA;
 }
 
-cpi_status cpi_denoise(const void* model, const float* gamma_in, float* gamma_out, int32_t ha,
-                       int32_t wa, int32_t hb, int32_t wb, cpi_stream stream) {
-    (void)model, (void)gamma_in, (void)gamma_out, (void)ha, (void)wa, (void)hb, (void)wb,
-        (void)stream;
-    return CPI_ERR_UNSUPPORTED;
+static bool denoise_shape_ok(int32_t ha, int32_t wa, int32_t hb, int32_t wb) {
+    return ha >= 1 && wa >= 1 && hb >= 1 && wb >= 1 && (int64_t)hb * wb <= 65535 &&
+           (int64_t)ha * wa <= ((int64_t)1 << 24);
+}
+
+size_t cpi_denoise_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb, int32_t training) {
+    if (!denoise_shape_ok(ha, wa, hb, wb)) return 0;
+    return denoise_layout(ha, wa, hb, wb, training != 0).bytes;
+}
+
+cpi_status cpi_denoise(const float* model, const float* gamma_in, float* gamma_out, int32_t ha, int32_t wa,
+                       int32_t hb, int32_t wb, void* workspace, size_t workspace_bytes, cpi_stream stream) {
+    if (!model || !gamma_in || !gamma_out || !denoise_shape_ok(ha, wa, hb, wb)) return CPI_ERR_INVALID_ARG;
+    const DenoiseLayout L = denoise_layout(ha, wa, hb, wb, false);
+    if (!workspace || workspace_bytes < L.bytes || !aligned(workspace, 256)) return CPI_ERR_WORKSPACE;
+    DeviceInfo* dev = nullptr;
+    if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, st);
+    if (e == cudaSuccess) e = denoise_output(ws, L, (int64_t)hb * wb * ha * wa, gamma_out, st);
+    return cuda_status(e);
+}
+
+cpi_status cpi_denoise_grad(const float* model, const float* gamma_in, const float* gamma_target, int32_t ha,
+                            int32_t wa, int32_t hb, int32_t wb, float* grad, float* loss, void* workspace,
+                            size_t workspace_bytes, cpi_stream stream) {
+    if (!model || !gamma_in || !gamma_target || !grad || !loss || !denoise_shape_ok(ha, wa, hb, wb))
+        return CPI_ERR_INVALID_ARG;
+    const DenoiseLayout L = denoise_layout(ha, wa, hb, wb, true);
+    if (!workspace || workspace_bytes < L.bytes || !aligned(workspace, 256)) return CPI_ERR_WORKSPACE;
+    DeviceInfo* dev = nullptr;
+    if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    uint8_t* ws = static_cast<uint8_t*>(workspace);
+    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, st);
+    if (e == cudaSuccess) e = denoise_backward(model, gamma_target, ha, wa, hb, wb, ws, L, grad, loss, st);
+    return cuda_status(e);
+}
+
+cpi_status cpi_denoise_adam(float* model, float* m, float* v, const float* grad, int64_t step, float lr,
+                            cpi_stream stream) {
+    if (!model || !m || !v || !grad || step < 1 || !(lr > 0.0f) || !std::isfinite(lr)) return CPI_ERR_INVALID_ARG;
+    DeviceInfo* dev = nullptr;
+    if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+    return cuda_status(denoise_adam(model, m, v, grad, step, lr, reinterpret_cast<cudaStream_t>(stream)));
 }
 
 cpi_status cpi_device_status(cpi_stream stream, int32_t clear) {

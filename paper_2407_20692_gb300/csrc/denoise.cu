@@ -1,0 +1,488 @@
+// Learned denoiser of Gamma (the paper has none; the network is the project's
+// "learned denoiser" row): a 4-layer 3 x 3 convolutional network that maps
+// Gamma measured from few frames to Gamma of many frames, trained on pairs the
+// method generates.  The plain Gamma of Eq. (1) stays the fallback and the
+// judge of its error.
+//
+// Network, per angular slice b = (br, bc) of Gamma (float [Mb][ha * wa]):
+//   input x: 9 channels, the slices of the 3 x 3 angular neighbourhood
+//            (br + dy, bc + dx), channel 3 (dy + 1) + (dx + 1), zero outside the
+//            angular grid, the whole of Gamma scaled by s = 1 / rms(Gamma_in);
+//   a1 = relu(conv(x; 9 -> 32)), a2 = relu(conv(a1; 32 -> 32)),
+//   a3 = relu(conv(a2; 32 -> 32)), y = x[4] + conv(a3; 32 -> 1)
+//   (3 x 3 kernels, zero padding 1, biases); Gamma_out = y / s.
+// Storage: x, a1..a3 and the weights in use are bfloat16 (round to nearest
+// even from float32); every sum is float32; y, the gradients and the float32
+// master weights are float32.  Training minimises mean((y - s Gamma_target)^2)
+// with Adam.
+//
+// Kernels are direct convolutions on the FP32 pipe: a CTA computes a tile of
+// 8 x 32 output pixels of one slice for every output channel, each thread two
+// pixels (rows r and r + 4 of its column) times all output channels, the input
+// tile (with its 1-pixel halo) and the bf16-rounded weights staged in shared
+// memory ([Cin][tap][Cout], so the output channels of one tap are read as
+// broadcast vectors).  Weight gradients are summed per CTA over a fixed range
+// of slices and the per-CTA partials added in a fixed order, so every result is
+// deterministic.
+#include <cuda_bf16.h>
+
+#include "kernels.cuh"
+
+namespace cpi {
+namespace {
+
+constexpr int kTH = 8, kTW = 32;           // output tile: 8 rows x 32 columns
+constexpr int kConvThreads = 128;          // 2 pixels per thread
+constexpr int kSumBlocks = 256;
+
+__device__ __forceinline__ float bf16r(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// ------------------------------------------------------------------ scale
+__global__ void dn_sumsq_kernel(const float* __restrict__ g, int64_t n, double* __restrict__ part) {
+    __shared__ double red[256];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = (double)g[i];
+        acc += v * v;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+// s = 1 / rms, from the per-block sums in block order
+__global__ void dn_scale_kernel(const double* __restrict__ part, int nparts, int64_t n, float* __restrict__ scale) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (int i = 0; i < nparts; ++i) t += part[i];
+    const double ms = t / (double)n;
+    *scale = ms > 0.0 ? (float)(1.0 / sqrt(ms)) : 1.0f;
+}
+
+// ------------------------------------------------------------------ input stack
+// x[b][c][p] = bf16(Gamma[nb(b, c)][p] * s), zero outside the angular grid.
+__global__ void dn_stack_kernel(const float* __restrict__ g, const float* __restrict__ scale, int hb, int wb,
+                                int64_t ma, __nv_bfloat16* __restrict__ x) {
+    const int b = blockIdx.z, c = blockIdx.y;
+    const int br = b / wb, bc = b - br * wb;
+    const int r = br + c / 3 - 1, q = bc + c % 3 - 1;
+    const bool in = r >= 0 && r < hb && q >= 0 && q < wb;
+    const float s = *scale;
+    const float* src = in ? g + (int64_t)(r * wb + q) * ma : g;
+    __nv_bfloat16* dst = x + ((int64_t)b * 9 + c) * ma;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < ma; p += (int64_t)gridDim.x * blockDim.x)
+        dst[p] = __float2bfloat16_rn(in ? src[p] * s : 0.0f);
+}
+
+// ------------------------------------------------------------------ convolution
+// MODE 0: hidden layer forward, bf16 in, out = bf16(relu(conv + bias)).
+// MODE 1: last layer forward (COUT = 1), out (float) = x[4] + conv + bias.
+// MODE 2: gradient with respect to a layer's input: "input" = the gradient at
+//         the layer's output (float), masked by mask > 0 (the layer's ReLU) when
+//         mask is given; kernel flipped and transposed; no bias; out float.
+enum { kFwdHidden = 0, kFwdLast = 1, kBwdData = 2 };
+
+template <int CIN, int COUT, int MODE>
+__global__ void __launch_bounds__(kConvThreads)
+    dn_conv_kernel(const void* __restrict__ in_v, const __nv_bfloat16* __restrict__ mask,
+                   const float* __restrict__ w, const float* __restrict__ bias,
+                   const __nv_bfloat16* __restrict__ x0, void* __restrict__ out_v, int H, int W) {
+    extern __shared__ __align__(16) float sm[];
+    constexpr int TP = (kTH + 2) * (kTW + 2);
+    float* sIn = sm;                          // [CIN][kTH + 2][kTW + 2]
+    float* sW = sm + CIN * TP;                // [CIN][9][COUT]
+    const int b = blockIdx.z;
+    const int y0 = blockIdx.y * kTH, x0c = blockIdx.x * kTW;
+    const int64_t HW = (int64_t)H * W;
+    const int tid = threadIdx.x;
+
+    // weights, rounded to bf16
+    for (int i = tid; i < CIN * 9 * COUT; i += kConvThreads) {
+        const int co = i % COUT, rest = i / COUT;
+        const int tap = rest % 9, ci = rest / 9;
+        float v;
+        if (MODE == kBwdData) {
+            // this kernel's input channel ci is the layer's output channel;
+            // its output channel co is the layer's input channel; taps flipped
+            v = w[((int64_t)ci * COUT + co) * 9 + (8 - tap)];
+        } else {
+            v = w[((int64_t)co * CIN + ci) * 9 + tap];
+        }
+        sW[i] = bf16r(v);
+    }
+    // input tile with halo
+    for (int i = tid; i < CIN * TP; i += kConvThreads) {
+        const int ci = i / TP, rem = i - ci * TP;
+        const int ty = rem / (kTW + 2), tx = rem - ty * (kTW + 2);
+        const int yy = y0 + ty - 1, xx = x0c + tx - 1;
+        float v = 0.0f;
+        if (yy >= 0 && yy < H && xx >= 0 && xx < W) {
+            const int64_t idx = ((int64_t)b * CIN + ci) * HW + (int64_t)yy * W + xx;
+            if (MODE == kBwdData) {
+                v = static_cast<const float*>(in_v)[idx];
+                if (mask != nullptr && !(__bfloat162float(mask[idx]) > 0.0f)) v = 0.0f;
+            } else {
+                v = __bfloat162float(static_cast<const __nv_bfloat16*>(in_v)[idx]);
+            }
+        }
+        sIn[i] = v;
+    }
+    __syncthreads();
+
+    const int cx = tid % kTW, ry = tid / kTW;      // column, first row (0..3); second row ry + 4
+    float acc[2][COUT];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) acc[k][co] = 0.0f;
+#pragma unroll 1
+    for (int ci = 0; ci < CIN; ++ci) {
+        const float* src = sIn + ci * TP;
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+            const int ky = tap / 3, kx = tap % 3;
+            const float v0 = src[(ry + ky) * (kTW + 2) + cx + kx];
+            const float v1 = src[(ry + 4 + ky) * (kTW + 2) + cx + kx];
+            const float* wt = sW + (ci * 9 + tap) * COUT;
+            if constexpr (COUT % 4 == 0) {
+#pragma unroll
+                for (int co = 0; co < COUT; co += 4) {
+                    const float4 q = *reinterpret_cast<const float4*>(wt + co);
+                    acc[0][co] = __fmaf_rn(q.x, v0, acc[0][co]);
+                    acc[1][co] = __fmaf_rn(q.x, v1, acc[1][co]);
+                    acc[0][co + 1] = __fmaf_rn(q.y, v0, acc[0][co + 1]);
+                    acc[1][co + 1] = __fmaf_rn(q.y, v1, acc[1][co + 1]);
+                    acc[0][co + 2] = __fmaf_rn(q.z, v0, acc[0][co + 2]);
+                    acc[1][co + 2] = __fmaf_rn(q.z, v1, acc[1][co + 2]);
+                    acc[0][co + 3] = __fmaf_rn(q.w, v0, acc[0][co + 3]);
+                    acc[1][co + 3] = __fmaf_rn(q.w, v1, acc[1][co + 3]);
+                }
+            } else {
+#pragma unroll
+                for (int co = 0; co < COUT; ++co) {
+                    acc[0][co] = __fmaf_rn(wt[co], v0, acc[0][co]);
+                    acc[1][co] = __fmaf_rn(wt[co], v1, acc[1][co]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int yy = y0 + ry + 4 * k, xx = x0c + cx;
+        if (yy >= H || xx >= W) continue;
+        const int64_t p = (int64_t)yy * W + xx;
+        if (MODE == kFwdHidden) {
+            __nv_bfloat16* o = static_cast<__nv_bfloat16*>(out_v);
+#pragma unroll
+            for (int co = 0; co < COUT; ++co)
+                o[((int64_t)b * COUT + co) * HW + p] = __float2bfloat16_rn(fmaxf(acc[k][co] + bias[co], 0.0f));
+        } else if (MODE == kFwdLast) {
+            float* o = static_cast<float*>(out_v);
+            const float xc = __bfloat162float(x0[((int64_t)b * 9 + 4) * HW + p]);
+            o[(int64_t)b * HW + p] = xc + (acc[k][0] + bias[0]);
+        } else {
+            float* o = static_cast<float*>(out_v);
+#pragma unroll
+            for (int co = 0; co < COUT; ++co) o[((int64_t)b * COUT + co) * HW + p] = acc[k][co];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ weight gradients
+// Partial gradient of one layer over slices [b0, b1): thread t < CIN * 9 owns
+// (ci, tap) = (t / 9, t % 9) and all COUT output channels; threads t < COUT also
+// sum the bias gradient.  d = gradient at the layer's output (masked by mask > 0
+// when given), in = the layer's input (bf16).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(((CIN * 9 + 31) / 32) * 32)
+    dn_wgrad_kernel(const __nv_bfloat16* __restrict__ in, const float* __restrict__ d,
+                    const __nv_bfloat16* __restrict__ mask, int B, int H, int W, int slices_per_cta,
+                    float* __restrict__ part) {
+    constexpr int NT = ((CIN * 9 + 31) / 32) * 32;
+    constexpr int TP = (kTH + 2) * (kTW + 2);
+    extern __shared__ __align__(16) float sm[];
+    float* sIn = sm;                              // [CIN][kTH + 2][kTW + 2]
+    float* sD = sm + CIN * TP;                    // [kTH * kTW][COUT]
+    const int tid = threadIdx.x;
+    const bool owner = tid < CIN * 9;
+    const int ci = tid / 9, tap = tid % 9, ky = tap / 3, kx = tap % 3;
+    const int64_t HW = (int64_t)H * W;
+    float acc[COUT];
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) acc[co] = 0.0f;
+    float bacc = 0.0f;
+    const int b0 = blockIdx.x * slices_per_cta, b1 = min(b0 + slices_per_cta, B);
+    for (int b = b0; b < b1; ++b) {
+        for (int y0 = 0; y0 < H; y0 += kTH) {
+            for (int x0 = 0; x0 < W; x0 += kTW) {
+                __syncthreads();   // previous tile consumed
+                for (int i = tid; i < CIN * TP; i += NT) {
+                    const int c = i / TP, rem = i - c * TP;
+                    const int ty = rem / (kTW + 2), tx = rem - ty * (kTW + 2);
+                    const int yy = y0 + ty - 1, xx = x0 + tx - 1;
+                    float v = 0.0f;
+                    if (yy >= 0 && yy < H && xx >= 0 && xx < W)
+                        v = __bfloat162float(in[((int64_t)b * CIN + c) * HW + (int64_t)yy * W + xx]);
+                    sIn[i] = v;
+                }
+                for (int i = tid; i < kTH * kTW * COUT; i += NT) {
+                    const int co = i / (kTH * kTW), p = i - co * (kTH * kTW);
+                    const int yy = y0 + p / kTW, xx = x0 + p % kTW;
+                    float v = 0.0f;
+                    if (yy < H && xx < W) {
+                        const int64_t idx = ((int64_t)b * COUT + co) * HW + (int64_t)yy * W + xx;
+                        v = d[idx];
+                        if (mask != nullptr && !(__bfloat162float(mask[idx]) > 0.0f)) v = 0.0f;
+                    }
+                    sD[p * COUT + co] = v;
+                }
+                __syncthreads();
+                if (owner) {
+#pragma unroll 4
+                    for (int p = 0; p < kTH * kTW; ++p) {
+                        const int py = p / kTW, px = p % kTW;
+                        const float v = sIn[ci * TP + (py + ky) * (kTW + 2) + px + kx];
+                        const float* dd = sD + p * COUT;
+                        if constexpr (COUT % 4 == 0) {
+#pragma unroll
+                            for (int co = 0; co < COUT; co += 4) {
+                                const float4 q = *reinterpret_cast<const float4*>(dd + co);
+                                acc[co] = __fmaf_rn(q.x, v, acc[co]);
+                                acc[co + 1] = __fmaf_rn(q.y, v, acc[co + 1]);
+                                acc[co + 2] = __fmaf_rn(q.z, v, acc[co + 2]);
+                                acc[co + 3] = __fmaf_rn(q.w, v, acc[co + 3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int co = 0; co < COUT; ++co) acc[co] = __fmaf_rn(dd[co], v, acc[co]);
+                        }
+                    }
+                }
+                if (tid < COUT)
+                    for (int p = 0; p < kTH * kTW; ++p) bacc += sD[p * COUT + tid];
+            }
+        }
+    }
+    constexpr int NWB = COUT * CIN * 9 + COUT;
+    float* out = part + (int64_t)blockIdx.x * NWB;
+    if (owner)
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) out[(co * CIN + ci) * 9 + tap] = acc[co];
+    if (tid < COUT) out[COUT * CIN * 9 + tid] = bacc;
+}
+
+// grad[k] = sum over CTAs of part[cta][k], CTAs in order
+__global__ void dn_reduce_parts_kernel(const float* __restrict__ part, int nparts, int n, float* __restrict__ grad) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    float s = 0.0f;
+    for (int i = 0; i < nparts; ++i) s += part[(int64_t)i * n + k];
+    grad[k] = s;
+}
+
+// ------------------------------------------------------------------ loss
+// dY = 2 (y - s t) / count; per-block sums of (y - s t)^2 in float64.
+__global__ void dn_mse_kernel(const float* __restrict__ y, const float* __restrict__ t,
+                              const float* __restrict__ scale, int64_t n, float* __restrict__ dy,
+                              double* __restrict__ part) {
+    __shared__ double red[256];
+    const float s = *scale;
+    const float inv = 2.0f / (float)n;
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float e = y[i] - t[i] * s;
+        dy[i] = e * inv;
+        acc += (double)e * (double)e;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int k = 128; k > 0; k >>= 1) {
+        if ((int)threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void dn_loss_kernel(const double* __restrict__ part, int nparts, int64_t n, float* __restrict__ loss) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (int i = 0; i < nparts; ++i) t += part[i];
+    *loss = (float)(t / (double)n);
+}
+
+// out[i] = y[i] / s
+__global__ void dn_unscale_kernel(const float* __restrict__ y, const float* __restrict__ scale, int64_t n,
+                                  float* __restrict__ out) {
+    const float s = *scale;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = y[i] / s;
+}
+
+// ------------------------------------------------------------------ Adam
+// b1, b2 and their complements 1 - b1, 1 - b2 come rounded separately (1 - 0.999f
+// in float32 is 1.3e-5 away from 0.001).
+__global__ void dn_adam_kernel(float* __restrict__ w, float* __restrict__ m, float* __restrict__ v,
+                               const float* __restrict__ g, int n, float lr, float b1, float omb1, float b2,
+                               float omb2, float eps, float c1, float c2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + omb1 * gi;
+    const float vi = b2 * v[i] + omb2 * (gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+template <int CIN, int COUT, int MODE>
+cudaError_t conv(const void* in, const __nv_bfloat16* mask, const float* w, const float* bias,
+                 const __nv_bfloat16* x0, void* out, int B, int H, int W, cudaStream_t st) {
+    const size_t smem = sizeof(float) * ((size_t)CIN * (kTH + 2) * (kTW + 2) + (size_t)CIN * 9 * COUT);
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(dn_conv_kernel<CIN, COUT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    dim3 grid((unsigned)((W + kTW - 1) / kTW), (unsigned)((H + kTH - 1) / kTH), (unsigned)B);
+    dn_conv_kernel<CIN, COUT, MODE><<<grid, kConvThreads, smem, st>>>(in, mask, w, bias, x0, out, H, W);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t wgrad(const __nv_bfloat16* in, const float* d, const __nv_bfloat16* mask, int B, int H, int W,
+                  int nparts, float* part, float* grad, cudaStream_t st) {
+    constexpr int NT = ((CIN * 9 + 31) / 32) * 32;
+    const size_t smem = sizeof(float) * ((size_t)CIN * (kTH + 2) * (kTW + 2) + (size_t)kTH * kTW * COUT);
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(dn_wgrad_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    const int per = (B + nparts - 1) / nparts;
+    const int used = (B + per - 1) / per;
+    dn_wgrad_kernel<CIN, COUT><<<used, NT, smem, st>>>(in, d, mask, B, H, W, per, part);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    constexpr int n = COUT * CIN * 9 + COUT;
+    dn_reduce_parts_kernel<<<(n + 255) / 256, 256, 0, st>>>(part, used, n, grad);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+// Parameter offsets in the model blob.
+constexpr int64_t kW0 = 0, kB0 = kW0 + 32 * 9 * 9, kW1 = kB0 + 32, kB1 = kW1 + 32 * 32 * 9, kW2 = kB1 + 32,
+                  kB2 = kW2 + 32 * 32 * 9, kW3 = kB2 + 32, kB3 = kW3 + 32 * 9;
+static_assert(kB3 + 1 == kDenoiserParams, "model blob layout");
+
+DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training) {
+    DenoiseLayout L{};
+    const int64_t B = (int64_t)hb * wb, HW = (int64_t)ha * wa;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 255) / 256 * 256;
+        return at;
+    };
+    L.scale = take(sizeof(float));
+    L.sums = take(sizeof(double) * kSumBlocks);
+    L.x0 = take(2 * (size_t)(B * 9 * HW));
+    L.a1 = take(2 * (size_t)(B * 32 * HW));
+    L.a2 = take(2 * (size_t)(B * 32 * HW));
+    L.a3 = take(2 * (size_t)(B * 32 * HW));
+    L.y = take(4 * (size_t)(B * HW));
+    if (training) {
+        L.dy = take(4 * (size_t)(B * HW));
+        L.d_hi = take(4 * (size_t)(B * 32 * HW));
+        L.d_lo = take(4 * (size_t)(B * 32 * HW));
+        L.part = take(sizeof(float) * (size_t)kDenoiseParts * (32 * 32 * 9 + 32));
+    }
+    L.bytes = o;
+    return L;
+}
+
+cudaError_t denoise_forward(const float* model, const float* gamma_in, int ha, int wa, int hb, int wb,
+                            uint8_t* ws, const DenoiseLayout& L, cudaStream_t st) {
+    const int B = hb * wb;
+    const int64_t HW = (int64_t)ha * wa, n = (int64_t)B * HW;
+    float* scale = reinterpret_cast<float*>(ws + L.scale);
+    double* sums = reinterpret_cast<double*>(ws + L.sums);
+    auto* x0 = reinterpret_cast<__nv_bfloat16*>(ws + L.x0);
+    auto* a1 = reinterpret_cast<__nv_bfloat16*>(ws + L.a1);
+    auto* a2 = reinterpret_cast<__nv_bfloat16*>(ws + L.a2);
+    auto* a3 = reinterpret_cast<__nv_bfloat16*>(ws + L.a3);
+    float* y = reinterpret_cast<float*>(ws + L.y);
+    dn_sumsq_kernel<<<kSumBlocks, 256, 0, st>>>(gamma_in, n, sums);
+    dn_scale_kernel<<<1, 32, 0, st>>>(sums, kSumBlocks, n, scale);
+    dn_stack_kernel<<<dim3((unsigned)((HW + 255) / 256 < 64 ? (HW + 255) / 256 : 64), 9, (unsigned)B), 256, 0, st>>>(
+        gamma_in, scale, hb, wb, HW, x0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if ((e = conv<9, 32, kFwdHidden>(x0, nullptr, model + kW0, model + kB0, nullptr, a1, B, ha, wa, st)) != cudaSuccess) return e;
+    if ((e = conv<32, 32, kFwdHidden>(a1, nullptr, model + kW1, model + kB1, nullptr, a2, B, ha, wa, st)) != cudaSuccess) return e;
+    if ((e = conv<32, 32, kFwdHidden>(a2, nullptr, model + kW2, model + kB2, nullptr, a3, B, ha, wa, st)) != cudaSuccess) return e;
+    return conv<32, 1, kFwdLast>(a3, nullptr, model + kW3, model + kB3, x0, y, B, ha, wa, st);
+}
+
+cudaError_t denoise_output(const uint8_t* ws, const DenoiseLayout& L, int64_t n, float* gamma_out, cudaStream_t st) {
+    dn_unscale_kernel<<<1024, 256, 0, st>>>(reinterpret_cast<const float*>(ws + L.y),
+                                            reinterpret_cast<const float*>(ws + L.scale), n, gamma_out);
+    return cudaGetLastError();
+}
+
+cudaError_t denoise_backward(const float* model, const float* gamma_target, int ha, int wa, int hb, int wb,
+                             uint8_t* ws, const DenoiseLayout& L, float* grad, float* loss, cudaStream_t st) {
+    const int B = hb * wb;
+    const int64_t HW = (int64_t)ha * wa, n = (int64_t)B * HW;
+    const float* scale = reinterpret_cast<const float*>(ws + L.scale);
+    double* sums = reinterpret_cast<double*>(ws + L.sums);
+    auto* x0 = reinterpret_cast<const __nv_bfloat16*>(ws + L.x0);
+    auto* a1 = reinterpret_cast<const __nv_bfloat16*>(ws + L.a1);
+    auto* a2 = reinterpret_cast<const __nv_bfloat16*>(ws + L.a2);
+    auto* a3 = reinterpret_cast<const __nv_bfloat16*>(ws + L.a3);
+    const float* y = reinterpret_cast<const float*>(ws + L.y);
+    float* dy = reinterpret_cast<float*>(ws + L.dy);
+    float* dhi = reinterpret_cast<float*>(ws + L.d_hi);
+    float* dlo = reinterpret_cast<float*>(ws + L.d_lo);
+    float* part = reinterpret_cast<float*>(ws + L.part);
+    dn_mse_kernel<<<kSumBlocks, 256, 0, st>>>(y, gamma_target, scale, n, dy, sums);
+    dn_loss_kernel<<<1, 32, 0, st>>>(sums, kSumBlocks, n, loss);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    // layer 3 (32 -> 1): d at its output = dy
+    if ((e = wgrad<32, 1>(a3, dy, nullptr, B, ha, wa, kDenoiseParts, part, grad + kW3, st)) != cudaSuccess) return e;
+    if ((e = conv<1, 32, kBwdData>(dy, nullptr, model + kW3, nullptr, nullptr, dhi, B, ha, wa, st)) != cudaSuccess) return e;
+    // layer 2: d at its output = dhi masked by a3
+    if ((e = wgrad<32, 32>(a2, dhi, a3, B, ha, wa, kDenoiseParts, part, grad + kW2, st)) != cudaSuccess) return e;
+    if ((e = conv<32, 32, kBwdData>(dhi, a3, model + kW2, nullptr, nullptr, dlo, B, ha, wa, st)) != cudaSuccess) return e;
+    // layer 1: d at its output = dlo masked by a2
+    if ((e = wgrad<32, 32>(a1, dlo, a2, B, ha, wa, kDenoiseParts, part, grad + kW1, st)) != cudaSuccess) return e;
+    if ((e = conv<32, 32, kBwdData>(dlo, a2, model + kW1, nullptr, nullptr, dhi, B, ha, wa, st)) != cudaSuccess) return e;
+    // layer 0: d at its output = dhi masked by a1
+    return wgrad<9, 32>(x0, dhi, a1, B, ha, wa, kDenoiseParts, part, grad + kW0, st);
+}
+
+cudaError_t denoise_adam(float* model, float* m, float* v, const float* grad, int64_t step, float lr,
+                         cudaStream_t st) {
+    const float c1 = (float)(1.0 - pow(0.9, (double)step)), c2 = (float)(1.0 - pow(0.999, (double)step));
+    dn_adam_kernel<<<(kDenoiserParams + 255) / 256, 256, 0, st>>>(model, m, v, grad, kDenoiserParams, lr, 0.9f, 0.1f,
+                                                                    0.999f, 0.001f, 1e-8f, c1, c2);
+    return cudaGetLastError();
+}
+
+}  // namespace cpi

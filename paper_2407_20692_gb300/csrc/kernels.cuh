@@ -118,6 +118,24 @@ cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const 
 cudaError_t launch_refocus_reduce(const float* partial, int n_ranges, int64_t per_range,
                                   float* out, cudaStream_t st);
 
+// ------------------------------------------------------------------ denoiser
+constexpr int kDenoiserParams = 21409;    // model blob floats
+constexpr int kDenoiseParts = 256;        // CTAs of a weight-gradient pass (fixed-order partials)
+struct DenoiseLayout {                    // byte offsets in the workspace
+    size_t scale, sums, x0, a1, a2, a3, y, dy, d_hi, d_lo, part, bytes;
+};
+DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training);
+// scale, stacked input, activations and y of the network on gamma_in
+cudaError_t denoise_forward(const float* model, const float* gamma_in, int ha, int wa, int hb, int wb,
+                            uint8_t* ws, const DenoiseLayout& L, cudaStream_t st);
+cudaError_t denoise_output(const uint8_t* ws, const DenoiseLayout& L, int64_t n, float* gamma_out,
+                           cudaStream_t st);
+// after denoise_forward: loss and gradient of the model blob
+cudaError_t denoise_backward(const float* model, const float* gamma_target, int ha, int wa, int hb, int wb,
+                             uint8_t* ws, const DenoiseLayout& L, float* grad, float* loss, cudaStream_t st);
+cudaError_t denoise_adam(float* model, float* m, float* v, const float* grad, int64_t step, float lr,
+                         cudaStream_t st);
+
 // ------------------------------------------------------------------ self test
 cudaError_t launch_wait_selftest(unsigned int* status, unsigned long long timeout_ns,
                                  cudaStream_t st);

@@ -1,0 +1,166 @@
+"""GPU parity of the Gamma denoiser against its oracle (oracle/denoiser.py).
+
+Both sides round the stacked input, the weights in use and the hidden
+activations to bfloat16 at the same points; the remaining differences are the
+order of float32 sums (FP32 on the GPU, float64 in the oracle) and the rare
+bfloat16 rounding that this order moves across a rounding boundary (one
+activation then differs by one bfloat16 unit, 2^-8 of its size, which reaches
+an output through weights of order 0.1).  Tolerances: outputs within 2e-3 of
+the largest output (mean difference below 2e-5 of it); gradients, layer by
+layer, within 2e-3 of the layer's largest gradient component."""
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2407_20692_gb300 as cpi
+from oracle import denoiser as dn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _ready(cuda_ready):
+    yield
+
+
+def _model(seed, noise=0.05):
+    rng = np.random.default_rng(seed)
+    blob = dn.init_blob(seed).astype(np.float64) + noise * rng.standard_normal(dn.N_PARAMS)
+    return blob.astype(np.float32)
+
+
+def _gamma(seed, hb, wb, ha, wa):
+    """Smooth-ish random Gamma slices plus noise, float32 [hb*wb][ha*wa]."""
+    rng = np.random.default_rng(seed)
+    base = rng.standard_normal((hb * wb, ha, wa))
+    base = base + np.roll(base, 1, axis=1) + np.roll(base, 1, axis=2)
+    return (0.01 * base).astype(np.float32).reshape(hb * wb, ha * wa)
+
+
+def _dev(a):
+    return torch.tensor(np.ascontiguousarray(a), device="cuda")
+
+
+def test_denoise_forward_matches_oracle_small():
+    hb, wb, ha, wa = 3, 4, 12, 20
+    blob = _model(1)
+    g = _gamma(2, hb, wb, ha, wa)
+    ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(_dev(g))
+    cpi.cpi_denoise(_dev(blob), _dev(g), out, ha, wa, hb, wb, ws)
+    torch.cuda.synchronize()
+    want = dn.denoise(blob, g.reshape(-1, ha, wa), hb, wb).reshape(hb * wb, -1)
+    s = dn.scale_of(g)
+    d = np.abs(out.cpu().numpy() - want) * s                 # in units of the network output y
+    ymax = np.abs(want).max() * s
+    assert d.max() <= 2e-3 * ymax, d.max() / ymax
+    assert d.mean() <= 2e-5 * ymax, d.mean() / ymax
+
+
+def test_denoise_forward_matches_oracle_on_sampled_slices_of_the_full_workload():
+    """64x64 spatial vs 32x32 angular: the oracle evaluates the network on a few
+    slices (corners, edges, interior), the GPU on all 1024."""
+    hb = wb = 32
+    ha = wa = 64
+    blob = _model(3)
+    g = _gamma(4, hb, wb, ha, wa)
+    ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(_dev(g))
+    cpi.cpi_denoise(_dev(blob), _dev(g), out, ha, wa, hb, wb, ws)
+    torch.cuda.synchronize()
+    s = dn.scale_of(g)
+    x = dn.stack(g.reshape(-1, ha, wa), hb, wb, s)
+    idx = np.array([0, wb - 1, (hb - 1) * wb, hb * wb - 1, 5, 17 * wb, 17 * wb + wb - 1, 500, 777])
+    y, _ = dn.forward(blob, x[idx])
+    got = out.cpu().numpy()[idx].reshape(len(idx), ha, wa) * s
+    d = np.abs(got - y)
+    ymax = np.abs(y).max()
+    assert d.max() <= 2e-3 * ymax, d.max() / ymax
+    assert d.mean() <= 2e-5 * ymax, d.mean() / ymax
+
+
+def _grad(blob, g, t, hb, wb, ha, wa):
+    ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb, training=True), dtype=torch.uint8,
+                     device="cuda")
+    grad = torch.empty(cpi.DENOISER_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    cpi.cpi_denoise_grad(_dev(blob), _dev(g), _dev(t), ha, wa, hb, wb, grad, loss, ws)
+    torch.cuda.synchronize()
+    return grad.cpu().numpy(), float(loss.item())
+
+
+def test_denoise_gradient_matches_oracle_and_is_deterministic():
+    hb, wb, ha, wa = 3, 5, 16, 24
+    blob = _model(5)
+    g = _gamma(6, hb, wb, ha, wa)
+    t = _gamma(7, hb, wb, ha, wa) * 0.5 + g * 0.5
+    got, loss = _grad(blob, g, t, hb, wb, ha, wa)
+    want_loss, want = dn.loss_and_grad(blob, g.reshape(-1, ha, wa), t.reshape(-1, ha, wa), hb, wb)
+    assert abs(loss - want_loss) <= 1e-4 * want_loss
+    o = 0
+    for ci, co in dn.LAYERS:
+        n = co * ci * 9 + co
+        gl, wl = got[o:o + n], want[o:o + n]
+        assert np.abs(gl - wl).max() <= 2e-3 * np.abs(wl).max(), (ci, co, np.abs(gl - wl).max() / np.abs(wl).max())
+        o += n
+    again, loss2 = _grad(blob, g, t, hb, wb, ha, wa)
+    assert np.array_equal(got.view(np.uint32), again.view(np.uint32)) and loss2 == loss
+
+
+def test_adam_step_matches_oracle():
+    rng = np.random.default_rng(8)
+    n = cpi.DENOISER_PARAMS
+    w = rng.standard_normal(n).astype(np.float32)
+    m = (0.01 * rng.standard_normal(n)).astype(np.float32)
+    v = (1e-4 * rng.random(n)).astype(np.float32)
+    g = (0.1 * rng.standard_normal(n)).astype(np.float32)
+    dw, dm, dv = _dev(w), _dev(m), _dev(v)
+    cpi.cpi_denoise_adam(dw, dm, dv, _dev(g), 3, 1e-3)
+    torch.cuda.synchronize()
+    w2, m2, v2 = dn.adam(w.astype(np.float64), m.astype(np.float64), v.astype(np.float64), g.astype(np.float64),
+                         3, 1e-3)
+    # FP32 against float64: a few roundings of each term (0.9 m + 0.1 g can cancel,
+    # so the bound is on the size of the terms, not of the result)
+    u = 2.0 ** -24
+    tm = 0.9 * np.abs(m) + 0.1 * np.abs(g)
+    tv = 0.999 * np.abs(v) + 0.001 * g.astype(np.float64) ** 2
+    assert (np.abs(dm.cpu().numpy() - m2) <= 8 * u * tm).all()
+    assert (np.abs(dv.cpu().numpy() - v2) <= 8 * u * tv).all()
+    step_size = np.abs(w2 - w)
+    assert (np.abs(dw.cpu().numpy() - w2) <= 8 * u * (np.abs(w) + step_size) + 64 * u * step_size).all()
+
+
+def test_training_steps_reduce_the_loss():
+    hb, wb, ha, wa = 4, 4, 16, 16
+    rng = np.random.default_rng(9)
+    clean = _gamma(10, hb, wb, ha, wa)
+    noisy = (clean + 0.01 * rng.standard_normal(clean.shape)).astype(np.float32)
+    model = _dev(dn.init_blob(11))
+    m = torch.zeros_like(model)
+    v = torch.zeros_like(model)
+    ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb, training=True), dtype=torch.uint8,
+                     device="cuda")
+    grad = torch.empty_like(model)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    gi, gt = _dev(noisy), _dev(clean)
+    losses = []
+    for step in range(1, 61):
+        cpi.cpi_denoise_grad(model, gi, gt, ha, wa, hb, wb, grad, loss, ws)
+        cpi.cpi_denoise_adam(model, m, v, grad, step, 3e-3)
+        losses.append(float(loss.item()))
+    assert losses[-1] < 0.5 * losses[0], (losses[0], losses[-1])
+
+
+def test_denoise_argument_errors():
+    ws = torch.empty(1024, dtype=torch.uint8, device="cuda")
+    x = torch.zeros(64, device="cuda")
+    with pytest.raises(cpi.CpiError) as e:
+        cpi.cpi_denoise(x, x, x, 0, 8, 2, 2, ws)
+    assert e.value.code == 1
+    with pytest.raises(cpi.CpiError) as e:
+        cpi.cpi_denoise(x, x, x, 8, 8, 2, 2, ws)            # workspace too small
+    assert e.value.code == 3
+    with pytest.raises(cpi.CpiError) as e:
+        cpi.cpi_denoise_adam(x, x, x, x, 0, 1e-3)           # steps count from 1
+    assert e.value.code == 1
