@@ -164,3 +164,63 @@ def test_denoise_argument_errors():
     with pytest.raises(cpi.CpiError) as e:
         cpi.cpi_denoise_adam(x, x, x, x, 0, 1e-3)           # steps count from 1
     assert e.value.code == 1
+
+
+def _gamma_prefixes(acq, prefixes):
+    import synth
+
+    A, B = synth.generate(acq, "cuda")
+    fr, lay = synth.pack_side_by_side(A, B, 8)
+    la, lb = lay["a"], lay["b"]
+    mk = lambda l: cpi.frames(fr, 8, l["height"], l["width"], l["x0"], l["y0"], l["row_stride"],
+                              l["frame_stride_bytes"])
+    a, b = mk(la), mk(lb)
+    ma, mb = la["height"] * la["width"], lb["height"] * lb["width"]
+    s_ab = torch.empty((ma, mb), dtype=torch.int64, device="cuda")
+    s_a = torch.empty(ma, dtype=torch.int64, device="cuda")
+    s_b = torch.empty(mb, dtype=torch.int64, device="cuda")
+    g64 = torch.empty((ma, mb), dtype=torch.float64, device="cuda")
+    ws = torch.empty(cpi.cpi_correlate_workspace_size(a, b, max(prefixes)), dtype=torch.uint8, device="cuda")
+    out = []
+    for k in prefixes:
+        g32 = torch.empty((mb, ma), dtype=torch.float32, device="cuda")
+        cpi.cpi_correlate(a, b, k, s_ab, s_a, s_b, g64, g32, ws)
+        out.append(g32)
+    return out
+
+
+def test_committed_model_refocuses_better_from_5000_frames_than_plain_gamma_from_50000():
+    """The trained model shipped with the library (trained on Gamma from 1000
+    frames of seeded objects, targets the closed-form expected Gamma): on a seed
+    outside its training set, the refocused stack of the denoised Gamma from 5000
+    frames is closer to the refocused closed form than that of the plain Gamma
+    from 50000 frames, and closer than zeros."""
+    import os
+
+    import synth
+
+    path = os.path.join(os.path.dirname(cpi.__file__), "models", "denoiser_64x64_32x32_n1000.npy")
+    model = _dev(np.load(path))
+    ha = wa = 64
+    hb = wb = 32
+    acq = synth.Acquisition(64, 32, 50000, 2.0, "poisson8", seed=777001, mask_seed=777001)
+    g5k, g50k = _gamma_prefixes(acq, [5000, 50000])
+    ref = synth.expected_gamma_counts(acq, "cuda", n_frames=10 ** 12).t().contiguous().to(torch.float32)
+    ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb), dtype=torch.uint8, device="cuda")
+    den = torch.empty_like(g5k)
+    cpi.cpi_denoise(model, g5k, den, ha, wa, hb, wb, ws)
+    alpha, beta = synth.uniform_planes(32)
+    planes = cpi.plane_array(alpha, beta)
+    rws = torch.empty(cpi.cpi_refocus_workspace_size(ha, wa, hb, wb, 32), dtype=torch.uint8, device="cuda")
+
+    def refocused(g):
+        r = torch.empty((32, ha, wa), dtype=torch.float32, device="cuda")
+        cpi.cpi_refocus(g, ha, wa, hb, wb, planes, r, rws)
+        return r.double()
+
+    r_ref = refocused(ref)
+    err = lambda g: float(torch.linalg.vector_norm(refocused(g) - r_ref) / torch.linalg.vector_norm(r_ref))
+    e_den, e_plain = err(den), err(g50k)
+    torch.cuda.synchronize()
+    assert cpi.cpi_device_status() == 0
+    assert e_den < e_plain and e_den < 1.0, (e_den, e_plain)
