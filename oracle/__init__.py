@@ -107,6 +107,28 @@ def correlate(frames_a, da: dict, frames_b, db: dict, n: int, rows=None, gamma=T
     return {"s_ab": s_ab, "s_a": s_a, "s_b": s_b, "gamma": g}
 
 
+def correlate_rows(frames_a, da: dict, frames_b, db: dict, n: int, r0: int, r1: int):
+    """Rows r0 .. r1 - 1 of Eq. (1) only, for outputs too large to hold whole:
+    returns dict(s_ab [r1 - r0][Mb], s_a, s_b, gamma [r1 - r0][Mb]).  The C routine
+    indexes its outputs by the full row number and writes only rows r0 .. r1 - 1,
+    so it is given addresses that place row r0 at the start of the row buffers."""
+    fa, fb = _as_frames(frames_a), _as_frames(frames_b)
+    Ma, Mb = da["height"] * da["width"], db["height"] * db["width"]
+    assert 0 <= r0 < r1 <= Ma
+    s_ab = np.zeros((r1 - r0, Mb), dtype=np.int64)
+    g = np.zeros((r1 - r0, Mb), dtype=np.float64)
+    s_a = np.zeros(Ma, dtype=np.int64)
+    s_b = np.zeros(Mb, dtype=np.int64)
+    shift = r0 * Mb * 8
+    A, B = _desc(fa, da), _desc(fb, db)
+    rc = lib().oracle_correlate(ctypes.byref(A), ctypes.byref(B), n, r0, r1,
+                                ctypes.c_void_p(s_ab.ctypes.data - shift), s_a.ctypes.data, s_b.ctypes.data,
+                                ctypes.c_void_p(g.ctypes.data - shift))
+    if rc:
+        raise ValueError(f"oracle_correlate failed ({rc})")
+    return {"s_ab": s_ab, "s_a": s_a, "s_b": s_b, "gamma": g}
+
+
 def refocus(gamma: np.ndarray, ha: int, wa: int, hb: int, wb: int, alpha, beta) -> np.ndarray:
     """Refocused stack [P, ha, wa] (float64) from Gamma [ha*wa, hb*wb] (float64)."""
     g = np.ascontiguousarray(gamma, dtype=np.float64)

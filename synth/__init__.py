@@ -10,6 +10,8 @@ from .frames import (  # noqa: F401
     Acquisition,
     CONFIGS,
     batched_acquisitions,
+    bin_file_frames,
+    bin_file_layout,
     generate,
     model_maps,
     expected_gamma_counts,

@@ -342,5 +342,35 @@ def pack_side_by_side(A: torch.Tensor, B: torch.Tensor, bits: int):
     return frames.contiguous(), layout
 
 
+def bin_file_frames(n: int, seed: int, height: int = 256, width: int = 512, p: float = 0.1, device="cpu"):
+    """Binary frames in the layout of the paper's .bin files (Section 2): each frame
+    is height x width pixels, two side-by-side images (A: columns 0 .. width/2 - 1,
+    B: the rest), 1 bit per pixel, rows packed least-significant-bit first.
+
+    For scale runs, where the source model would cost a 2-D FFT of the whole
+    source grid per frame: pixels are Bernoulli(p_i) with a per-frame intensity
+    p_i = p (1 + 0.5 u_i), u_i uniform on [-1, 1], shared by both images, so
+    every pixel pair is positively correlated (Gamma = Var(p_i) > 0).  Returns a
+    uint8 tensor [n, height * width / 8]."""
+    device = torch.device(device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    out = torch.empty((n, height * width // 8), dtype=torch.uint8, device=device)
+    for f0 in range(0, n, _BATCH):
+        nb = min(_BATCH, n - f0)
+        pi = p * (1.0 + 0.5 * (2.0 * torch.rand((nb, 1), generator=gen, device=device) - 1.0))
+        bits = (torch.rand((nb, height * width), generator=gen, device=device) < pi).to(torch.uint8)
+        out[f0:f0 + nb] = pack_bits_lsb(bits)
+    return out
+
+
+def bin_file_layout(height: int = 256, width: int = 512):
+    """Frame descriptors of the two images of bin_file_frames (fields of cpi_frames)."""
+    half = width // 2
+    common = dict(bits=1, height=height, width=half, y0=0, row_stride=width,
+                  frame_stride_bytes=height * width // 8, bit_order=0)
+    return {"a": dict(x0=0, **common), "b": dict(x0=half, **common)}
+
+
 def with_seed(acq: Acquisition, seed: int) -> Acquisition:
     return replace(acq, seed=seed)

@@ -311,3 +311,21 @@ def test_refocus_linear(oracle_mod):
     o2 = oracle_mod.refocus(g2, ha, wa, hb, wb, al, be)
     o12 = oracle_mod.refocus(g1 + 3.0 * g2, ha, wa, hb, wb, al, be)
     assert np.max(np.abs(o12 - (o1 + 3.0 * o2))) < 1e-12 * 4 * hb * wb * 4
+
+
+def test_row_subset_equals_the_full_oracle_on_bin_layout_frames(oracle_mod):
+    """oracle.correlate_rows (rows of outputs too large to hold whole) gives the
+    same rows as the full computation, on frames in the layout of the paper's
+    .bin files (two side-by-side images, LSB-first bits)."""
+    import synth
+
+    fr = synth.bin_file_frames(300, 1, height=16, width=64, p=0.2)
+    lay = synth.bin_file_layout(16, 64)
+    h = fr.numpy()
+    full = oracle_mod.correlate(h, lay["a"], h, lay["b"], 300)
+    part = oracle_mod.correlate_rows(h, lay["a"], h, lay["b"], 300, 100, 140)
+    assert np.array_equal(full["s_ab"][100:140], part["s_ab"])
+    assert np.array_equal(full["gamma"][100:140].view(np.int64), part["gamma"].view(np.int64))
+    assert np.array_equal(full["s_a"], part["s_a"]) and np.array_equal(full["s_b"], part["s_b"])
+    # the shared per-frame intensity makes every pixel pair correlated: Gamma = Var(p_i)
+    assert abs(full["gamma"].mean() - (0.1 ** 2) / 3) < 5e-4
