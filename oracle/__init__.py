@@ -56,6 +56,10 @@ def lib():
         _lib.oracle_correlate.argtypes = [P(_Frames), P(_Frames), ctypes.c_int64, ctypes.c_int64,
                                           ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_void_p, ctypes.c_void_p]
+        _lib.oracle_refocus4d.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                          ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
+        _lib.oracle_refocus4d.restype = ctypes.c_int
         _lib.oracle_refocus.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32,
                                         ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
                                         ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]
@@ -141,6 +145,20 @@ def refocus(gamma: np.ndarray, ha: int, wa: int, hb: int, wb: int, alpha, beta) 
                               out.ctypes.data)
     if rc:
         raise ValueError(f"oracle_refocus failed ({rc})")
+    return out
+
+
+def refocus4d(gamma: np.ndarray, ha: int, wa: int, hb: int, wb: int, alpha, beta, gam, delta) -> np.ndarray:
+    """4-D multilinear refocused stack [P, ha, wa] (float64) from Gamma [ha*wa, hb*wb]."""
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    assert g.shape == (ha * wa, hb * wb)
+    co = [np.ascontiguousarray(v, dtype=np.float64) for v in (alpha, beta, gam, delta)]
+    P = len(co[0])
+    assert all(len(v) == P for v in co)
+    out = np.empty((P, ha, wa), dtype=np.float64)
+    rc = lib().oracle_refocus4d(g.ctypes.data, ha, wa, hb, wb, *[v.ctypes.data for v in co], P, out.ctypes.data)
+    if rc:
+        raise ValueError(f"oracle_refocus4d failed ({rc})")
     return out
 
 

@@ -185,6 +185,62 @@ int oracle_refocus(const double *gamma, int32_t ha, int32_t wa, int32_t hb, int3
     return 0;
 }
 
+/*
+ * 4-D multilinear refocusing (Section 4.1: the prototype interpolates Gamma in
+ * all four coordinates, the points depending on the plane).  Reading: plane p
+ * has four coefficients (alpha, beta, gamma, delta); for output pixel x
+ * (centred spatial coordinates) and angular pixel j (centred), Gamma is sampled
+ * at the spatial point  u_a = alpha*x + beta*(j scaled to spatial pixels)  and
+ * the angular point     u_b = gamma*(x scaled to angular pixels) + delta*j,
+ * by multilinear interpolation over the 2 x 2 x 2 x 2 neighbouring grid points
+ * (taps outside either grid count as 0), and the samples are summed over j.
+ * gamma = 0, delta = 1 is the refocusing of oracle_refocus.
+ *   planes : alpha[p], beta[p], gam[p], delta[p]
+ */
+int oracle_refocus4d(const double *g, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
+                     const double *alpha, const double *beta, const double *gam, const double *delta,
+                     int32_t n_planes, double *out)
+{
+    if (ha <= 0 || wa <= 0 || hb <= 0 || wb <= 0 || n_planes < 0) return 1;
+    const int64_t Mb = (int64_t)hb * wb;
+    const double cxa = (wa - 1) / 2.0, cya = (ha - 1) / 2.0;
+    const double cxb = (wb - 1) / 2.0, cyb = (hb - 1) / 2.0;
+    const double sx = (double)wa / (double)wb, sy = (double)ha / (double)hb;   /* angular -> spatial */
+#pragma omp parallel for collapse(2) schedule(dynamic, 1)
+    for (int32_t p = 0; p < n_planes; ++p) {
+        for (int32_t r = 0; r < ha; ++r) {
+            const double al = alpha[p], be = beta[p], ga = gam[p], de = delta[p];
+            for (int32_t c = 0; c < wa; ++c) {
+                double acc = 0.0;
+                for (int32_t jr = 0; jr < hb; ++jr) {
+                    const double uay = al * (r - cya) + be * sy * (jr - cyb) + cya;
+                    const double uby = ga * (r - cya) / sy + de * (jr - cyb) + cyb;
+                    const double fay0 = floor(uay), fby0 = floor(uby);
+                    const double fay = uay - fay0, fby = uby - fby0;
+                    for (int32_t jc = 0; jc < wb; ++jc) {
+                        const double uax = al * (c - cxa) + be * sx * (jc - cxb) + cxa;
+                        const double ubx = ga * (c - cxa) / sx + de * (jc - cxb) + cxb;
+                        const double fax0 = floor(uax), fbx0 = floor(ubx);
+                        const double fax = uax - fax0, fbx = ubx - fbx0;
+                        for (int t = 0; t < 16; ++t) {
+                            const int dya = t & 1, dxa = (t >> 1) & 1, dyb = (t >> 2) & 1, dxb = (t >> 3) & 1;
+                            const int64_t ya = (int64_t)fay0 + dya, xa = (int64_t)fax0 + dxa;
+                            const int64_t yb = (int64_t)fby0 + dyb, xb = (int64_t)fbx0 + dxb;
+                            if (ya < 0 || ya >= ha || xa < 0 || xa >= wa) continue;
+                            if (yb < 0 || yb >= hb || xb < 0 || xb >= wb) continue;
+                            const double w = (dya ? fay : 1.0 - fay) * (dxa ? fax : 1.0 - fax) *
+                                             (dyb ? fby : 1.0 - fby) * (dxb ? fbx : 1.0 - fbx);
+                            acc += w * g[(ya * wa + xa) * Mb + yb * wb + xb];
+                        }
+                    }
+                }
+                out[((int64_t)p * ha + r) * wa + c] = acc;
+            }
+        }
+    }
+    return 0;
+}
+
 /* Number of threads an OpenMP parallel region of this library uses. */
 int oracle_threads(void)
 {

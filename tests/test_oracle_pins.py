@@ -329,3 +329,50 @@ def test_row_subset_equals_the_full_oracle_on_bin_layout_frames(oracle_mod):
     assert np.array_equal(full["s_a"], part["s_a"]) and np.array_equal(full["s_b"], part["s_b"])
     # the shared per-frame intensity makes every pixel pair correlated: Gamma = Var(p_i)
     assert abs(full["gamma"].mean() - (0.1 ** 2) / 3) < 5e-4
+
+
+def _scipy_refocus4d(gamma, ha, wa, hb, wb, alpha, beta, gam, delta):
+    """The 4-D refocusing written with scipy's N-D linear interpolation of the
+    4-D array G[ya, xa, yb, xb] (grid-constant: 0 outside)."""
+    from scipy import ndimage
+
+    g4 = gamma.reshape(ha, wa, hb, wb)
+    cxa, cya, cxb, cyb = (wa - 1) / 2, (ha - 1) / 2, (wb - 1) / 2, (hb - 1) / 2
+    sx, sy = wa / wb, ha / hb
+    rr, cc = np.meshgrid(np.arange(ha), np.arange(wa), indexing="ij")
+    out = np.zeros((len(alpha), ha, wa))
+    for p, (al, be, ga, de) in enumerate(zip(alpha, beta, gam, delta)):
+        for jr in range(hb):
+            for jc in range(wb):
+                coords = [al * (rr - cya) + be * sy * (jr - cyb) + cya,
+                          al * (cc - cxa) + be * sx * (jc - cxb) + cxa,
+                          ga * (rr - cya) / sy + de * (jr - cyb) + cyb,
+                          ga * (cc - cxa) / sx + de * (jc - cxb) + cxb]
+                out[p] += ndimage.map_coordinates(g4, coords, order=1, mode="grid-constant", cval=0.0,
+                                                  prefilter=False)
+    return out
+
+
+def test_refocus4d_matches_scipy_4d_linear_interpolation(oracle_mod):
+    rng = np.random.default_rng(17)
+    ha, wa, hb, wb = 7, 9, 4, 5
+    gamma = rng.standard_normal((ha * wa, hb * wb))
+    alpha = np.array([0.6, 1.0, 1.3, 0.9])
+    beta = np.array([0.4, 0.0, -0.3, 0.25])
+    gam = np.array([0.3, 0.0, -0.45, 0.7])
+    delta = np.array([0.8, 1.0, 1.2, 0.5])
+    out = oracle_mod.refocus4d(gamma, ha, wa, hb, wb, alpha, beta, gam, delta)
+    ref = _scipy_refocus4d(gamma, ha, wa, hb, wb, alpha, beta, gam, delta)
+    assert np.max(np.abs(out - ref)) <= 1e-12 * np.abs(gamma).sum(1).max()
+
+
+def test_refocus4d_reduces_to_the_2d_refocusing(oracle_mod):
+    """gamma = 0, delta = 1: the angular sample points are the angular pixels."""
+    rng = np.random.default_rng(18)
+    ha, wa, hb, wb = 8, 10, 4, 5
+    gamma = rng.standard_normal((ha * wa, hb * wb))
+    alpha = np.array([0.5, 1.0, 1.4])
+    beta = 1.0 - alpha
+    out4 = oracle_mod.refocus4d(gamma, ha, wa, hb, wb, alpha, beta, np.zeros(3), np.ones(3))
+    out2 = oracle_mod.refocus(gamma, ha, wa, hb, wb, alpha, beta)
+    assert np.max(np.abs(out4 - out2)) <= 1e-12 * np.abs(gamma).sum(1).max()
