@@ -184,6 +184,35 @@ CPI_API cpi_status cpi_refocus(const float *gamma_f32, int32_t ha, int32_t wa, i
                        size_t workspace_bytes, cpi_stream stream);
 
 /* --------------------------------------------------------------------------
+ * 4-D multilinear refocusing (Section 4.1: the prototype interpolates Gamma in
+ * all four coordinates, the interpolation points depending on the refocusing
+ * plane).  Plane p has four coefficients; with x and rb as in cpi_refocus and
+ * the angular pixel j (centred), Gamma is sampled at
+ *   spatial point  u_a = alpha_p * x + beta_p * rb
+ *   angular point  u_b = gamma_p * (x scaled to angular pixels: x * wb/wa, hb/ha) + delta_p * j
+ * by multilinear interpolation over the 16 neighbouring grid points (taps
+ * outside either grid count as 0), and the samples are summed over j:
+ *   out[p][r][c] = sum over j of Gamma~(u_a, u_b).
+ * gamma = 0, delta = 1 is cpi_refocus.  Error: at most ~1e-6 of
+ * max|Gamma| times the total in-grid interpolation weight of the output
+ * (compensated FP32 sums over the angular columns, FP64 over the rows).
+ *
+ *   gamma_f32 : float [hb*wb][ha*wa], slice-major (as cpi_refocus)
+ *   planes    : HOST array of n_planes cpi_plane4, |coefficients| <= 1e6
+ *   out       : float [n_planes][ha][wa]
+ *   workspace : DEVICE, 256-byte aligned, cpi_refocus4d_workspace_size bytes
+ *               (planes are processed in chunks of up to 64)
+ * Requires ha, wa, hb, wb >= 1 and ha * wa, hb * wb <= 2^24.
+ * -------------------------------------------------------------------------- */
+typedef struct {
+    double alpha, beta, gamma, delta;
+} cpi_plane4;
+CPI_API size_t cpi_refocus4d_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb, int32_t n_planes);
+CPI_API cpi_status cpi_refocus4d(const float *gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
+                                 const cpi_plane4 *planes, int32_t n_planes, float *out, void *workspace,
+                                 size_t workspace_bytes, cpi_stream stream);
+
+/* --------------------------------------------------------------------------
  * Batches of independent acquisitions of uneven sizes (many correlations and
  * their refocusings in one call).  The paper processes one acquisition at a
  * time; a batch runs every item's Eq. (1) and refocusing as above, but the

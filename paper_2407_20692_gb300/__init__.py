@@ -21,7 +21,8 @@ __all__ = [
     "CPI_STAGE_INGEST", "CPI_STAGE_MOMENTS", "CPI_STAGE_FOLD", "EXPORTED", "cpi_correlate_noalloc",
     "NOALLOC_SCRATCH_BYTES", "cpi_batch_item", "batch_items", "CPI_BATCH_GRAPH", "CPI_BATCH_TUNE",
     "cpi_batch_workspace_size", "cpi_batch_correlate", "cpi_denoise_workspace_size", "cpi_denoise_grad",
-    "cpi_denoise_adam", "DENOISER_PARAMS", "denoiser_init",
+    "cpi_denoise_adam", "DENOISER_PARAMS", "denoiser_init", "cpi_plane4", "plane4_array",
+    "cpi_refocus4d_workspace_size", "cpi_refocus4d",
 ]
 CPI_BATCH_GRAPH, CPI_BATCH_TUNE = 1, 2
 DENOISER_PARAMS = 21409
@@ -37,7 +38,7 @@ EXPORTED = [
     "cpi_refocus_workspace_size", "cpi_refocus", "cpi_denoise", "cpi_device_status",
     "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout", "cpi_correlate_noalloc",
     "cpi_batch_workspace_size", "cpi_batch_correlate", "cpi_denoise_workspace_size", "cpi_denoise_grad",
-    "cpi_denoise_adam",
+    "cpi_denoise_adam", "cpi_refocus4d_workspace_size", "cpi_refocus4d",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -64,6 +65,11 @@ class cpi_frames(ctypes.Structure):
 
 class cpi_plane(ctypes.Structure):
     _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double)]
+
+
+class cpi_plane4(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("beta", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("delta", ctypes.c_double)]
 
 
 class cpi_batch_item(ctypes.Structure):
@@ -113,6 +119,8 @@ def load(path: str | None = None):
         "cpi_refocus_workspace_size": ([i32, i32, i32, i32, i32], sz),
         "cpi_refocus": ([_P, i32, i32, i32, i32, ctypes.POINTER(cpi_plane), i32, _P, _P, sz, _P], st),
         "cpi_denoise_workspace_size": ([i32, i32, i32, i32, i32], sz),
+        "cpi_refocus4d_workspace_size": ([i32, i32, i32, i32, i32], sz),
+        "cpi_refocus4d": ([_P, i32, i32, i32, i32, ctypes.POINTER(cpi_plane4), i32, _P, _P, sz, _P], st),
         "cpi_denoise": ([_P, _P, _P, i32, i32, i32, i32, _P, sz, _P], st),
         "cpi_denoise_grad": ([_P, _P, _P, i32, i32, i32, i32, _P, _P, _P, sz, _P], st),
         "cpi_denoise_adam": ([_P, _P, _P, _P, i64, ctypes.c_float, _P], st),
@@ -161,6 +169,25 @@ def frames(data, bits: int, height: int, width: int, x0: int = 0, y0: int = 0,
     if fs is None:
         fs = height * rs if bits == 8 else (height * rs + 7) // 8
     return cpi_frames(addr, bits, height, width, x0, y0, rs, fs, bit_order)
+
+
+def plane4_array(alpha, beta, gamma, delta):
+    n = len(alpha)
+    arr = (cpi_plane4 * n)()
+    for i in range(n):
+        arr[i].alpha, arr[i].beta = float(alpha[i]), float(beta[i])
+        arr[i].gamma, arr[i].delta = float(gamma[i]), float(delta[i])
+    return arr
+
+
+def cpi_refocus4d_workspace_size(ha, wa, hb, wb, n_planes) -> int:
+    return load().cpi_refocus4d_workspace_size(ha, wa, hb, wb, n_planes)
+
+
+def cpi_refocus4d(gamma_f32, ha, wa, hb, wb, planes, out, workspace, stream=None):
+    """planes: a ctypes array from plane4_array() (host memory)."""
+    _check(load().cpi_refocus4d(_ptr(gamma_f32), ha, wa, hb, wb, planes, len(planes), _ptr(out), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream)), "cpi_refocus4d")
 
 
 def plane_array(alpha, beta):

@@ -22,7 +22,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
           "--expt-relaxed-constexpr", "-diag-suppress", "177"]
 # Files whose floating point must follow the written expression order exactly.
-NO_FMA = {"refocus.cu"}
+NO_FMA = {"refocus.cu", "refocus4d.cu"}
 
 
 def _nvcc() -> str:

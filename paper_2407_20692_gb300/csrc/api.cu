@@ -752,6 +752,46 @@ cpi_status cpi_batch_correlate(const cpi_batch_item* items, int32_t n_items, voi
     return cudaGraphLaunch(exec, st) == cudaSuccess ? CPI_OK : CPI_ERR_CUDA;
 }
 
+size_t cpi_refocus4d_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb, int32_t n_planes) {
+    if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || n_planes < 1) return 0;
+    if ((int64_t)ha * wa > kMaxPixels || (int64_t)hb * wb > kMaxPixels) return 0;
+    return refocus4d_layout(ha, wa, hb, wb, n_planes).bytes;
+}
+
+cpi_status cpi_refocus4d(const float* gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
+                         const cpi_plane4* planes, int32_t n_planes, float* out, void* workspace,
+                         size_t workspace_bytes, cpi_stream stream) {
+    if (!gamma_f32 || !planes || !out || n_planes < 1) return CPI_ERR_INVALID_ARG;
+    if (ha < 1 || wa < 1 || hb < 1 || wb < 1) return CPI_ERR_INVALID_ARG;
+    if ((int64_t)ha * wa > kMaxPixels || (int64_t)hb * wb > kMaxPixels) return CPI_ERR_INVALID_ARG;
+    if (!aligned(gamma_f32, 4) || !aligned(out, 4)) return CPI_ERR_INVALID_ARG;
+    for (int i = 0; i < n_planes; ++i) {
+        const double c[4] = {planes[i].alpha, planes[i].beta, planes[i].gamma, planes[i].delta};
+        for (double v : c)
+            if (!(std::fabs(v) <= kRefocusMaxCoef)) return CPI_ERR_INVALID_ARG;
+    }
+    const Refocus4dLayout L = refocus4d_layout(ha, wa, hb, wb, n_planes);
+    if (!workspace || workspace_bytes < L.bytes || !aligned(workspace, 256)) return CPI_ERR_WORKSPACE;
+    DeviceInfo* dev = nullptr;
+    if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    Plane4Block pb;
+    for (int p0 = 0; p0 < n_planes; p0 += L.chunk) {
+        const int np = n_planes - p0 < L.chunk ? n_planes - p0 : L.chunk;
+        std::memset(&pb, 0, sizeof(pb));
+        for (int i = 0; i < np; ++i) {
+            pb.c[i][0] = planes[p0 + i].alpha;
+            pb.c[i][1] = planes[p0 + i].beta;
+            pb.c[i][2] = planes[p0 + i].gamma;
+            pb.c[i][3] = planes[p0 + i].delta;
+        }
+        const cudaError_t e = launch_refocus4d_chunk(gamma_f32, ha, wa, hb, wb, pb, np, static_cast<uint8_t*>(workspace),
+                                                     L, out + (int64_t)p0 * ha * wa, st);
+        if (e != cudaSuccess) return CPI_ERR_CUDA;
+    }
+    return CPI_OK;
+}
+
 static bool denoise_shape_ok(int32_t ha, int32_t wa, int32_t hb, int32_t wb) {
     return ha >= 1 && wa >= 1 && hb >= 1 && wb >= 1 && (int64_t)hb * wb <= 65535 &&
            (int64_t)ha * wa <= ((int64_t)1 << 24);

@@ -118,6 +118,22 @@ cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const 
 cudaError_t launch_refocus_reduce(const float* partial, int n_ranges, int64_t per_range,
                                   float* out, cudaStream_t st);
 
+// ------------------------------------------------------------------ 4-D refocus
+constexpr int kRefocus4dChunk = 64;        // planes per launch chunk (at most)
+struct Plane4Block {
+    double c[kRefocus4dChunk][4];          // alpha, beta, gamma, delta
+};
+struct Refocus4dLayout {                   // byte offsets in the workspace
+    int chunk;                             // planes per chunk
+    int64_t stride;                        // elements per coordinate table
+    size_t tables, c_hi, c_lo, bytes;
+};
+Refocus4dLayout refocus4d_layout(int ha, int wa, int hb, int wb, int n_planes);
+bool refocus4d_box_fits(int wa, int wb);
+// planes of one chunk (np <= layout.chunk); out = [np][ha][wa]
+cudaError_t launch_refocus4d_chunk(const float* gamma_f32, int ha, int wa, int hb, int wb, const Plane4Block& coef,
+                                   int np, uint8_t* ws, const Refocus4dLayout& L, float* out, cudaStream_t st);
+
 // ------------------------------------------------------------------ denoiser
 constexpr int kDenoiserParams = 21409;    // model blob floats
 constexpr int kDenoiseParts = 256;        // CTAs of a weight-gradient pass (fixed-order partials)

@@ -1,0 +1,248 @@
+// 4-D multilinear refocusing (Section 4.1: the prototype interpolates Gamma in
+// all four coordinates, the interpolation points depending on the plane).
+// Plane p has four coefficients (alpha, beta, gamma, delta).  For output pixel
+// x (centred spatial coordinates) and angular pixel j (centred), Gamma is
+// sampled at
+//     u_a = alpha x + beta (j in spatial pixels)      (spatial point)
+//     u_b = gamma (x in angular pixels) + delta j     (angular point)
+// by multilinear interpolation over the 16 neighbouring grid points (taps
+// outside either grid count as 0), and the samples are summed over j.
+// gamma = 0, delta = 1 is the 2-D refocusing of refocus.cu.
+//
+// The sample point separates into a column part (x_c, j_c) -> (xa, xb) and a
+// row part (x_r, j_r) -> (ya, yb).  Stage 1 contracts the columns: for every
+// pair of rows (ya, yb), Gamma restricted to them is a W_b x W_a matrix
+// G[xb][xa] (one 2-D box of Gamma's slice-major layout), and
+//     C[p][ya][yb][x_c] = sum_{j_c} sum_{xa, xb taps} w w G[xb][xa],
+// one CTA per (ya, yb) for every plane of the chunk, the box staged in shared
+// memory with a 2-pixel zero border (or read from global memory when it does
+// not fit), Kahan-compensated over j_c and stored as a float pair (sum and
+// compensation).  Stage 2 contracts the rows in FP64 (a 1/W_b share of the
+// work):  out[p][x_r][x_c] = sum_{j_r} sum_{ya, yb taps} w w C[p][ya][yb][x_c].
+// Coordinates are 32.32 fixed point, A(x) + B(j), each rounded once from FP64;
+// fractions rounded to 24 bits (exact weights).
+//
+// This file is compiled without FMA contraction (Kahan steps).
+#include "kernels.cuh"
+
+namespace cpi {
+namespace {
+
+constexpr int kPad = 2;              // zero border of the staged box
+constexpr int kR4Threads = 256;
+
+__device__ __forceinline__ long long r4_fix(double v) { return __double2ll_rn(v * 4294967296.0); }
+
+struct R4Frac {
+    int i;
+    float f;
+};
+__device__ __forceinline__ R4Frac r4_split(long long u) {
+    const long long u24 = (u + 128) >> 8;
+    return {(int)(u24 >> 24), (float)(int)(u24 & 0xFFFFFF) * 0x1p-24f};
+}
+
+__device__ __forceinline__ void r4_kahan(float& acc, float& cmp, float v) {
+    const float y = v - cmp;
+    const float t = acc + y;
+    cmp = (t - acc) - y;
+    acc = t;
+}
+
+// Per-plane coordinate tables (fixed point), chunk planes p0 .. p0 + np - 1:
+//   x axis: TAx[p][c] = alpha (c - cxa) + cxa,        TBx[p][j] = beta sx (j - cxb)
+//           TAbx[p][c] = gamma (c - cxa) / sx + cxb,  TBbx[p][j] = delta (j - cxb)
+//   y axis: the same with rows (ha, hb, sy).
+__global__ void r4_tables_kernel(const Plane4Block co, int np, int ha, int wa, int hb, int wb,
+                                 long long* __restrict__ t, int64_t stride) {
+    const int p = blockIdx.x;
+    if (p >= np) return;
+    const double al = co.c[p][0], be = co.c[p][1], ga = co.c[p][2], de = co.c[p][3];
+    const double cxa = 0.5 * (wa - 1), cya = 0.5 * (ha - 1), cxb = 0.5 * (wb - 1), cyb = 0.5 * (hb - 1);
+    const double sx = (double)wa / (double)wb, sy = (double)ha / (double)hb;
+    long long* TAx = t + 0 * stride + (int64_t)p * wa;
+    long long* TAbx = t + 1 * stride + (int64_t)p * wa;
+    long long* TBx = t + 2 * stride + (int64_t)p * wb;
+    long long* TBbx = t + 3 * stride + (int64_t)p * wb;
+    long long* TAy = t + 4 * stride + (int64_t)p * ha;
+    long long* TAby = t + 5 * stride + (int64_t)p * ha;
+    long long* TBy = t + 6 * stride + (int64_t)p * hb;
+    long long* TBby = t + 7 * stride + (int64_t)p * hb;
+    for (int c = threadIdx.x; c < wa; c += blockDim.x) {
+        TAx[c] = r4_fix(al * (c - cxa) + cxa);
+        TAbx[c] = r4_fix(ga * (c - cxa) / sx + cxb);
+    }
+    for (int j = threadIdx.x; j < wb; j += blockDim.x) {
+        TBx[j] = r4_fix(be * sx * (j - cxb));
+        TBbx[j] = r4_fix(de * (j - cxb));
+    }
+    for (int r = threadIdx.x; r < ha; r += blockDim.x) {
+        TAy[r] = r4_fix(al * (r - cya) + cya);
+        TAby[r] = r4_fix(ga * (r - cya) / sy + cyb);
+    }
+    for (int j = threadIdx.x; j < hb; j += blockDim.x) {
+        TBy[j] = r4_fix(be * sy * (j - cyb));
+        TBby[j] = r4_fix(de * (j - cyb));
+    }
+}
+
+// Stage 1: CTA (yb, ya); every plane of the chunk; threads over x_c.
+template <bool kSmem>
+__global__ void __launch_bounds__(kR4Threads) r4_cols_kernel(const float* __restrict__ g, int np, int ha, int wa,
+                                                             int hb, int wb, const long long* __restrict__ t,
+                                                             int64_t stride, float* __restrict__ c_hi,
+                                                             float* __restrict__ c_lo) {
+    extern __shared__ __align__(16) float sm[];
+    const int yb = blockIdx.x, ya = blockIdx.y;
+    const int64_t ma = (int64_t)ha * wa;
+    const int WP = wa + 2 * kPad, HP = wb + 2 * kPad;     // padded box: HP rows (xb) x WP columns (xa)
+    long long* sB = reinterpret_cast<long long*>(sm);      // [2][wb]: TBx, TBbx of the current plane
+    float* box = reinterpret_cast<float*>(sB + 2 * wb);
+    const float* gbase = g + ((int64_t)yb * wb) * ma + (int64_t)ya * wa;   // G[xb][xa] = gbase[xb*ma + xa]
+    if constexpr (kSmem) {
+        for (int i = threadIdx.x; i < HP * WP; i += kR4Threads) {
+            const int r = i / WP, q = i - r * WP;
+            const int xb = r - kPad, xa = q - kPad;
+            box[i] = (xb >= 0 && xb < wb && xa >= 0 && xa < wa) ? g[(int64_t)(yb * wb + xb) * ma + ya * wa + xa] : 0.0f;
+        }
+    }
+    for (int p = 0; p < np; ++p) {
+        __syncthreads();   // box ready / previous plane's tables consumed
+        for (int j = threadIdx.x; j < wb; j += kR4Threads) {
+            sB[j] = t[2 * stride + (int64_t)p * wb + j];
+            sB[wb + j] = t[3 * stride + (int64_t)p * wb + j];
+        }
+        __syncthreads();
+        for (int xc = threadIdx.x; xc < wa; xc += kR4Threads) {
+            const long long ax = t[0 * stride + (int64_t)p * wa + xc];
+            const long long abx = t[1 * stride + (int64_t)p * wa + xc];
+            float acc = 0.0f, cmp = 0.0f;
+            for (int jc = 0; jc < wb; ++jc) {
+                const R4Frac fa = r4_split(ax + sB[jc]);
+                const R4Frac fb = r4_split(abx + sB[wb + jc]);
+                float v;
+                if constexpr (kSmem) {
+                    const int xa = min(max(fa.i, -kPad), wa) + kPad;
+                    const int xb = min(max(fb.i, -kPad), wb) + kPad;
+                    const float* q0 = box + xb * WP + xa;
+                    const float top = __fmaf_rn(fa.f, q0[1], (1.0f - fa.f) * q0[0]);
+                    const float bot = __fmaf_rn(fa.f, q0[WP + 1], (1.0f - fa.f) * q0[WP]);
+                    v = __fmaf_rn(fb.f, bot, (1.0f - fb.f) * top);
+                } else {
+                    float s[2][2];
+#pragma unroll
+                    for (int db = 0; db < 2; ++db)
+#pragma unroll
+                        for (int da = 0; da < 2; ++da) {
+                            const int xa = fa.i + da, xb = fb.i + db;
+                            s[db][da] = (xa >= 0 && xa < wa && xb >= 0 && xb < wb) ? __ldg(gbase + (int64_t)xb * ma + xa)
+                                                                                 : 0.0f;
+                        }
+                    const float top = __fmaf_rn(fa.f, s[0][1], (1.0f - fa.f) * s[0][0]);
+                    const float bot = __fmaf_rn(fa.f, s[1][1], (1.0f - fa.f) * s[1][0]);
+                    v = __fmaf_rn(fb.f, bot, (1.0f - fb.f) * top);
+                }
+                r4_kahan(acc, cmp, v);
+            }
+            const int64_t o = (((int64_t)p * ha + ya) * hb + yb) * wa + xc;
+            c_hi[o] = acc;
+            c_lo[o] = -cmp;
+        }
+    }
+}
+
+// Stage 2: CTA (x_r, plane); threads over x_c; FP64 sums.
+__global__ void __launch_bounds__(kR4Threads) r4_rows_kernel(const float* __restrict__ c_hi,
+                                                             const float* __restrict__ c_lo, int ha, int wa, int hb,
+                                                             const long long* __restrict__ t, int64_t stride,
+                                                             float* __restrict__ out) {
+    const int xr = blockIdx.x, p = blockIdx.y;
+    const long long ay = t[4 * stride + (int64_t)p * ha + xr];
+    const long long aby = t[5 * stride + (int64_t)p * ha + xr];
+    for (int xc = threadIdx.x; xc < wa; xc += kR4Threads) {
+        double acc = 0.0;
+        for (int jr = 0; jr < hb; ++jr) {
+            const R4Frac fa = r4_split(ay + t[6 * stride + (int64_t)p * hb + jr]);
+            const R4Frac fb = r4_split(aby + t[7 * stride + (int64_t)p * hb + jr]);
+#pragma unroll
+            for (int db = 0; db < 2; ++db) {
+                const int yb = fb.i + db;
+                if (yb < 0 || yb >= hb) continue;
+                const double wb_ = db ? (double)fb.f : 1.0 - (double)fb.f;
+#pragma unroll
+                for (int da = 0; da < 2; ++da) {
+                    const int ya = fa.i + da;
+                    if (ya < 0 || ya >= ha) continue;
+                    const double w = wb_ * (da ? (double)fa.f : 1.0 - (double)fa.f);
+                    const int64_t o = (((int64_t)p * ha + ya) * hb + yb) * wa + xc;
+                    acc += w * ((double)c_hi[o] + (double)c_lo[o]);
+                }
+            }
+        }
+        out[((int64_t)p * ha + xr) * wa + xc] = (float)acc;
+    }
+}
+
+}  // namespace
+
+Refocus4dLayout refocus4d_layout(int ha, int wa, int hb, int wb, int n_planes) {
+    Refocus4dLayout L{};
+    const int64_t per_plane = (int64_t)ha * hb * wa;          // C entries per plane
+    int chunk = n_planes < kRefocus4dChunk ? n_planes : kRefocus4dChunk;
+    while (chunk > 1 && (int64_t)chunk * per_plane * 8 > ((int64_t)4 << 30)) chunk /= 2;
+    L.chunk = chunk;
+    int m = ha;
+    if (wa > m) m = wa;
+    if (hb > m) m = hb;
+    if (wb > m) m = wb;
+    L.stride = (int64_t)chunk * m;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 255) / 256 * 256;
+        return at;
+    };
+    L.tables = take(sizeof(long long) * 8 * (size_t)L.stride);
+    L.c_hi = take(sizeof(float) * (size_t)(chunk * per_plane));
+    L.c_lo = take(sizeof(float) * (size_t)(chunk * per_plane));
+    L.bytes = o;
+    return L;
+}
+
+bool refocus4d_box_fits(int wa, int wb) {
+    const size_t smem = sizeof(long long) * 2 * (size_t)wb + sizeof(float) * (size_t)(wb + 2 * kPad) * (wa + 2 * kPad);
+    return smem <= 200 * 1024;
+}
+
+cudaError_t launch_refocus4d_chunk(const float* gamma_f32, int ha, int wa, int hb, int wb, const Plane4Block& coef,
+                                   int np, uint8_t* ws, const Refocus4dLayout& L, float* out, cudaStream_t st) {
+    long long* t = reinterpret_cast<long long*>(ws + L.tables);
+    float* c_hi = reinterpret_cast<float*>(ws + L.c_hi);
+    float* c_lo = reinterpret_cast<float*>(ws + L.c_lo);
+    r4_tables_kernel<<<np, 128, 0, st>>>(coef, np, ha, wa, hb, wb, t, L.stride);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 g1((unsigned)hb, (unsigned)ha);
+    if (refocus4d_box_fits(wa, wb)) {
+        const size_t smem = sizeof(long long) * 2 * (size_t)wb + sizeof(float) * (size_t)(wb + 2 * kPad) * (wa + 2 * kPad);
+        static bool attr[64] = {};
+        int dev = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!attr[dev]) {
+            if ((e = cudaFuncSetAttribute(r4_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          200 * 1024)) != cudaSuccess)
+                return e;
+            attr[dev] = true;
+        }
+        r4_cols_kernel<true><<<g1, kR4Threads, smem, st>>>(gamma_f32, np, ha, wa, hb, wb, t, L.stride, c_hi, c_lo);
+    } else {
+        r4_cols_kernel<false><<<g1, kR4Threads, sizeof(long long) * 2 * (size_t)wb, st>>>(gamma_f32, np, ha, wa, hb,
+                                                                                         wb, t, L.stride, c_hi, c_lo);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    r4_rows_kernel<<<dim3((unsigned)ha, (unsigned)np), kR4Threads, 0, st>>>(c_hi, c_lo, ha, wa, hb, t, L.stride, out);
+    return cudaGetLastError();
+}
+
+}  // namespace cpi
