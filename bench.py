@@ -37,6 +37,7 @@ WORKLOADS = {
     "batched": (None, 256),      # 64 uneven uint8 acquisitions, one batch call per step
     "denoise": (None, 0),        # learned denoiser: training, inference and frames saved
     "paper_scale": (None, 0),    # 256x256 vs 256x256 binary, .bin-file blocks, Gamma 65536 x 65536
+    "refocus4d": (None, 0),      # 4-D multilinear refocusing at the paper's RoIs and plane counts
 }
 L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
 
@@ -801,6 +802,79 @@ def run_paper_scale(args, world, rank):
     }
 
 
+def refocus4d_planes(P):
+    """Plane coefficients of the 4-D refocusing workload: alpha uniform in
+    [0.5, 1.5], beta = 1 - alpha, gamma = (alpha - 1) / 2, delta = 1 - gamma."""
+    import numpy as np
+
+    a = np.linspace(0.5, 1.5, P) if P > 1 else np.array([1.0])
+    g = 0.5 * (a - 1.0)
+    return a, 1.0 - a, g, 1.0 - g
+
+
+def run_refocus4d(args, world, rank):
+    """4-D multilinear refocusing (Section 4.1) of a 128x128 vs 128x128 Gamma
+    (16384 x 16384) for 100, 261 and 1000 planes and of a 256x256 vs 256x256 Gamma
+    (65536 x 65536) for 100 planes (the RoIs and plane counts of the paper's
+    refocusing benchmark).  Gamma is synthetic FP32 (the kernels' cost does not
+    depend on its values)."""
+    import numpy as np
+    import torch
+
+    import paper_2407_20692_gb300 as cpi
+
+    cpi.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    cases = [(128, 100), (128, 261), (128, 1000), (256, 100)]
+    if args.r4_side:
+        cases = [(args.r4_side, args.r4_planes)]
+    res = {}
+    for side, P in cases:
+        ha = wa = hb = wb = side
+        M = side * side
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(4207 + side)
+        g32 = torch.randn((M, M), generator=gen, device=dev, dtype=torch.float32)
+        planes = cpi.plane4_array(*refocus4d_planes(P))
+        out = torch.empty((P, ha, wa), dtype=torch.float32, device=dev)
+        ws = torch.empty(cpi.cpi_refocus4d_workspace_size(ha, wa, hb, wb, P), dtype=torch.uint8, device=dev)
+        reps = args.steps if args.r4_side else 3 if side == 128 else 1
+        cpi.cpi_refocus4d(g32, ha, wa, hb, wb, planes, out, ws)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            cpi.cpi_refocus4d(g32, ha, wa, hb, wb, planes, out, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        if cpi.cpi_device_status() != 0:
+            raise RuntimeError("device status error")
+        ms = e0.elapsed_time(e1) / reps
+        res[f"{side}x{side}_P{P}"] = {"ms": ms, "planes_per_s": P / (ms / 1e3),
+                                      "per_plane_gamma_gbs": P * M * M * 4 / (ms / 1e3) / 1e9}
+        del g32, ws, out
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return None
+    head = res["128x128_P261"] if "128x128_P261" in res else next(iter(res.values()))
+    peaks, src = _peaks()
+    return {
+        "metric": "4-D multilinear refocusing planes/s, 128x128 vs 128x128 Gamma (16384 x 16384), 261 planes",
+        "value": head["planes_per_s"], "unit": "planes/s", "n_gpus": world, "steps": 3, "warmup": 1,
+        "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 sums (compensated) over angular columns, f64 over angular rows",
+        "data": "synthetic (random FP32 Gamma)",
+        "config": {"workload": "refocus4d", "cases": list(res), "parallelism": f"replicas x{world}"},
+        "cases": res,
+        "roofline": {"kernel": "4-D refocusing (column stage + FP64 row stage)", "bound": "hbm",
+                     "achieved": head["per_plane_gamma_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": head["per_plane_gamma_gbs"] / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": f"{src} hbm copy",
+                     "work": "P x Ma x Mb x 4 B (one FP32 Gamma read per plane)"},
+        "gpu_launches": None,
+    }
+
+
 def ws_row_bytes(n, bits):
     pad = 256 if bits == 1 else 128
     k = (n + pad - 1) // pad * pad
@@ -911,6 +985,8 @@ def main():
     ap.add_argument("--denoise-train-seeds", type=int, default=None)
     ap.add_argument("--denoise-epochs", type=int, default=None)
     ap.add_argument("--save-model", default=None)
+    ap.add_argument("--r4-side", type=int, default=0, help="refocus4d: one case, side x side vs side x side")
+    ap.add_argument("--r4-planes", type=int, default=64, help="refocus4d: planes of the --r4-side case")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -923,6 +999,8 @@ def main():
         line = run_denoise(args, world, rank)
     elif args.workload == "paper_scale":
         line = run_paper_scale(args, world, rank)
+    elif args.workload == "refocus4d":
+        line = run_refocus4d(args, world, rank)
     else:
         line = run_native(args, world, rank, local)
     if rank == 0 and line is not None:

@@ -96,14 +96,16 @@ bool make_operand_map(CUtensorMap* m, void* base, bool bf16, int64_t rows, int64
     return r == CUDA_SUCCESS;
 }
 
-// Slice-major FP32 Gamma as [Mb * ha rows][wa columns]; box (wa + 8) x ha starting
-// at column -4 returns each slice with 4 zero columns on both sides.
-bool make_slice_map(CUtensorMap* m, const float* g, int ha, int wa, int64_t mb) {
+// Slice-major FP32 Gamma as [Mb * ha rows][wa columns], rows pitch floats apart
+// (a multiple of 4); box (wa4 + 8) x ha starting at column -4 (wa4 = wa rounded
+// up to a multiple of 4) returns each slice with zeros in every column outside
+// 0 .. wa-1.
+bool make_slice_map(CUtensorMap* m, const float* g, int ha, int wa, int64_t mb, int pitch) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)wa, (cuuint64_t)(mb * ha)};
-    cuuint64_t strides[1] = {(cuuint64_t)wa * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)(wa + 8), (cuuint32_t)ha};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)(((wa + 3) & ~3) + 8), (cuuint32_t)ha};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(g), dims, strides, box,
                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -308,7 +310,9 @@ size_t refocus_ws_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb, int32_t n
     if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || n_planes < 1) return 0;
     const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
     const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, sm);
-    return round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(float), 256);
+    const size_t partial = round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(float), 256);
+    const int pitch = refocus_pitch(ha, wa, wb);
+    return partial + round_up((size_t)hb * wb * ha * (size_t)pitch * sizeof(float), 256);
 }
 
 cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
@@ -335,7 +339,21 @@ cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
     const int64_t elements = (int64_t)hb * wb * ha * wa;
     if (pipe && elements >= ((int64_t)1 << 31) - 1024) return CPI_ERR_UNSUPPORTED;
     if (staging == 1 && !make_gamma_map(&tm, gamma_f32, elements)) return CPI_ERR_CUDA;
-    if (staging == 2 && !make_slice_map(&tm, gamma_f32, ha, wa, (int64_t)hb * wb)) return CPI_ERR_CUDA;
+    if (staging == 2) {
+        // rows that are not 16-byte multiples: stage from a copy with padded rows
+        const int pitch = refocus_pitch(ha, wa, wb);
+        const float* src = gamma_f32;
+        if (pitch != 0) {
+            const size_t part_bytes =
+                round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(float), 256);
+            float* copy = reinterpret_cast<float*>(static_cast<uint8_t*>(workspace) + part_bytes);
+            const cudaError_t e =
+                launch_refocus_repack(gamma_f32, copy, (int64_t)hb * wb * ha, wa, pitch, dev->sm_count, st);
+            if (e != cudaSuccess) return CPI_ERR_CUDA;
+            src = copy;
+        }
+        if (!make_slice_map(&tm, src, ha, wa, (int64_t)hb * wb, pitch != 0 ? pitch : wa)) return CPI_ERR_CUDA;
+    }
     PlaneBlock pb;
     for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {
         const int np = n_planes - p0 < kRefocusMaxPlanesPerLaunch ? n_planes - p0

@@ -104,9 +104,17 @@ constexpr double kRefocusMaxCoef = 1.0e6;
 size_t refocus_smem_bytes(int ha, int wa, int wb);
 // Pipelined kernel (TMA-staged slices).  refocus_staging: 0 = direct kernel (no
 // tensor map), 1 = 1-D tensor map over all Mb*ha*wa elements with a 256-element
-// box, 2 = 2-D map over [Mb*ha rows][wa columns] with a (wa + 8) x ha box.
+// box, 2 = 2-D map over [Mb*ha rows][wa columns] (row stride refocus_pitch()
+// floats when that is non-zero, else wa) with a (wa4 + 8) x ha box, wa4 = wa
+// rounded up to a multiple of 4.
 bool refocus_pipelined(int ha, int wa, int wb);
 int refocus_staging(int ha, int wa, int wb);
+// Row pitch (floats) of the padded copy of Gamma that 2-D staging needs when wa
+// is not a multiple of 4, else 0 (Gamma is staged from the caller's buffer).
+int refocus_pitch(int ha, int wa, int wb);
+// dst[r * pitch + c] = gamma_f32[r * wa + c] for rows r < rows, c < wa.
+cudaError_t launch_refocus_repack(const float* gamma_f32, float* dst, int64_t rows, int wa, int pitch,
+                                  int sm_count, cudaStream_t st);
 // Number of ranges the angular pixels are split into (one partial image each),
 // and the size of one range (angular rows for the pipelined kernel, angular
 // pixels for the direct one).

@@ -117,9 +117,12 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* m, uin
 // buffers, one TMA copy (group) each, completion counted on full[stage].  The
 // last warp to finish with a buffer (a shared counter per stage) issues the copy
 // of the slice kStages further on into it, so no thread ever waits for a free
-// buffer.  Staging: a 2-D box of (wa + 8) x ha from column -4 when wa % 4 == 0
-// (the 4 columns on each side come back as zeros, the out-of-grid taps), else
-// 1-D boxes of 256 elements from the 16-byte boundary at or below the slice.
+// buffer.  Staging: a 2-D box of (wa4 + 8) x ha from column -4, wa4 = wa
+// rounded up to a multiple of 4 (columns outside 0 .. wa-1 come back as zeros:
+// the out-of-grid taps), when wa4 + 8 <= 256 and ha <= 256.  A Gamma whose rows
+// are not 16-byte multiples is first copied with its rows padded to wa4 floats
+// (refocus_repack_kernel).  Wider slices: 1-D boxes of 256 elements from the
+// 16-byte boundary at or below the slice.
 //
 // Thread t owns column c = t % wa and rows rp + R*k (R = kThreads / wa).  For
 // each staged slice and each plane of the unit it reads its x taps (from a
@@ -186,7 +189,7 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
     extern __shared__ __align__(128) float sm_raw[];
     const int ha = kWA ? kHA : geo.ha, wa = kWA ? kWA : geo.wa, hb = geo.hb, wb = geo.wb;
     const int Ma = ha * wa;
-    const int WS = kPad ? wa + kPadL + kPadR : wa;     // staged row stride
+    const int WS = kPad ? ((wa + 3) & ~3) + kPadL + kPadR : wa;     // staged row stride
     const int slice_f = geo.slice_f;                   // floats per stage buffer (multiple of 32)
     uint8_t* p = reinterpret_cast<uint8_t*>(
         sm_raw + (((128u - (static_cast<uint32_t>(__cvta_generic_to_shared(sm_raw)) & 127u)) & 127u) >> 2));
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
     const int R = kThreads / wa;
     constexpr int kWdiv = kWA > 0 ? kWA : 1;
     constexpr bool kFull = kWA > 0 && kThreads % kWdiv == 0 && kHA == KR * (kThreads / kWdiv);
-    constexpr int kRStep = (kThreads / kWdiv) * (kWA + (kPad ? kPadL + kPadR : 0));
+    constexpr int kRStep = (kThreads / kWdiv) * (((kWA + 3) & ~3) + (kPad ? kPadL + kPadR : 0));
     const int c = tid % wa, rp = tid / wa;
     const bool active = kFull || rp < R;
     const int nk = kFull ? KR : (active ? max(0, min(KR, (ha - rp + R - 1) / R)) : 0);
@@ -402,6 +405,18 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
     }
 }
 
+// ------------------------------------------------------------ repack
+// Row pitch change for 2-D staging: dst[r * pitch + c] = src[r * wa + c] for the
+// rows of every slice (the pitch's extra columns are left as they are; the
+// tensor map's width is wa, so the copy reads them back as zeros).
+__global__ void __launch_bounds__(256) refocus_repack_kernel(const float* __restrict__ src, float* __restrict__ dst,
+                                                             int64_t n, int wa, int pitch) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = i / wa;
+        dst[r * pitch + (i - r * wa)] = src[i];
+    }
+}
+
 // ------------------------------------------------------------ direct kernel
 // Fallback for spatial images too large for the pipelined kernel's registers:
 // CTA = (range of angular pixels, plane, band of output rows); each angular
@@ -532,10 +547,12 @@ struct PipeCfg {
     int pb, nstep, stages, kr;
 };
 
-bool pad_staging(int ha, int wa) { return wa % 4 == 0 && wa + kPadL + kPadR <= 256 && ha <= 256; }
+int pitch4(int wa) { return (wa + 3) & ~3; }
+
+bool pad_staging(int ha, int wa) { return pitch4(wa) + kPadL + kPadR <= 256 && ha <= 256; }
 
 int slice_floats(int ha, int wa, bool pad) {
-    return pad ? ((ha * (wa + kPadL + kPadR) + 31) & ~31) : pipe_boxes(ha, wa) * kBox;
+    return pad ? ((ha * (pitch4(wa) + kPadL + kPadR) + 31) & ~31) : pipe_boxes(ha, wa) * kBox;
 }
 
 size_t pipe_smem(int ha, int wa, int wb, const PipeCfg& c) {
@@ -648,6 +665,21 @@ int refocus_staging(int ha, int wa, int wb) {
     const RefocusVariant v = refocus_variant(ha, wa, wb);
     if (!v.pipe) return 0;
     return v.cfg.pad ? 2 : 1;
+}
+
+int refocus_pitch(int ha, int wa, int wb) {
+    return refocus_staging(ha, wa, wb) == 2 && wa % 4 != 0 ? pitch4(wa) : 0;
+}
+
+cudaError_t launch_refocus_repack(const float* gamma_f32, float* dst, int64_t rows, int wa, int pitch,
+                                  int sm_count, cudaStream_t st) {
+    const int64_t n = rows * wa;
+    int64_t blocks = (n + 255) / 256;
+    const int64_t cap = 8 * (int64_t)sm_count;
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    refocus_repack_kernel<<<(unsigned)blocks, 256, 0, st>>>(gamma_f32, dst, n, wa, pitch);
+    return cudaGetLastError();
 }
 
 size_t refocus_smem_bytes(int ha, int wa, int wb) {

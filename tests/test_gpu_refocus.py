@@ -39,14 +39,18 @@ def test_refocus_hand_worked():
 
 
 @pytest.mark.parametrize("ha,wa,hb,wb", [
-    (9, 12, 4, 6),        # separable, TMA staging, 2 planes per CTA
+    (9, 12, 4, 6),        # 2-D staging, 8 planes per unit
     (64, 64, 32, 32),     # compile-time 64 x 64 shape
-    (33, 70, 7, 5),       # separable, cp.async staging (width not a multiple of 4)
-    (5, 300, 3, 2),       # TMA box too wide: cp.async staging
-    (96, 96, 8, 8),       # one plane per CTA, 32 rows per thread, TMA
-    (72, 72, 6, 6),       # one plane per CTA, 16 rows per thread
-    (100, 90, 3, 3),      # one plane per CTA, cp.async staging
-    (128, 128, 4, 4),     # one plane per CTA, two staged slices
+    (33, 70, 7, 5),       # width 2 mod 4: 2-D staging from a row-padded copy
+    (17, 33, 5, 3),       # width 1 mod 4
+    (46, 95, 4, 4),       # width 3 mod 4, 2 planes per unit
+    (31, 247, 2, 3),      # widest row-padded 2-D box (248 + 8 columns)
+    (7, 249, 2, 2),       # padded row too wide for a 2-D box: 1-D staging
+    (5, 300, 3, 2),       # 1-D staging, width above 256
+    (96, 96, 8, 8),       # one plane per unit, 32 rows per thread
+    (72, 72, 6, 6),       # one plane per unit, 16 rows per thread
+    (100, 90, 3, 3),      # one plane per unit, row-padded copy
+    (128, 128, 4, 4),     # one plane per unit, two staged slices
     (200, 120, 2, 2),     # 50 rows per thread: direct kernel
 ])
 def test_refocus_random_gamma(ha, wa, hb, wb):
