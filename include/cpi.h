@@ -195,7 +195,8 @@ CPI_API cpi_status cpi_refocus(const float *gamma_f32, int32_t ha, int32_t wa, i
  *   out[p][r][c] = sum over j of Gamma~(u_a, u_b).
  * gamma = 0, delta = 1 is cpi_refocus.  Error: at most ~1e-6 of
  * max|Gamma| times the total in-grid interpolation weight of the output
- * (compensated FP32 sums over the angular columns, FP64 over the rows).
+ * (compensated FP32 sums over the angular columns; over the rows, FP32
+ * double-float sums rounded once).
  *
  *   gamma_f32 : float [hb*wb][ha*wa], slice-major (as cpi_refocus)
  *   planes    : HOST array of n_planes cpi_plane4, |coefficients| <= 1e6

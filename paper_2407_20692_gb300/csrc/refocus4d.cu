@@ -17,8 +17,9 @@
 // one CTA per (ya, yb) for every plane of the chunk, the box staged in shared
 // memory with a 2-pixel zero border (or read from global memory when it does
 // not fit), Kahan-compensated over j_c and stored as a float pair (sum and
-// compensation).  Stage 2 contracts the rows in FP64 (a 1/W_b share of the
-// work):  out[p][x_r][x_c] = sum_{j_r} sum_{ya, yb taps} w w C[p][ya][yb][x_c].
+// compensation).  Stage 2 contracts the rows (a 1/W_b share of the work) in
+// double-float FP32 arithmetic, exact up to one final rounding:
+//     out[p][x_r][x_c] = sum_{j_r} sum_{ya, yb taps} w w C[p][ya][yb][x_c].
 // Coordinates are 32.32 fixed point, A(x) + B(j), each rounded once from FP64;
 // fractions rounded to 24 bits (exact weights).
 //
@@ -86,18 +87,20 @@ __global__ void r4_tables_kernel(const Plane4Block co, int np, int ha, int wa, i
     }
 }
 
-// Stage 1: CTA (yb, ya); every plane of the chunk; threads over x_c.
+// Stage 1: CTA (yb, ya); every plane of the chunk, G planes at a time; thread
+// w of a pass takes plane p0 + w / wa and column x_c = w % wa (so narrow images
+// still give every thread work).  sB holds the G planes' angular-column tables.
 template <bool kSmem>
-__global__ void __launch_bounds__(kR4Threads) r4_cols_kernel(const float* __restrict__ g, int np, int ha, int wa,
-                                                             int hb, int wb, const long long* __restrict__ t,
+__global__ void __launch_bounds__(kR4Threads) r4_cols_kernel(const float* __restrict__ g, int np, int G, int ha,
+                                                             int wa, int hb, int wb, const long long* __restrict__ t,
                                                              int64_t stride, float* __restrict__ c_hi,
                                                              float* __restrict__ c_lo) {
     extern __shared__ __align__(16) float sm[];
     const int yb = blockIdx.x, ya = blockIdx.y;
     const int64_t ma = (int64_t)ha * wa;
     const int WP = wa + 2 * kPad, HP = wb + 2 * kPad;     // padded box: HP rows (xb) x WP columns (xa)
-    long long* sB = reinterpret_cast<long long*>(sm);      // [2][wb]: TBx, TBbx of the current plane
-    float* box = reinterpret_cast<float*>(sB + 2 * wb);
+    long long* sB = reinterpret_cast<long long*>(sm);      // [G][2][wb]: TBx, TBbx of the pass's planes
+    float* box = reinterpret_cast<float*>(sB + 2 * (size_t)G * wb);
     const float* gbase = g + ((int64_t)yb * wb) * ma + (int64_t)ya * wa;   // G[xb][xa] = gbase[xb*ma + xa]
     if constexpr (kSmem) {
         for (int i = threadIdx.x; i < HP * WP; i += kR4Threads) {
@@ -106,20 +109,24 @@ __global__ void __launch_bounds__(kR4Threads) r4_cols_kernel(const float* __rest
             box[i] = (xb >= 0 && xb < wb && xa >= 0 && xa < wa) ? g[(int64_t)(yb * wb + xb) * ma + ya * wa + xa] : 0.0f;
         }
     }
-    for (int p = 0; p < np; ++p) {
-        __syncthreads();   // box ready / previous plane's tables consumed
-        for (int j = threadIdx.x; j < wb; j += kR4Threads) {
-            sB[j] = t[2 * stride + (int64_t)p * wb + j];
-            sB[wb + j] = t[3 * stride + (int64_t)p * wb + j];
+    for (int p0 = 0; p0 < np; p0 += G) {
+        const int gp = min(G, np - p0);
+        __syncthreads();   // box ready / previous pass's tables consumed
+        for (int i = threadIdx.x; i < gp * wb; i += kR4Threads) {
+            const int k = i / wb, j = i - k * wb;
+            sB[(2 * k) * wb + j] = t[2 * stride + (int64_t)(p0 + k) * wb + j];
+            sB[(2 * k + 1) * wb + j] = t[3 * stride + (int64_t)(p0 + k) * wb + j];
         }
         __syncthreads();
-        for (int xc = threadIdx.x; xc < wa; xc += kR4Threads) {
+        for (int w = threadIdx.x; w < gp * wa; w += kR4Threads) {
+            const int k = w / wa, xc = w - k * wa, p = p0 + k;
+            const long long* B = sB + 2 * k * wb;
             const long long ax = t[0 * stride + (int64_t)p * wa + xc];
             const long long abx = t[1 * stride + (int64_t)p * wa + xc];
             float acc = 0.0f, cmp = 0.0f;
             for (int jc = 0; jc < wb; ++jc) {
-                const R4Frac fa = r4_split(ax + sB[jc]);
-                const R4Frac fb = r4_split(abx + sB[wb + jc]);
+                const R4Frac fa = r4_split(ax + B[jc]);
+                const R4Frac fb = r4_split(abx + B[wb + jc]);
                 float v;
                 if constexpr (kSmem) {
                     const int xa = min(max(fa.i, -kPad), wa) + kPad;
@@ -151,16 +158,37 @@ __global__ void __launch_bounds__(kR4Threads) r4_cols_kernel(const float* __rest
     }
 }
 
-// Stage 2: CTA (x_r, plane); threads over x_c; FP64 sums.
+// (sh, sl) += wa * wb * (ch + cl) with error-free FP32 transformations: the
+// weight product and the leading product are split exactly with fused
+// multiply-adds (TwoProduct), the leading term is added by TwoSum; the
+// remaining second-order terms go to sl.  The sum is exact up to O(u^2) per
+// term; one rounding (sh + sl) ends it.
+__device__ __forceinline__ void r4_df_add(float& sh, float& sl, float wa, float wb, float ch, float cl) {
+    const float pw = wa * wb;
+    const float ew = __fmaf_rn(wa, wb, -pw);
+    const float th = pw * ch;
+    float te = __fmaf_rn(pw, ch, -th);
+    te = __fmaf_rn(pw, cl, __fmaf_rn(ew, ch, te));
+    const float s = sh + th;
+    const float bb = s - sh;
+    const float err = (sh - (s - bb)) + (th - bb);
+    sl = sl + (err + te);
+    sh = s;
+}
+
+// Stage 2: CTA (block of G output rows, plane); thread w takes row
+// blockIdx.x * G + w / wa and column w % wa.  Double-float sums (r4_df_add).
 __global__ void __launch_bounds__(kR4Threads) r4_rows_kernel(const float* __restrict__ c_hi,
-                                                             const float* __restrict__ c_lo, int ha, int wa, int hb,
-                                                             const long long* __restrict__ t, int64_t stride,
+                                                             const float* __restrict__ c_lo, int G, int ha, int wa,
+                                                             int hb, const long long* __restrict__ t, int64_t stride,
                                                              float* __restrict__ out) {
-    const int xr = blockIdx.x, p = blockIdx.y;
-    const long long ay = t[4 * stride + (int64_t)p * ha + xr];
-    const long long aby = t[5 * stride + (int64_t)p * ha + xr];
-    for (int xc = threadIdx.x; xc < wa; xc += kR4Threads) {
-        double acc = 0.0;
+    const int p = blockIdx.y;
+    for (int w = threadIdx.x; w < G * wa; w += kR4Threads) {
+        const int k = w / wa, xc = w - k * wa, xr = blockIdx.x * G + k;
+        if (xr >= ha) continue;
+        const long long ay = t[4 * stride + (int64_t)p * ha + xr];
+        const long long aby = t[5 * stride + (int64_t)p * ha + xr];
+        float sh = 0.0f, sl = 0.0f;
         for (int jr = 0; jr < hb; ++jr) {
             const R4Frac fa = r4_split(ay + t[6 * stride + (int64_t)p * hb + jr]);
             const R4Frac fb = r4_split(aby + t[7 * stride + (int64_t)p * hb + jr]);
@@ -168,18 +196,18 @@ __global__ void __launch_bounds__(kR4Threads) r4_rows_kernel(const float* __rest
             for (int db = 0; db < 2; ++db) {
                 const int yb = fb.i + db;
                 if (yb < 0 || yb >= hb) continue;
-                const double wb_ = db ? (double)fb.f : 1.0 - (double)fb.f;
+                const float wbw = db ? fb.f : 1.0f - fb.f;
 #pragma unroll
                 for (int da = 0; da < 2; ++da) {
                     const int ya = fa.i + da;
                     if (ya < 0 || ya >= ha) continue;
-                    const double w = wb_ * (da ? (double)fa.f : 1.0 - (double)fa.f);
+                    const float waw = da ? fa.f : 1.0f - fa.f;
                     const int64_t o = (((int64_t)p * ha + ya) * hb + yb) * wa + xc;
-                    acc += w * ((double)c_hi[o] + (double)c_lo[o]);
+                    r4_df_add(sh, sl, waw, wbw, c_hi[o], c_lo[o]);
                 }
             }
         }
-        out[((int64_t)p * ha + xr) * wa + xc] = (float)acc;
+        out[((int64_t)p * ha + xr) * wa + xc] = sh + sl;
     }
 }
 
@@ -209,9 +237,19 @@ Refocus4dLayout refocus4d_layout(int ha, int wa, int hb, int wb, int n_planes) {
     return L;
 }
 
+namespace {
+// planes per pass of the column stage and the shared memory it takes
+int r4_col_group(int wa, int wb, int np) {
+    int G = wa < kR4Threads ? kR4Threads / wa : 1;
+    if (G > np) G = np;
+    while (G > 1 && (size_t)G * 2 * wb * sizeof(long long) > 16 * 1024) --G;
+    return G < 1 ? 1 : G;
+}
+size_t r4_box_bytes(int wa, int wb) { return sizeof(float) * (size_t)(wb + 2 * kPad) * (wa + 2 * kPad); }
+}  // namespace
+
 bool refocus4d_box_fits(int wa, int wb) {
-    const size_t smem = sizeof(long long) * 2 * (size_t)wb + sizeof(float) * (size_t)(wb + 2 * kPad) * (wa + 2 * kPad);
-    return smem <= 200 * 1024;
+    return sizeof(long long) * 2 * (size_t)wb + r4_box_bytes(wa, wb) <= 200 * 1024;
 }
 
 cudaError_t launch_refocus4d_chunk(const float* gamma_f32, int ha, int wa, int hb, int wb, const Plane4Block& coef,
@@ -223,8 +261,10 @@ cudaError_t launch_refocus4d_chunk(const float* gamma_f32, int ha, int wa, int h
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const dim3 g1((unsigned)hb, (unsigned)ha);
+    int G = r4_col_group(wa, wb, np);
     if (refocus4d_box_fits(wa, wb)) {
-        const size_t smem = sizeof(long long) * 2 * (size_t)wb + sizeof(float) * (size_t)(wb + 2 * kPad) * (wa + 2 * kPad);
+        while (G > 1 && sizeof(long long) * 2 * (size_t)G * wb + r4_box_bytes(wa, wb) > 200 * 1024) --G;
+        const size_t smem = sizeof(long long) * 2 * (size_t)G * wb + r4_box_bytes(wa, wb);
         static bool attr[64] = {};
         int dev = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
@@ -235,13 +275,15 @@ cudaError_t launch_refocus4d_chunk(const float* gamma_f32, int ha, int wa, int h
                 return e;
             attr[dev] = true;
         }
-        r4_cols_kernel<true><<<g1, kR4Threads, smem, st>>>(gamma_f32, np, ha, wa, hb, wb, t, L.stride, c_hi, c_lo);
+        r4_cols_kernel<true><<<g1, kR4Threads, smem, st>>>(gamma_f32, np, G, ha, wa, hb, wb, t, L.stride, c_hi, c_lo);
     } else {
-        r4_cols_kernel<false><<<g1, kR4Threads, sizeof(long long) * 2 * (size_t)wb, st>>>(gamma_f32, np, ha, wa, hb,
-                                                                                         wb, t, L.stride, c_hi, c_lo);
+        r4_cols_kernel<false><<<g1, kR4Threads, sizeof(long long) * 2 * (size_t)G * wb, st>>>(
+            gamma_f32, np, G, ha, wa, hb, wb, t, L.stride, c_hi, c_lo);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    r4_rows_kernel<<<dim3((unsigned)ha, (unsigned)np), kR4Threads, 0, st>>>(c_hi, c_lo, ha, wa, hb, t, L.stride, out);
+    const int Gr = wa < kR4Threads ? kR4Threads / wa : 1;
+    r4_rows_kernel<<<dim3((unsigned)((ha + Gr - 1) / Gr), (unsigned)np), kR4Threads, 0, st>>>(c_hi, c_lo, Gr, ha, wa,
+                                                                                            hb, t, L.stride, out);
     return cudaGetLastError();
 }
 

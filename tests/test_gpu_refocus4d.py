@@ -3,10 +3,10 @@
 Tolerance, per unit of interpolation weight as for the 2-D refocusing:
 |R_gpu - R_fp64| <= 1e-6 max|Gamma| W_p(x), W_p(x) the total in-grid weight
 (the refocusing of an all-ones Gamma).  The kernels' error: Gamma rounded to FP32
-(u/2), four weight fractions rounded to 24 bits (u each), the 16-tap sample in
-FP32 (about 4u of the summed terms), Kahan sums over the angular columns (2u),
-the column sums kept as float pairs and the row stage in FP64: about 10.5u,
-6.3e-7."""
+(u/2), four weight fractions rounded to 24 bits (u each), the 4-tap column
+sample in FP32 (about 4u of the summed terms), Kahan sums over the angular
+columns (2u), the column sums kept as float pairs, the row stage in double-float
+FP32 (exact up to the final rounding, u/2): about 11u, 6.6e-7."""
 
 import numpy as np
 import pytest
@@ -43,6 +43,8 @@ _CO = (np.array([0.6, 1.0, 1.3, 0.9, 1.0]), np.array([0.4, 0.0, -0.3, 0.25, 0.0]
     (16, 12, 6, 8),
     (2, 260, 2, 200),      # box too large for shared memory: global-memory path
     (33, 17, 3, 2),
+    (12, 100, 5, 6),       # two planes per column pass, the last pass ragged
+    (9, 300, 3, 4),        # wider than a CTA's threads: columns loop
 ])
 def test_refocus4d_random_gamma_matches_oracle(ha, wa, hb, wb):
     rng = np.random.default_rng(ha * 100 + wa)
