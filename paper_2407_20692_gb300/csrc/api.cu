@@ -484,6 +484,66 @@ cpi_status launch_batch_moments(const cpi_batch_item* items, const BatchPlan& bp
     return CPI_OK;
 }
 
+// The batch's refocusings are spread over kRefocusForks side streams (parallel
+// branches when captured into a graph), longest first, each to the branch with
+// the least work so far, so that one item's tail overlaps the others' work.
+constexpr int kRefocusForks = 4;
+struct ForkStreams {
+    std::mutex mu;
+    bool ready[kMaxDevices] = {};
+    cudaStream_t side[kMaxDevices][kRefocusForks] = {};
+    cudaEvent_t fork[kMaxDevices] = {};
+    cudaEvent_t join[kMaxDevices][kRefocusForks] = {};
+};
+ForkStreams g_forks;
+
+cpi_status run_batch_refocus(const cpi_batch_item* items, const BatchPlan& bp, uint8_t* ws, cudaStream_t st) {
+    std::vector<int> rf;
+    for (int i = 0; i < (int)bp.it.size(); ++i)
+        if (items[i].n_planes > 0) rf.push_back(i);
+    auto one = [&](int i, cudaStream_t s) {
+        const cpi_batch_item& b = items[i];
+        return run_refocus(b.gamma_f32, b.a.height, b.a.width, b.b.height, b.b.width, b.planes, b.n_planes,
+                           b.refocus_out, ws + bp.it[i].rws_off, bp.it[i].rws_bytes, s);
+    };
+    if (rf.size() < 2) return rf.empty() ? CPI_OK : one(rf[0], st);
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CPI_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_forks.mu);
+    if (!g_forks.ready[dev]) {
+        if (cudaEventCreateWithFlags(&g_forks.fork[dev], cudaEventDisableTiming) != cudaSuccess) return CPI_ERR_CUDA;
+        for (int k = 0; k < kRefocusForks; ++k)
+            if (cudaStreamCreateWithFlags(&g_forks.side[dev][k], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&g_forks.join[dev][k], cudaEventDisableTiming) != cudaSuccess)
+                return CPI_ERR_CUDA;
+        g_forks.ready[dev] = true;
+    }
+    auto cost = [&](int i) {
+        const cpi_batch_item& b = items[i];
+        return (double)b.n_planes * b.a.height * b.a.width * b.b.height * b.b.width;
+    };
+    std::stable_sort(rf.begin(), rf.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    if (cudaEventRecord(g_forks.fork[dev], st) != cudaSuccess) return CPI_ERR_CUDA;
+    for (int k = 0; k < kRefocusForks; ++k)
+        if (cudaStreamWaitEvent(g_forks.side[dev][k], g_forks.fork[dev], 0) != cudaSuccess) return CPI_ERR_CUDA;
+    double load[kRefocusForks] = {};
+    cpi_status result = CPI_OK;
+    for (int i : rf) {
+        int k = 0;
+        for (int q = 1; q < kRefocusForks; ++q)
+            if (load[q] < load[k]) k = q;
+        load[k] += cost(i);
+        result = one(i, g_forks.side[dev][k]);
+        if (result != CPI_OK) break;
+    }
+    // join every branch, also after an error (a capture must not end with a branch open)
+    for (int k = 0; k < kRefocusForks; ++k)
+        if (cudaEventRecord(g_forks.join[dev][k], g_forks.side[dev][k]) != cudaSuccess ||
+            cudaStreamWaitEvent(st, g_forks.join[dev][k], 0) != cudaSuccess)
+            result = CPI_ERR_CUDA;
+    return result;
+}
+
 cpi_status run_batch(const cpi_batch_item* items, const BatchPlan& bp, uint8_t* ws, DeviceInfo* dev,
                      cudaStream_t st) {
     const int n = (int)bp.it.size();
@@ -501,14 +561,7 @@ cpi_status run_batch(const cpi_batch_item* items, const BatchPlan& bp, uint8_t* 
                       b.gamma_f32, ws + bp.it[i].ws_off, dev, st);
         if (s != CPI_OK) return s;
     }
-    for (int i = 0; i < n; ++i) {
-        const cpi_batch_item& b = items[i];
-        if (b.n_planes == 0) continue;
-        s = run_refocus(b.gamma_f32, b.a.height, b.a.width, b.b.height, b.b.width, b.planes, b.n_planes,
-                        b.refocus_out, ws + bp.it[i].rws_off, bp.it[i].rws_bytes, st);
-        if (s != CPI_OK) return s;
-    }
-    return CPI_OK;
+    return run_batch_refocus(items, bp, ws, st);
 }
 
 uint64_t fnv(uint64_t h, const void* p, size_t n) {

@@ -128,9 +128,9 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* m, uin
 // each staged slice and each plane of the unit it reads its x taps (from a
 // per-plane-block table when it fits in shared memory, else computes them),
 // adds NSTEP slices with fused multiply-adds and Kahan-adds the step's sum into
-// its U values.  After the unit's last slice the U images go to shared memory
-// and are interpolated along y; this angular row's contribution to each output
-// pixel is written to partial[br][plane][pixel].
+// its U values.  After the unit's last slice each plane's U image in turn goes
+// to shared memory and is interpolated along y; this angular row's contribution
+// to each output pixel is written to partial[br][plane][pixel].
 //
 // Every wait is bounded (the device status word records a time out).  A slice
 // that never arrives stops every thread at that same slice, so no barrier is
@@ -203,12 +203,11 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
     p += sizeof(long long) * (size_t)PB * wa;
     long long* const bx = reinterpret_cast<long long*>(p);        // [PB][wb]
     p += sizeof(long long) * (size_t)PB * wb;
-    float* const U = reinterpret_cast<float*>(p);                 // [PB][ha + 2*kUPad][wa]
+    float* const U = reinterpret_cast<float*>(p);                 // [ha + 2*kUPad][wa], one plane at a time
     __shared__ __align__(8) uint64_t full[kMaxStages];
     __shared__ unsigned int relcnt[kMaxStages];
 
     const int tid = threadIdx.x, lane = tid & 31;
-    const int UH = ha + 2 * kUPad;
     const int n_pb = (geo.n_planes + PB - 1) / PB;
     const int n_units = hb * n_pb;
     const int n_mine = blockIdx.x < n_units ? (n_units - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
@@ -242,10 +241,9 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
         }
         fence_barrier_init();
     }
-    for (int i = tid; i < PB * 2 * kUPad * wa; i += kThreads) {   // zero border rows of U
-        const int j = i / (2 * kUPad * wa), rem = i - j * 2 * kUPad * wa;
-        const int row = rem / wa, x = rem - row * wa;
-        U[(j * UH + (row < kUPad ? row : ha + row)) * wa + x] = 0.0f;
+    for (int i = tid; i < 2 * kUPad * wa; i += kThreads) {   // zero border rows of U
+        const int row = i / wa, x = i - row * wa;
+        U[(row < kUPad ? row : ha + row) * wa + x] = 0.0f;
     }
     __syncthreads();
     if (tid == 0)
@@ -371,25 +369,24 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
             }
         }
 
-        // y-interpolation of this angular row
+        // y-interpolation of this angular row, one plane at a time through U
         __syncthreads();   // the previous unit's U and y taps are no longer read
-#pragma unroll
-        for (int j = 0; j < PB; ++j)
-#pragma unroll
-            for (int kk = 0; kk < KR; ++kk)
-                if (j < np && (kFull || kk < nk)) U[(j * UH + rp + R * kk + kUPad) * wa + c] = Ua[j][kk] - Uc[j][kk];
         for (int i = tid; i < np * ha; i += kThreads) {
             const int j = i / ha, r = i - j * ha;
             const long long uy = fix32(pl.alpha[p0 + j] * ((double)r - cya) + cya) +
                                  fix32((pl.beta[p0 + j] * sy) * ((double)br - cyb));
             PTap t = padded_tap(uy, ha);
-            t.off = (j * UH + t.off) * wa;
+            t.off *= wa;
             yt[i] = t;
         }
-        __syncthreads();
 #pragma unroll
         for (int j = 0; j < PB; ++j) {
             if (j < np) {
+                if (j > 0) __syncthreads();   // U of the previous plane is no longer read
+#pragma unroll
+                for (int kk = 0; kk < KR; ++kk)
+                    if (kFull || kk < nk) U[(rp + R * kk + kUPad) * wa + c] = Ua[j][kk] - Uc[j][kk];
+                __syncthreads();
                 float* dst = partial + ((int64_t)br * geo.total_planes + geo.plane_offset + p0 + j) * Ma;
 #pragma unroll
                 for (int kk = 0; kk < KR; ++kk) {
@@ -560,7 +557,7 @@ size_t pipe_smem(int ha, int wa, int wb, const PipeCfg& c) {
     if (c.table) b += (c.pad ? sizeof(XTab<true>) : sizeof(XTab<false>)) * (size_t)c.pb * wb * wa;
     b += (sizeof(PTap) * (size_t)c.pb * ha + 15) & ~(size_t)15;
     b += sizeof(long long) * (size_t)c.pb * (wa + wb);
-    b += sizeof(float) * (size_t)c.pb * (ha + 2 * kUPad) * wa;
+    b += sizeof(float) * (size_t)(ha + 2 * kUPad) * wa;
     return b;
 }
 
