@@ -97,15 +97,15 @@ bool make_operand_map(CUtensorMap* m, void* base, bool bf16, int64_t rows, int64
 }
 
 // Slice-major FP32 Gamma as [Mb * ha rows][wa columns], rows pitch floats apart
-// (a multiple of 4); box (wa4 + 8) x ha starting at column -4 (wa4 = wa rounded
+// (a multiple of 4); box (wa4 + 8) x box_rows starting at column -4 (wa4 = wa rounded
 // up to a multiple of 4) returns each slice with zeros in every column outside
-// 0 .. wa-1.
-bool make_slice_map(CUtensorMap* m, const float* g, int ha, int wa, int64_t mb, int pitch) {
+// 0 .. wa-1 (box_rows: the slice's ha rows and a few of the next slice's).
+bool make_slice_map(CUtensorMap* m, const float* g, int ha, int wa, int64_t mb, int pitch, int box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
     cuuint64_t dims[2] = {(cuuint64_t)wa, (cuuint64_t)(mb * ha)};
     cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)(((wa + 3) & ~3) + 8), (cuuint32_t)ha};
+    cuuint32_t box[2] = {(cuuint32_t)(((wa + 3) & ~3) + 8), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(g), dims, strides, box,
                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -352,7 +352,8 @@ cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
             if (e != cudaSuccess) return CPI_ERR_CUDA;
             src = copy;
         }
-        if (!make_slice_map(&tm, src, ha, wa, (int64_t)hb * wb, pitch != 0 ? pitch : wa)) return CPI_ERR_CUDA;
+        if (!make_slice_map(&tm, src, ha, wa, (int64_t)hb * wb, pitch != 0 ? pitch : wa, refocus_box_rows(ha, wa)))
+            return CPI_ERR_CUDA;
     }
     PlaneBlock pb;
     for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {

@@ -112,6 +112,8 @@ int refocus_staging(int ha, int wa, int wb);
 // Row pitch (floats) of the padded copy of Gamma that 2-D staging needs when wa
 // is not a multiple of 4, else 0 (Gamma is staged from the caller's buffer).
 int refocus_pitch(int ha, int wa, int wb);
+// Rows of one staged slice box (the slice's ha rows and up to NK - 1 more).
+int refocus_box_rows(int ha, int wa);
 // dst[r * pitch + c] = gamma_f32[r * wa + c] for rows r < rows, c < wa.
 cudaError_t launch_refocus_repack(const float* gamma_f32, float* dst, int64_t rows, int wa, int pitch,
                                   int sm_count, cudaStream_t st);

@@ -140,6 +140,20 @@ constexpr int kMaxStages = 4;
 constexpr int kPadL = 4;         // zero columns left of a 2-D staged row (TMA x start -4)
 constexpr int kPadR = 4;
 
+// Rows of the spatial image per thread: NK = ceil(ha / floor(kThreads / wa)),
+// the threads of one column split the rows into R = ceil(ha / NK) row sets
+// (thread row rp takes rows rp, rp + R, ...).  Every thread runs NK rows; the
+// R * NK - ha (< NK) rows past the image are staged too (the next slice's rows,
+// or zeros past Gamma's end) and their sums are dropped.
+struct RowSplit {
+    int R, NK;
+};
+__host__ __device__ inline RowSplit row_split(int ha, int wa) {
+    const int r0 = kThreads / wa;
+    const int nk = (ha + r0 - 1) / r0;
+    return {(ha + nk - 1) / nk, nk};
+}
+
 template <bool kPad>
 struct XTab;
 template <>
@@ -215,7 +229,9 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
     const double cxa = 0.5 * (double)(wa - 1), cya = 0.5 * (double)(ha - 1);
     const double cxb = 0.5 * (double)(wb - 1), cyb = 0.5 * (double)(hb - 1);
     const double sx = (double)wa / (double)wb, sy = (double)ha / (double)hb;
-    const uint32_t stage_bytes = (uint32_t)(kPad ? ha * WS * sizeof(float) : geo.boxes * kBox * sizeof(float));
+    const RowSplit rs = row_split(ha, wa);
+    const int BH = rs.R * rs.NK;                       // staged rows per slice (>= ha)
+    const uint32_t stage_bytes = (uint32_t)(kPad ? BH * WS * sizeof(float) : geo.boxes * kBox * sizeof(float));
 
     // slice q of this CTA (q-th slice of its unit sequence) -> stage q % kStages
     auto issue = [&](uint32_t q) {
@@ -249,12 +265,13 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
     if (tid == 0)
         for (uint32_t q = 0; q < (uint32_t)kStages && q < total_sl; ++q) issue(q);
 
-    const int R = kThreads / wa;
+    const int R = rs.R, NK = rs.NK;
     constexpr int kWdiv = kWA > 0 ? kWA : 1;
     constexpr bool kFull = kWA > 0 && kThreads % kWdiv == 0 && kHA == KR * (kThreads / kWdiv);
     constexpr int kRStep = (kThreads / kWdiv) * (((kWA + 3) & ~3) + (kPad ? kPadL + kPadR : 0));
     const int c = tid % wa, rp = tid / wa;
     const bool active = kFull || rp < R;
+    // rows of the image this thread owns (the U writes); it computes NK rows
     const int nk = kFull ? KR : (active ? max(0, min(KR, (ha - rp + R - 1) / R)) : 0);
     const int rstep = R * WS;
     uint32_t g = 0;          // slices of this CTA consumed so far
@@ -312,32 +329,60 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
                 const int sh1 = kPad ? 0 : (int)(((long long)(br * wb + bc0 + 1) * Ma) & 3);
                 const float* S0 = buf0 + (size_t)s0 * slice_f + rp * WS + sh0;
                 const float* S1 = buf0 + (size_t)s1 * slice_f + rp * WS + sh1;
+                // rows outer, planes inner (groups of 2 or 4 planes with their
+                // taps in registers); planes past the block's last take its taps
+                // and rows past the image are computed from staged data, both
+                // dropped at the U writes
+                constexpr int PG = KR >= 8 ? (PB < 2 ? PB : 2) : (PB < 4 ? PB : 4);
+                const bool two = NSTEP == 2 && nsl == 2;
 #pragma unroll
-                for (int j = 0; j < PB; ++j) {
-                    if (j < np) {
+                for (int g0 = 0; g0 < PB; g0 += PG) {
+                    const float* qa[PG];
+                    const float* qb[PG];
+                    float a0[PG], a1[PG], b0[PG], b1[PG];
+#pragma unroll
+                    for (int jj = 0; jj < PG; ++jj) {
+                        const int j = min(g0 + jj, np - 1);
                         int oa, ob = 0;
-                        float a0, a1, b0 = 0.0f, b1 = 0.0f;
+                        b0[jj] = 0.0f;
+                        b1[jj] = 0.0f;
                         if constexpr (kTable) {
-                            read_xtab<kPad>(&xtab[(j * wb + bc0) * wa + c], oa, a0, a1);
-                            if (NSTEP == 2 && nsl == 2)
-                                read_xtab<kPad>(&xtab[(j * wb + bc0 + 1) * wa + c], ob, b0, b1);
+                            read_xtab<kPad>(&xtab[(j * wb + bc0) * wa + c], oa, a0[jj], a1[jj]);
+                            if (two) read_xtab<kPad>(&xtab[(j * wb + bc0 + 1) * wa + c], ob, b0[jj], b1[jj]);
                         } else {
                             const XTab<kPad> ta = make_xtab<kPad>(ax[j * wa + c] + bx[j * wb + bc0], wa, 0);
-                            read_xtab<kPad>(&ta, oa, a0, a1);
-                            if (NSTEP == 2 && nsl == 2) {
+                            read_xtab<kPad>(&ta, oa, a0[jj], a1[jj]);
+                            if (two) {
                                 const XTab<kPad> tb = make_xtab<kPad>(ax[j * wa + c] + bx[j * wb + bc0 + 1], wa, 0);
-                                read_xtab<kPad>(&tb, ob, b0, b1);
+                                read_xtab<kPad>(&tb, ob, b0[jj], b1[jj]);
                             }
                         }
-                        const float* qa = S0 + oa;
-                        const float* qb = S1 + ob;
+                        qa[jj] = S0 + oa;
+                        qb[jj] = S1 + ob;
+                    }
+                    if (two) {
 #pragma unroll
                         for (int kk = 0; kk < KR; ++kk) {
-                            if (kFull || kk < nk) {
+                            if (kFull || kk < NK) {
                                 const int o = kWA ? kk * kRStep : kk * rstep;
-                                float t = __fmaf_rn(a1, qa[o + 1], a0 * qa[o]);
-                                if (NSTEP == 2 && nsl == 2) t = __fmaf_rn(b1, qb[o + 1], __fmaf_rn(b0, qb[o], t));
-                                kahan_add(Ua[j][kk], Uc[j][kk], t);
+#pragma unroll
+                                for (int jj = 0; jj < PG; ++jj) {
+                                    float t = __fmaf_rn(a1[jj], qa[jj][o + 1], a0[jj] * qa[jj][o]);
+                                    t = __fmaf_rn(b1[jj], qb[jj][o + 1], __fmaf_rn(b0[jj], qb[jj][o], t));
+                                    kahan_add(Ua[g0 + jj][kk], Uc[g0 + jj][kk], t);
+                                }
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int kk = 0; kk < KR; ++kk) {
+                            if (kFull || kk < NK) {
+                                const int o = kWA ? kk * kRStep : kk * rstep;
+#pragma unroll
+                                for (int jj = 0; jj < PG; ++jj) {
+                                    const float t = __fmaf_rn(a1[jj], qa[jj][o + 1], a0[jj] * qa[jj][o]);
+                                    kahan_add(Ua[g0 + jj][kk], Uc[g0 + jj][kk], t);
+                                }
                             }
                         }
                     }
@@ -531,8 +576,13 @@ constexpr size_t kSmemCap = 220 * 1024;
 
 // 1-D staging: 256-element boxes covering the slice from the 16-byte boundary
 // at or below its start (and one value past it when wa == 1).
+int box_rows(int ha, int wa) {
+    const RowSplit rs = row_split(ha, wa);
+    return rs.R * rs.NK;
+}
+
 int pipe_boxes(int ha, int wa) {
-    const int64_t ma = (int64_t)ha * wa;
+    const int64_t ma = (int64_t)box_rows(ha, wa) * wa;
     const int64_t lead = (ma % 4 == 0) ? 0 : 3;
     const int64_t tail = (wa == 1) ? 1 : 0;
     return (int)((lead + ma + tail + kBox - 1) / kBox);
@@ -546,10 +596,10 @@ struct PipeCfg {
 
 int pitch4(int wa) { return (wa + 3) & ~3; }
 
-bool pad_staging(int ha, int wa) { return pitch4(wa) + kPadL + kPadR <= 256 && ha <= 256; }
+bool pad_staging(int ha, int wa) { return pitch4(wa) + kPadL + kPadR <= 256 && box_rows(ha, wa) <= 256; }
 
 int slice_floats(int ha, int wa, bool pad) {
-    return pad ? ((ha * (pitch4(wa) + kPadL + kPadR) + 31) & ~31) : pipe_boxes(ha, wa) * kBox;
+    return pad ? ((box_rows(ha, wa) * (pitch4(wa) + kPadL + kPadR) + 31) & ~31) : pipe_boxes(ha, wa) * kBox;
 }
 
 size_t pipe_smem(int ha, int wa, int wb, const PipeCfg& c) {
@@ -561,10 +611,7 @@ size_t pipe_smem(int ha, int wa, int wb, const PipeCfg& c) {
     return b;
 }
 
-int rows_per_thread(int ha, int wa) {
-    const int R = kThreads / wa;
-    return R > 0 ? (ha + R - 1) / R : 1 << 30;
-}
+int rows_per_thread(int ha, int wa) { return wa <= kThreads ? row_split(ha, wa).NK : 1 << 30; }
 
 int pow2_at_least(int v, int lo) {
     int k = lo;
@@ -663,6 +710,8 @@ int refocus_staging(int ha, int wa, int wb) {
     if (!v.pipe) return 0;
     return v.cfg.pad ? 2 : 1;
 }
+
+int refocus_box_rows(int ha, int wa) { return box_rows(ha, wa); }
 
 int refocus_pitch(int ha, int wa, int wb) {
     return refocus_staging(ha, wa, wb) == 2 && wa % 4 != 0 ? pitch4(wa) : 0;
