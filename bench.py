@@ -270,7 +270,7 @@ def run_native(args, world, rank, local):
 
     # ---------------------------------------------------------------- roofline
     roofs = rooflines(ma, mb, n, n_planes, acq.bits, dict(ingest=ingest_ms, moments=moments_ms,
-                                                          fold=fold_ms, refocus=refocus_ms))
+                                                          fold=fold_ms, refocus=refocus_ms), args.workload)
     dominant = max(roofs, key=lambda k: roofs[k]["ms"])
     roof = dict(roofs[dominant])
     # ---------------------------------------------------------------- e2e through the C ABI
@@ -331,9 +331,10 @@ SM_COUNT = 152
 SMEM_BYTES_PER_CLK = 128          # shared-memory load bandwidth per SM per clock
 
 
-def _traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, valid only while the
-    kernel's source files are unchanged since the capture (else None)."""
+def _traffic(kernel_key, workload):
+    """DRAM bytes per launch from the committed ncu summary, valid only for the
+    workload it was captured on and while the kernel's source files are unchanged
+    since the capture (else None)."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "traffic.json")
@@ -342,7 +343,7 @@ def _traffic(kernel_key):
     with open(path) as f:
         table = json.load(f)
     ent = table.get(kernel_key)
-    if not ent:
+    if not ent or ent.get("workload") != workload:
         return None
     h = hashlib.sha256()
     for rel in ent["sources"]:
@@ -355,7 +356,7 @@ def _traffic(kernel_key):
     return ent["dram_bytes_per_launch"]
 
 
-def rooflines(ma, mb, n, n_planes, bits, ms):
+def rooflines(ma, mb, n, n_planes, bits, ms, workload):
     """Roofline of each stage: algorithmic work per launch / measured time,
     against the measured peak of its bound (MEASURED_PEAKS.json)."""
     peaks, src = _peaks()
@@ -369,7 +370,7 @@ def rooflines(ma, mb, n, n_planes, bits, ms):
         kname = "moments (tcgen05 kind::f16, BF16 integer operands)"
     a = ops / (ms["moments"] / 1e3) / 1e12
     out["moments"] = {"kernel": kname, "bound": "tensor", "achieved": a, "peak": tc_peak,
-                      "unit": "TFLOP/s", "frac": a / tc_peak, "traffic": _traffic("moments"),
+                      "unit": "TFLOP/s", "frac": a / tc_peak, "traffic": _traffic("moments", workload),
                       "peak_source": tc_src, "ms": ms["moments"],
                       "work": "2*Ma*Mb*N int8-equivalent ops"}
     kpad = (n + 255) // 256 * 256 if bits == 1 else (n + 127) // 128 * 128
@@ -377,13 +378,13 @@ def rooflines(ma, mb, n, n_planes, bits, ms):
     a = ing / (ms["ingest"] / 1e3) / 1e9
     out["ingest"] = {"kernel": "ingest (frames -> K-major operands, marginals)", "bound": "hbm",
                      "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
-                     "traffic": _traffic("ingest"), "peak_source": f"{src} hbm copy", "ms": ms["ingest"],
+                     "traffic": _traffic("ingest", workload), "peak_source": f"{src} hbm copy", "ms": ms["ingest"],
                      "work": "frame bytes read + operand bytes written"}
     fb = ma * mb * (4 + 8 + 8 + 4)
     a = fb / (ms["fold"] / 1e3) / 1e9
     out["fold"] = {"kernel": "fold (int64 S_ab, FP64 Gamma, FP32 slice-major copy)", "bound": "hbm",
                    "achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": a / peaks["hbm_gbs"],
-                   "traffic": _traffic("fold"), "peak_source": f"{src} hbm copy", "ms": ms["fold"],
+                   "traffic": _traffic("fold", workload), "peak_source": f"{src} hbm copy", "ms": ms["fold"],
                    "work": "24 B per Gamma entry"}
     # Refocus, as the workload's metric defines it: per-plane Gamma FP32 traffic
     # (P planes x Ma x Mb x 4 B, what an unfused per-plane gather reads) per
@@ -396,7 +397,7 @@ def rooflines(ma, mb, n, n_planes, bits, ms):
     a = smem / (ms["refocus"] / 1e3) / 1e9
     out["refocus"] = {"kernel": "refocus (pipelined bilinear shift-and-sum, 4 planes per Gamma pass, + row reduce)",
                       "bound": "hbm", "achieved": eff, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                      "frac": eff / peaks["hbm_gbs"], "traffic": _traffic("refocus"),
+                      "frac": eff / peaks["hbm_gbs"], "traffic": _traffic("refocus", workload),
                       "peak_source": f"{src} hbm copy", "ms": ms["refocus"],
                       "work": "P x Ma x Mb x 4 B (one FP32 Gamma read per plane)",
                       "lsu": {"achieved": a, "peak": smem_peak, "unit": "GB/s", "frac": a / smem_peak,
@@ -860,17 +861,29 @@ def run_refocus4d(args, world, rank):
     peaks, src = _peaks()
     return {
         "metric": "4-D multilinear refocusing planes/s, 128x128 vs 128x128 Gamma (16384 x 16384), 261 planes",
-        "value": head["planes_per_s"], "unit": "planes/s", "n_gpus": world, "steps": 3, "warmup": 1,
+        "value": head["planes_per_s"], "unit": "planes/s", "n_gpus": world,
+        "steps": args.steps if args.r4_side else 3, "warmup": 1,
         "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 sums (compensated) over angular columns, f64 over angular rows",
         "data": "synthetic (random FP32 Gamma)",
         "config": {"workload": "refocus4d", "cases": list(res), "parallelism": f"replicas x{world}"},
         "cases": res,
-        "roofline": {"kernel": "4-D refocusing (column stage + FP64 row stage)", "bound": "hbm",
+        # As for the 2-D refocusing: per-plane Gamma FP32 traffic (what a per-plane
+        # gather reads) against the HBM copy peak.  The column stage reads Gamma
+        # from HBM once per 64 planes and is bound on chip (instruction issue and
+        # shared-memory loads: 16 B of box loads per column-stage sample).
+        "roofline": {"kernel": "4-D refocusing (column stage + double-float row stage)", "bound": "hbm",
                      "achieved": head["per_plane_gamma_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": head["per_plane_gamma_gbs"] / peaks["hbm_gbs"], "traffic": None,
                      "peak_source": f"{src} hbm copy",
-                     "work": "P x Ma x Mb x 4 B (one FP32 Gamma read per plane)"},
+                     "work": "P x Ma x Mb x 4 B (one FP32 Gamma read per plane)",
+                     "lsu": {"achieved": head["per_plane_gamma_gbs"] * 4.0,
+                             "peak": SM_COUNT * SMEM_BYTES_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9,
+                             "unit": "GB/s",
+                             "frac": head["per_plane_gamma_gbs"] * 4.0 / (
+                                 SM_COUNT * SMEM_BYTES_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9),
+                             "peak_source": "derived: 152 SMs x 128 B/clk shared-memory loads x max SM clock",
+                             "work": "16 B of shared-memory box loads per (plane, spatial pixel, angular pixel)"}},
         "gpu_launches": None,
     }
 

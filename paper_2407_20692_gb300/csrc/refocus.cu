@@ -292,11 +292,14 @@ __global__ void __launch_bounds__(kThreads, 1) refocus_pipe_kernel(const __grid_
                 bx[i] = fix32((pl.beta[p0 + j] * sx) * ((double)b - cxb));
             }
             __syncthreads();
-            if constexpr (kTable) {
-                for (int i = tid; i < np * wb * wa; i += kThreads) {
-                    const int j = i / (wb * wa), rem = i - j * wb * wa;
-                    const int b = rem / wa, x = rem - b * wa;
-                    xtab[i] = make_xtab<kPad>(ax[j * wa + x] + bx[j * wb + b], wa, 0);
+            if constexpr (kTable) {   // thread (rp, c) fills column c of table rows rp, rp + r0, ...
+                const int r0 = kThreads / wa;
+                if (rp < r0) {
+                    for (int j = 0; j < np; ++j) {
+                        const long long axj = ax[j * wa + c];
+                        for (int b = rp; b < wb; b += r0)
+                            xtab[(j * wb + b) * wa + c] = make_xtab<kPad>(axj + bx[j * wb + b], wa, 0);
+                    }
                 }
                 __syncthreads();
             }
