@@ -277,6 +277,14 @@ def run_native(args, world, rank, local):
     e2e = e2e_run(args, cpi, fr, lay, n, stream, dev, planes, n_planes, ws, rws)
     e2e_value = world * ops / _max_over_ranks(world, e2e["s_per_step"]) / 1e12
 
+    # ---------------------------------------------------------------- graph-replayed step
+    # The same step as one cpi_batch_correlate call with a single item: captured
+    # into a CUDA graph on first use and replayed (what a fixed-shape acquisition
+    # loop calls; removes the per-launch host dispatch that bounds small shapes).
+    graph_ms = graph_leg(args, cpi, dict(a=a, b=b, n_frames=n, s_ab=s_ab, s_a=s_a, s_b=s_b, gamma=gamma,
+                                         gamma_f32=g32, planes=planes, refocus_out=out), flush, stream, dev)
+    graph_ms = _max_over_ranks(world, graph_ms / 1e3) * 1e3
+
     # ---------------------------------------------------------------- CPU baseline (rank 0)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -318,6 +326,9 @@ def run_native(args, world, rank, local):
         "e2e": {"value": e2e_value, "unit": "TOPS (int8-equivalent)",
                 "h2d_bytes_per_step": e2e["h2d"], "d2h_bytes_per_step": e2e["d2h"],
                 "ms_per_step": e2e["s_per_step"] * 1e3},
+        "graph_replay": {"ms_per_step": graph_ms, "value": world * ops / (graph_ms / 1e3) / 1e12,
+                         "unit": "TOPS (int8-equivalent)",
+                         "call": "cpi_batch_correlate, one item, CPI_BATCH_GRAPH | CPI_BATCH_TUNE"},
         "gpu_launches": 5 * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
@@ -892,6 +903,29 @@ def ws_row_bytes(n, bits):
     pad = 256 if bits == 1 else 128
     k = (n + pad - 1) // pad * pad
     return k * (1 if bits == 1 else 2)
+
+
+def graph_leg(args, cpi, entry, flush, stream, dev):
+    """Mean device time (ms) of the whole step as a graph-replayed single-item
+    batch call, L2 flushed between steps (outside the timed pairs)."""
+    import torch
+
+    items = cpi.batch_items([entry])
+    wsb = torch.empty(cpi.cpi_batch_workspace_size(items), dtype=torch.uint8, device=dev)
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        cpi.cpi_batch_correlate(items, wsb, stream=stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for e0, e1 in evs:
+        flush.zero_()
+        e0.record(stream)
+        cpi.cpi_batch_correlate(items, wsb, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    if cpi.cpi_device_status() != 0:
+        raise RuntimeError("device status error in the graph-replayed leg")
+    return sum(e0.elapsed_time(e1) for e0, e1 in evs) / len(evs)
 
 
 def e2e_run(args, cpi, fr, lay, n, stream, dev, planes, n_planes, ws, rws):

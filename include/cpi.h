@@ -230,9 +230,12 @@ CPI_API cpi_status cpi_refocus4d(const float *gamma_f32, int32_t ha, int32_t wa,
  *   and replays it on later calls whose items (shapes, pointers, planes),
  *   workspace and settings are the same (a small per-device cache; the CUDA
  *   driver may reserve memory for each instantiated graph).
- *   CPI_BATCH_TUNE chooses, on first use of a batch shape, the frame-chunk
- *   split of the grouped launches (1, 2 or 4 times the minimum) by timing
- *   them; this first call synchronises the stream.
+ *   CPI_BATCH_TUNE chooses, on first use of a batch shape, the decomposition
+ *   of the grouped raw-moment launches by timing all six candidates on the
+ *   batch's operands: the frame-chunk split (1, 2 or 4 times the minimum)
+ *   times the output tile width (128 x 256 or 128 x 128); this first call
+ *   synchronises the stream.  Without it: split 1 and 128 x 256 tiles, or
+ *   128 x 128 tiles with CPI_BATCH_N128.
  * -------------------------------------------------------------------------- */
 typedef struct cpi_batch_item {
     cpi_frames a, b;
@@ -245,7 +248,7 @@ typedef struct cpi_batch_item {
     float *refocus_out;         /* device, [n_planes][ha][wa] */
 } cpi_batch_item;
 
-enum { CPI_BATCH_GRAPH = 1, CPI_BATCH_TUNE = 2 };
+enum { CPI_BATCH_GRAPH = 1, CPI_BATCH_TUNE = 2, CPI_BATCH_N128 = 4 };
 
 /* Workspace bytes of a batch (0 on invalid items). */
 CPI_API size_t cpi_batch_workspace_size(const cpi_batch_item *items, int32_t n_items);

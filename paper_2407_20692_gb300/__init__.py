@@ -19,12 +19,12 @@ __all__ = [
     "cpi_correlate_finalize", "cpi_correlate_stage", "cpi_refocus_workspace_size", "cpi_refocus",
     "cpi_denoise", "cpi_device_status", "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout",
     "CPI_STAGE_INGEST", "CPI_STAGE_MOMENTS", "CPI_STAGE_FOLD", "EXPORTED", "cpi_correlate_noalloc",
-    "NOALLOC_SCRATCH_BYTES", "cpi_batch_item", "batch_items", "CPI_BATCH_GRAPH", "CPI_BATCH_TUNE",
+    "NOALLOC_SCRATCH_BYTES", "cpi_batch_item", "batch_items", "CPI_BATCH_GRAPH", "CPI_BATCH_TUNE", "CPI_BATCH_N128",
     "cpi_batch_workspace_size", "cpi_batch_correlate", "cpi_denoise_workspace_size", "cpi_denoise_grad",
     "cpi_denoise_adam", "DENOISER_PARAMS", "denoiser_init", "cpi_plane4", "plane4_array",
     "cpi_refocus4d_workspace_size", "cpi_refocus4d",
 ]
-CPI_BATCH_GRAPH, CPI_BATCH_TUNE = 1, 2
+CPI_BATCH_GRAPH, CPI_BATCH_TUNE, CPI_BATCH_N128 = 1, 2, 4
 DENOISER_PARAMS = 21409
 
 CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD = 1, 2, 3

@@ -172,7 +172,7 @@ struct CorrPlan {
 // split == 0: single correlation (more frame chunks when the tiles alone cannot
 // fill the GPU); split >= 1: member of a batch, split x the minimum chunk count.
 cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm_count,
-                     CorrPlan* pl, int split = 0) {
+                     CorrPlan* pl, int split = 0, int block_n = 256) {
     cpi_status s = check_frames(a);
     if (s != CPI_OK) return s;
     s = check_frames(b);
@@ -189,7 +189,8 @@ cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm
     const int64_t kpad = (int64_t)round_up((size_t)n, (size_t)fpc);
     const int elem = p.bf16 ? 2 : 1;
     p.kstride_bytes = kpad * elem;
-    const MomentsShape sh = moments_shape(p.bf16);
+    if (block_n != 128 && block_n != 256) return CPI_ERR_INVALID_ARG;
+    const MomentsShape sh = moments_shape(p.bf16, block_n);
     p.k_blocks = (int)(kpad / sh.k_per_block);
     p.block_n = sh.block_n;
     p.tiles_m = (int)((p.Ma + 127) / 128);
@@ -274,7 +275,7 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
         L.n_units = pl.n_units;
         L.status = dev->status;
         L.timeout_ns = g_timeout_ns;
-        return cuda_status(launch_moments(pl.bf16, L, dev->sm_count, st));
+        return cuda_status(launch_moments(pl.bf16, pl.block_n, L, dev->sm_count, st));
     }
     if (stage == CPI_STAGE_FOLD) {
         return cuda_status(launch_fold(part, pl.n_chunks, pl.Ma, pl.Mb, s_ab, accumulate, 1, s_a,
@@ -397,10 +398,15 @@ struct BatchItemPlan {
 };
 struct BatchPlan {
     std::vector<BatchItemPlan> it;
+    int block_n = 256;          // output tile width of every grouped launch
     size_t ws_bytes = 0;
 };
 
-constexpr int kSplitCandidates[3] = {1, 2, 4};
+// Decompositions the batch tuner times: frame-chunk split x output tile width.
+struct BatchShape {
+    int split, block_n;
+};
+constexpr BatchShape kBatchCandidates[6] = {{1, 256}, {2, 256}, {4, 256}, {1, 128}, {2, 128}, {4, 128}};
 
 cpi_status check_batch_item(const cpi_batch_item& b) {
     if (!b.s_ab || !b.s_a || !b.s_b || !aligned(b.s_ab, 16) || !aligned(b.s_a, 16) || !aligned(b.s_b, 16))
@@ -419,16 +425,17 @@ cpi_status check_batch_item(const cpi_batch_item& b) {
     return CPI_OK;
 }
 
-cpi_status make_batch_plan(const cpi_batch_item* items, int n, int sm, int split, BatchPlan* bp) {
+cpi_status make_batch_plan(const cpi_batch_item* items, int n, int sm, BatchShape shape, BatchPlan* bp) {
     if (!items || n < 1) return CPI_ERR_INVALID_ARG;
     bp->it.assign(n, BatchItemPlan{});
+    bp->block_n = shape.block_n;
     size_t off = 0;
     for (int i = 0; i < n; ++i) {
         const cpi_batch_item& b = items[i];
         cpi_status s = check_batch_item(b);
         if (s != CPI_OK) return s;
         BatchItemPlan& ip = bp->it[i];
-        s = make_plan(&b.a, &b.b, b.n_frames, sm, &ip.pl, split);
+        s = make_plan(&b.a, &b.b, b.n_frames, sm, &ip.pl, shape.split, shape.block_n);
         if (s != CPI_OK) return s;
         ip.ws_off = off;
         off = round_up(off + ip.pl.ws_bytes, 1024);
@@ -478,7 +485,7 @@ cpi_status launch_batch_moments(const cpi_batch_item* items, const BatchPlan& bp
             L->n_units = (int)units;
             L->status = dev->status;
             L->timeout_ns = g_timeout_ns;
-            if (launch_moments_group(bf16, *L, dev->sm_count, st) != cudaSuccess) return CPI_ERR_CUDA;
+            if (launch_moments_group(bf16, bp.block_n, *L, dev->sm_count, st) != cudaSuccess) return CPI_ERR_CUDA;
         }
     }
     (void)items;
@@ -571,7 +578,7 @@ uint64_t fnv(uint64_t h, const void* p, size_t n) {
     return h;
 }
 
-// Shape of a batch (what the chunk-split tuning depends on).
+// Shape of a batch (what the tuned decomposition depends on).
 uint64_t batch_shape_key(const cpi_batch_item* items, int n, int dev) {
     uint64_t h = fnv(1469598103934665603ull, &n, sizeof(n));
     h = fnv(h, &dev, sizeof(dev));
@@ -585,11 +592,12 @@ uint64_t batch_shape_key(const cpi_batch_item* items, int n, int dev) {
 }
 
 // Everything a captured graph bakes in: shapes, pointers, plane coefficients,
-// workspace and the chosen split.
-uint64_t batch_graph_key(const cpi_batch_item* items, int n, const void* ws, int split, int dev) {
+// workspace and the chosen decomposition.
+uint64_t batch_graph_key(const cpi_batch_item* items, int n, const void* ws, BatchShape shape, int dev) {
     uint64_t h = fnv(1469598103934665603ull, &n, sizeof(n));
     h = fnv(h, &ws, sizeof(ws));
-    h = fnv(h, &split, sizeof(split));
+    h = fnv(h, &shape.split, sizeof(shape.split));
+    h = fnv(h, &shape.block_n, sizeof(shape.block_n));
     h = fnv(h, &dev, sizeof(dev));
     h = fnv(h, &g_timeout_ns, sizeof(g_timeout_ns));
     for (int i = 0; i < n; ++i) {
@@ -601,24 +609,24 @@ uint64_t batch_graph_key(const cpi_batch_item* items, int n, const void* ws, int
 
 struct BatchCache {
     std::mutex mu;
-    std::unordered_map<uint64_t, int> split;              // shape key -> tuned split
+    std::unordered_map<uint64_t, BatchShape> tuned;       // shape key -> tuned decomposition
     std::vector<std::pair<uint64_t, cudaGraphExec_t>> graphs[kMaxDevices];
     cudaStream_t capture_stream[kMaxDevices] = {};
 };
 BatchCache g_batch;
 constexpr size_t kMaxGraphs = 16;
 
-// Chunk split of the grouped raw-moment launches, tuned on first use of a batch
-// shape by timing the candidates (the launches run on whatever the workspace
-// holds; only their duration is used).
-cpi_status tuned_split(const cpi_batch_item* items, int n, uint8_t* ws, DeviceInfo* dev, int dev_id,
-                       cudaStream_t st, int* split_out) {
+// Decomposition of the grouped raw-moment launches (frame-chunk split x output
+// tile width), tuned on first use of a batch shape by timing every candidate on
+// the batch's own operands.
+cpi_status tuned_shape(const cpi_batch_item* items, int n, uint8_t* ws, DeviceInfo* dev, int dev_id,
+                       cudaStream_t st, BatchShape* shape_out) {
     const uint64_t key = batch_shape_key(items, n, dev_id);
     {
         std::lock_guard<std::mutex> lk(g_batch.mu);
-        auto it = g_batch.split.find(key);
-        if (it != g_batch.split.end()) {
-            *split_out = it->second;
+        auto it = g_batch.tuned.find(key);
+        if (it != g_batch.tuned.end()) {
+            *shape_out = it->second;
             return CPI_OK;
         }
     }
@@ -629,11 +637,11 @@ cpi_status tuned_split(const cpi_batch_item* items, int n, uint8_t* ws, DeviceIn
         return CPI_ERR_CUDA;
     }
     float best = 1e30f;
-    int best_split = 1;
+    BatchShape best_shape = kBatchCandidates[0];
     cpi_status s = CPI_OK;
-    for (int c = 0; c < 3 && s == CPI_OK; ++c) {
+    for (int c = 0; c < 6 && s == CPI_OK; ++c) {
         BatchPlan bp;
-        s = make_batch_plan(items, n, dev->sm_count, kSplitCandidates[c], &bp);
+        s = make_batch_plan(items, n, dev->sm_count, kBatchCandidates[c], &bp);
         if (s != CPI_OK) break;
         // real operands and value maxima in this candidate's layout, so that the
         // timed launches run the GEMM variant the batch will run
@@ -655,15 +663,15 @@ cpi_status tuned_split(const cpi_batch_item* items, int n, uint8_t* ws, DeviceIn
         cudaEventElapsedTime(&ms, e0, e1);
         if (ms < best) {
             best = ms;
-            best_split = kSplitCandidates[c];
+            best_shape = kBatchCandidates[c];
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != CPI_OK) return s;
     std::lock_guard<std::mutex> lk(g_batch.mu);
-    g_batch.split[key] = best_split;
-    *split_out = best_split;
+    g_batch.tuned[key] = best_shape;
+    *shape_out = best_shape;
     return CPI_OK;
 }
 
@@ -759,9 +767,9 @@ size_t cpi_batch_workspace_size(const cpi_batch_item* items, int32_t n_items) {
     int sm = 152;
     if (device_info(&dev) == cudaSuccess) sm = dev->sm_count;
     size_t most = 0;
-    for (int c = 0; c < 3; ++c) {
+    for (int c = 0; c < 6; ++c) {
         BatchPlan bp;
-        if (make_batch_plan(items, n_items, sm, kSplitCandidates[c], &bp) != CPI_OK) return 0;
+        if (make_batch_plan(items, n_items, sm, kBatchCandidates[c], &bp) != CPI_OK) return 0;
         most = bp.ws_bytes > most ? bp.ws_bytes : most;
     }
     return most;
@@ -775,22 +783,22 @@ cpi_status cpi_batch_correlate(const cpi_batch_item* items, int32_t n_items, voi
     if (cudaGetDevice(&dev_id) != cudaSuccess) return CPI_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     BatchPlan probe;
-    cpi_status s = make_batch_plan(items, n_items, dev->sm_count, 1, &probe);   // validates the items
+    cpi_status s = make_batch_plan(items, n_items, dev->sm_count, kBatchCandidates[0], &probe);   // validates the items
     if (s != CPI_OK) return s;
     if (!workspace || !aligned(workspace, 256) || workspace_bytes < cpi_batch_workspace_size(items, n_items))
         return CPI_ERR_WORKSPACE;
     uint8_t* ws = static_cast<uint8_t*>(workspace);
-    int split = 1;
+    BatchShape shape = (flags & CPI_BATCH_N128) ? BatchShape{1, 128} : kBatchCandidates[0];
     if (flags & CPI_BATCH_TUNE) {
-        s = tuned_split(items, n_items, ws, dev, dev_id, st, &split);
+        s = tuned_shape(items, n_items, ws, dev, dev_id, st, &shape);
         if (s != CPI_OK) return s;
     }
     BatchPlan bp;
-    s = make_batch_plan(items, n_items, dev->sm_count, split, &bp);
+    s = make_batch_plan(items, n_items, dev->sm_count, shape, &bp);
     if (s != CPI_OK) return s;
     if (!(flags & CPI_BATCH_GRAPH)) return run_batch(items, bp, ws, dev, st);
 
-    const uint64_t key = batch_graph_key(items, n_items, workspace, split, dev_id);
+    const uint64_t key = batch_graph_key(items, n_items, workspace, shape, dev_id);
     cudaGraphExec_t exec = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_batch.mu);

@@ -68,10 +68,11 @@ struct MomentsShape {
     int stages;
     size_t smem_bytes;
 };
-MomentsShape moments_shape(bool bf16);
+// block_n: the output tile's width, 256 (single correlations) or 128.
+MomentsShape moments_shape(bool bf16, int block_n = 256);
 
-cudaError_t launch_moments(bool bf16, const MomentsLaunch<1>& L, int sm_count, cudaStream_t st);
-cudaError_t launch_moments_group(bool bf16, const MomentsLaunch<kMaxGroup>& L, int sm_count,
+cudaError_t launch_moments(bool bf16, int block_n, const MomentsLaunch<1>& L, int sm_count, cudaStream_t st);
+cudaError_t launch_moments_group(bool bf16, int block_n, const MomentsLaunch<kMaxGroup>& L, int sm_count,
                                  cudaStream_t st);
 
 // ------------------------------------------------------------------ fold / finalize

@@ -44,20 +44,20 @@ constexpr int kRowBytes = 128;                 // K-block: one 128-byte swizzle 
 constexpr int kThreads = 320;                  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr int kEpiThreads = 256;
 
-template <bool kBf16>
+template <bool kBf16, int kBN>
 struct MomentsCfg {
-    static constexpr int kBlockN = 256;
-    static constexpr int kStages = 4;
+    static constexpr int kBlockN = kBN;                         // 256 or 128 (batches tune it)
+    static constexpr int kStages = kBN == 256 ? 4 : 6;
     static constexpr int kElem = kBf16 ? 2 : 1;
     static constexpr int kKPerBlock = kRowBytes / kElem;     // 64 / 128 elements
     static constexpr int kMmaK = 32 / kElem;                  // 16 / 32 elements per MMA
     static constexpr int kABytes = kBlockM * kRowBytes;       // 16 KiB
     static constexpr int kBBytes = kBlockN * kRowBytes;       // 32 KiB
-    // tensor memory (512 columns): FP8, two FP32 accumulators; BF16, one FP32
-    // accumulator and the int32 running sums at column 256
+    // tensor memory (2 x kBN columns): FP8, two FP32 accumulators; BF16, one FP32
+    // accumulator and the int32 running sums at column kBN
     static constexpr int kAcc = kBf16 ? 1 : 2;
-    static constexpr uint32_t kSumCol = 256;
-    static constexpr uint32_t kTmemCols = 512;
+    static constexpr uint32_t kSumCol = kBN;
+    static constexpr uint32_t kTmemCols = 2 * kBN;
     static constexpr size_t kSmem = 1024 + (size_t)kStages * (kABytes + kBBytes) + 256;
 };
 
@@ -123,10 +123,10 @@ __device__ __forceinline__ int segment_kblocks(const MomentsProblem& P) {
     return kb < 1 ? 1 : (kb > 0x40000000ull ? 0x40000000 : (int)kb);
 }
 
-template <bool kBf16, int K>
+template <bool kBf16, int kBN, int K>
 __global__ void __launch_bounds__(kThreads, 1)
     moments_kernel(const __grid_constant__ MomentsLaunch<K> L) {
-    using C = MomentsCfg<kBf16>;
+    using C = MomentsCfg<kBf16, kBN>;
     __shared__ int seg_kb[K];   // BF16: K blocks per exact FP32 segment, per problem
     if constexpr (kBf16)
         for (int p = threadIdx.x; p < L.n_problems; p += blockDim.x) seg_kb[p] = segment_kblocks(L.prob[p]);
@@ -367,15 +367,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 }  // namespace
 
-MomentsShape moments_shape(bool bf16) {
+MomentsShape moments_shape(bool bf16, int block_n) {
+    if (block_n == 128) {
+        if (bf16)
+            return {128, MomentsCfg<true, 128>::kKPerBlock, MomentsCfg<true, 128>::kStages, MomentsCfg<true, 128>::kSmem};
+        return {128, MomentsCfg<false, 128>::kKPerBlock, MomentsCfg<false, 128>::kStages, MomentsCfg<false, 128>::kSmem};
+    }
     if (bf16)
-        return {MomentsCfg<true>::kBlockN, MomentsCfg<true>::kKPerBlock, MomentsCfg<true>::kStages,
-                MomentsCfg<true>::kSmem};
-    return {MomentsCfg<false>::kBlockN, MomentsCfg<false>::kKPerBlock, MomentsCfg<false>::kStages,
-            MomentsCfg<false>::kSmem};
+        return {256, MomentsCfg<true, 256>::kKPerBlock, MomentsCfg<true, 256>::kStages, MomentsCfg<true, 256>::kSmem};
+    return {256, MomentsCfg<false, 256>::kKPerBlock, MomentsCfg<false, 256>::kStages, MomentsCfg<false, 256>::kSmem};
 }
 
-template <bool kBf16, int K>
+template <bool kBf16, int kBN, int K>
 static cudaError_t launch_impl(const MomentsLaunch<K>& L, int sm_count, cudaStream_t st) {
     // The shared-memory opt-in is a per-device function attribute: set it once per device.
     static bool attr_set[64] = {};
@@ -383,25 +386,34 @@ static cudaError_t launch_impl(const MomentsLaunch<K>& L, int sm_count, cudaStre
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    using C = MomentsCfg<kBf16>;
+    using C = MomentsCfg<kBf16, kBN>;
     if (!attr_set[dev]) {
-        e = cudaFuncSetAttribute(moments_kernel<kBf16, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(moments_kernel<kBf16, kBN, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)C::kSmem);
         if (e != cudaSuccess) return e;
         attr_set[dev] = true;
     }
     const int grid = L.n_units < sm_count ? L.n_units : sm_count;
-    moments_kernel<kBf16, K><<<grid, kThreads, C::kSmem, st>>>(L);
+    moments_kernel<kBf16, kBN, K><<<grid, kThreads, C::kSmem, st>>>(L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_moments(bool bf16, const MomentsLaunch<1>& L, int sm_count, cudaStream_t st) {
-    return bf16 ? launch_impl<true, 1>(L, sm_count, st) : launch_impl<false, 1>(L, sm_count, st);
+template <int K>
+static cudaError_t launch_any(bool bf16, int block_n, const MomentsLaunch<K>& L, int sm_count, cudaStream_t st) {
+    if (block_n == 128)
+        return bf16 ? launch_impl<true, 128, K>(L, sm_count, st) : launch_impl<false, 128, K>(L, sm_count, st);
+    if (block_n == 256)
+        return bf16 ? launch_impl<true, 256, K>(L, sm_count, st) : launch_impl<false, 256, K>(L, sm_count, st);
+    return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_moments_group(bool bf16, const MomentsLaunch<kMaxGroup>& L, int sm_count,
+cudaError_t launch_moments(bool bf16, int block_n, const MomentsLaunch<1>& L, int sm_count, cudaStream_t st) {
+    return launch_any<1>(bf16, block_n, L, sm_count, st);
+}
+
+cudaError_t launch_moments_group(bool bf16, int block_n, const MomentsLaunch<kMaxGroup>& L, int sm_count,
                                  cudaStream_t st) {
-    return bf16 ? launch_impl<true, kMaxGroup>(L, sm_count, st) : launch_impl<false, kMaxGroup>(L, sm_count, st);
+    return launch_any<kMaxGroup>(bf16, block_n, L, sm_count, st);
 }
 
 }  // namespace cpi

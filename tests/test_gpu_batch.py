@@ -84,6 +84,13 @@ def test_batch_equals_individual_calls_and_replays():
         e["s_ab"].zero_()
     cpi.cpi_batch_correlate(arr, ws, flags=0)
     _check(items, keep)
+    # 128 x 128 output tiles (without the tuner), also captured and replayed
+    for flags in (cpi.CPI_BATCH_N128, cpi.CPI_BATCH_N128 | cpi.CPI_BATCH_GRAPH):
+        for e in items:
+            e["s_ab"].zero_()
+            e["gamma"].zero_()
+        cpi.cpi_batch_correlate(arr, ws, flags=flags)
+        _check(items, keep)
 
 
 def test_batch_item_against_oracle():

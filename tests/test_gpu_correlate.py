@@ -230,9 +230,9 @@ def test_argument_errors_are_reported_before_launch():
     with pytest.raises(cpi.CpiError) as e:
         cpi.cpi_correlate(big8, big8, 20_000_000, s, v, v, None, None, ws)
     assert e.value.code == 2
-    with pytest.raises(cpi.CpiError) as e:
-        cpi.cpi_denoise(None, None, None, 4, 4, 4, 4)
-    assert e.value.code == 4
+    with pytest.raises(cpi.CpiError) as e:       # missing model and Gamma buffers
+        cpi.cpi_denoise(None, None, None, 4, 4, 4, 4, ws)
+    assert e.value.code == 1
 
 
 def test_wait_timeout_is_reported_and_context_survives():
