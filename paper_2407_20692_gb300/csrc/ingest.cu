@@ -3,10 +3,12 @@
 // The frames arrive frame-major (all pixels of frame i, then frame i+1, ...),
 // packed one bit per pixel (Section 2 of the paper) or one byte per pixel.  The
 // raw-moment contraction sums over frames, so each operand row must hold one
-// pixel's values over consecutive frames (K-major).  One CTA transposes a tile
-// of 32 pixels x 256 output bytes through shared memory:
-//   - 1-bit frames -> FP8 E4M3 bytes (0x00 / 0x38 = 1.0), 256 frames per CTA;
-//   - any frames   -> BF16 (integers 0..255 are exact), 128 frames per CTA.
+// pixel's values over consecutive frames (K-major):
+//   - 1-bit frames whose region rows are whole 32-pixel words apart ->
+//     FP8 E4M3 bytes (0x00 / 0x38 = 1.0), ingest_bits_kernel: a block of frames
+//     staged word-wise in shared memory, transposed 32 x 32 bits per warp;
+//   - any frames -> BF16 (integers 0..255 are exact; 1-bit frames that do not
+//     meet the above as E4M3), one CTA per tile of 32 pixels x 256 output bytes.
 // Frames at or beyond n_frames are written as 0, so every operand row is padded
 // to a whole number of CTA tiles.  The same pass adds the marginal sums
 // S_a = sum_i A_i (Eq. (1), second term) with exact int64 atomics.
@@ -139,102 +141,117 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t w, int lane) {
 }
 
 // Binary frames whose region rows are a multiple of 32 pixels wide, with
-// 4-byte aligned frames.  CTA = 32 consecutive region pixels (within one row) x
-// 1024 frames; warp w takes, in each of 4 rounds, frames f0 + 256r + 32w .. +31,
-// one frame per lane.  All 8 word loads are issued first; then each lane
-// funnel-shifts out the 32 pixel bits of its frame, the warp transposes the four
-// 32 x 32 bit blocks together (lane j then holds pixel j's bits over 32 frames),
-// and each bit becomes one E4M3 byte (0x38 = 1.0): 4 bits -> 4 bytes by one
-// multiply that spreads them 8 bits apart.  The bytes are staged in shared
-// memory and written as whole operand-row segments with coalesced stores.
-constexpr int kBitsRounds = 4;
-__global__ void __launch_bounds__(256) ingest_bits_kernel(FramesDev A, FramesDev B, int64_t n_frames,
-                                                          int64_t kstride_bytes, uint8_t* op_a,
-                                                          uint8_t* op_b, int64_t* s_a, int64_t* s_b,
-                                                          int tiles_a) {
-    const bool is_a = (int)blockIdx.x < tiles_a;
+// 4-byte aligned frames.  CTA = (region, chunk of kWC frame words) x block of
+// kFB frames.  Words w0 .. w0 + kWC of every frame of the block are loaded with
+// coalesced 4-byte loads into shared memory, in rows of kWP words (kWP odd: a
+// warp reading one word of 32 frames touches 32 banks).  Each warp then takes
+// whole 32-pixel tiles of the region whose first word lies in the chunk: per 32
+// frames, lane i funnel-shifts its frame's 32 pixel bits out of two words, the
+// warp transposes the 32 x 32 bit block (lane j then holds pixel j over the 32
+// frames), and each bit becomes one E4M3 byte (0x38 = 1.0; 4 bits -> 4 bytes by
+// one multiply that spreads them 8 bits apart).  The tile's 32 operand rows of
+// kFB bytes are staged per warp and stored as whole 128-byte lines; one int64
+// atomic per pixel adds the block's count to the marginal sum.
+constexpr int kFB = 128;                 // frames per CTA
+constexpr int kWC = 64;                  // frame words per chunk
+constexpr int kWP = kWC + 1;             // shared row pitch in words (odd)
+constexpr int kStageRow = kFB + 16;      // staged operand row, bytes
+constexpr size_t kBitsSmem = sizeof(uint32_t) * kFB * kWP + (size_t)8 * 32 * kStageRow;
+static_assert(kWP % 2 == 1, "odd pitch");
+
+__host__ __device__ inline int64_t floor_div(int64_t a, int64_t b) { return a >= 0 ? a / b : -((-a + b - 1) / b); }
+
+// First and last frame word a region's pixels occupy.
+__host__ __device__ inline int64_t region_first_word(const FramesDev& d) {
+    return ((int64_t)d.y0 * d.row_stride + d.x0) >> 5;
+}
+__host__ __device__ inline int64_t region_last_word(const FramesDev& d) {
+    return ((int64_t)(d.y0 + d.height - 1) * d.row_stride + d.x0 + d.width - 1) >> 5;
+}
+
+__global__ void __launch_bounds__(256) ingest_bits_kernel(FramesDev A, FramesDev B, int64_t n_frames, int64_t f_base,
+                                                          int64_t kstride_bytes, uint8_t* op_a, uint8_t* op_b,
+                                                          int64_t* s_a, int64_t* s_b, int chunks_a) {
+    extern __shared__ __align__(16) uint8_t smem_bits[];
+    uint32_t* S = reinterpret_cast<uint32_t*>(smem_bits);                       // [kFB][kWP]
+    const bool is_a = (int)blockIdx.x < chunks_a;
     const FramesDev d = is_a ? A : B;
-    const int tile = is_a ? (int)blockIdx.x : (int)blockIdx.x - tiles_a;
+    const int chunk = is_a ? (int)blockIdx.x : (int)blockIdx.x - chunks_a;
     uint8_t* op = is_a ? op_a : op_b;
     int64_t* s = is_a ? s_a : s_b;
-    const int64_t M = (int64_t)d.height * d.width;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ long long part[8][32];
-    __shared__ __align__(16) uint8_t stile[32][256 * kBitsRounds + 16];
+    uint8_t* st = smem_bits + sizeof(uint32_t) * kFB * kWP + (size_t)warp * 32 * kStageRow;
 
-    const int64_t p0 = (int64_t)tile * 32;               // first pixel; the 32 share one row
-    const int64_t y = p0 / d.width, x = p0 - y * d.width;
-    const int64_t e0 = (d.y0 + y) * d.row_stride + d.x0 + x;   // bit offset inside a frame
-    const int sh = (int)(e0 & 31);
-    const int64_t fcta = (int64_t)blockIdx.y * (256 * kBitsRounds);
-    uint32_t lo[kBitsRounds], hi[kBitsRounds];
+    const int64_t w0 = region_first_word(d) + (int64_t)chunk * kWC;
+    const int64_t words_per_frame = d.frame_stride >> 2;
+    const int64_t f0 = f_base + (int64_t)blockIdx.y * kFB;
+    // asynchronous 4-byte copies (all of a thread's loads in flight at once);
+    // words past the frames or past a frame's end are zero-filled
+    // (warp w copies frames w, w + 8, ...; lane l words l and l + 32, lane 0 also word 64)
+    static_assert(kWC == 64, "two words per lane plus one");
+    for (int fr = warp; fr < kFB; fr += 8) {
+        const int64_t f = f0 + fr;
+        const uint32_t* fbase = reinterpret_cast<const uint32_t*>(d.data + (f < n_frames ? f : 0) * d.frame_stride) + w0;
+        const uint32_t sbase = static_cast<uint32_t>(__cvta_generic_to_shared(S + fr * kWP));
 #pragma unroll
-    for (int r = 0; r < kBitsRounds; ++r) {
-        const int64_t f = fcta + r * 256 + warp * 32 + lane;
-        lo[r] = hi[r] = 0u;
-        if (f < n_frames) {
-            const uint32_t* w = reinterpret_cast<const uint32_t*>(d.data + f * d.frame_stride) + (e0 >> 5);
-            lo[r] = __ldg(w);
-            if (sh) hi[r] = __ldg(w + 1);
+        for (int k = 0; k < 3; ++k) {
+            const int w = k < 2 ? lane + 32 * k : 64;
+            if (k == 2 && lane != 0) break;
+            const bool in = f < n_frames && w0 + w < words_per_frame;
+            const uint32_t* src = in ? fbase + w : reinterpret_cast<const uint32_t*>(d.data);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(sbase + 4u * (uint32_t)w), "l"(src),
+                         "r"(in ? 4 : 0)
+                         : "memory");
         }
     }
-    const int64_t p = p0 + lane;
-    uint32_t col[kBitsRounds];
-#pragma unroll
-    for (int r = 0; r < kBitsRounds; ++r) {
-        uint32_t l = lo[r], h = hi[r];
-        if (d.bit_order) {   // MSB-first bytes: reverse the bits of every byte first
-            l = __byte_perm(__brev(l), 0, 0x0123);
-            h = __byte_perm(__brev(h), 0, 0x0123);
-        }
-        col[r] = __funnelshift_r(l, h, sh);
-    }
-    const uint32_t masks[5] = {0x0000FFFFu, 0x00FF00FFu, 0x0F0F0F0Fu, 0x33333333u, 0x55555555u};
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-        const int sw = 16 >> t;
-        const uint32_t m = masks[t];
-        uint32_t xx[kBitsRounds];
-#pragma unroll
-        for (int r = 0; r < kBitsRounds; ++r) xx[r] = __shfl_xor_sync(0xffffffffu, col[r], sw);
-#pragma unroll
-        for (int r = 0; r < kBitsRounds; ++r)
-            col[r] = (lane & sw) ? ((col[r] & ~m) | ((xx[r] >> sw) & m)) : ((col[r] & m) | ((xx[r] << sw) & ~m));
-    }
-    int cnt = 0;
-#pragma unroll
-    for (int r = 0; r < kBitsRounds; ++r) {
-        cnt += __popc(col[r]);
-        uint32_t o[8];
-#pragma unroll
-        for (int qq = 0; qq < 8; ++qq) {
-            const uint32_t nib = (col[r] >> (4 * qq)) & 0xFu;
-            o[qq] = ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
-        }
-        uint4* dst = reinterpret_cast<uint4*>(&stile[lane][r * 256 + warp * 32]);
-        dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-        dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
-    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
-    {
-        const int64_t cols = kstride_bytes - fcta < 1024 ? kstride_bytes - fcta : 1024;
+
+    // rows with a tile whose first bit e0 = (y0 + y) rs + x0 + 32 xt lies in the chunk
+    const int ntx = d.width >> 5;
+    const int64_t rs = d.row_stride, lo_bit = w0 << 5, hi_bit = (w0 + kWC) << 5;
+    int64_t ylo = -floor_div(-(lo_bit - d.x0 - 32 * (int64_t)(ntx - 1)), rs) - d.y0;
+    int64_t yhi = floor_div(hi_bit - 1 - d.x0, rs) - d.y0;
+    if (ylo < 0) ylo = 0;
+    if (yhi > d.height - 1) yhi = d.height - 1;
+    const int64_t n_items = yhi >= ylo ? (yhi - ylo + 1) * ntx : 0;
+    for (int64_t t = warp; t < n_items; t += 8) {
+        const int64_t y = ylo + t / ntx;
+        const int xt = (int)(t - (t / ntx) * ntx);
+        const int64_t e0 = (d.y0 + y) * rs + d.x0 + 32 * (int64_t)xt;
+        if (e0 < lo_bit || e0 >= hi_bit) continue;             // warp-uniform
+        const int wl = (int)((e0 >> 5) - w0), sh = (int)(e0 & 31);
+        int cnt = 0;
 #pragma unroll
-        for (int it = 0; it < 8; ++it) {
-            const int idx = it * 256 + threadIdx.x;
-            const int rr = idx >> 6, c16 = idx & 63;
-            const int64_t pp = p0 + rr;
-            if (pp < M && c16 * 16 < cols)
-                *reinterpret_cast<uint4*>(op + pp * kstride_bytes + fcta + c16 * 16) =
-                    *reinterpret_cast<const uint4*>(&stile[rr][c16 * 16]);
+        for (int g = 0; g < kFB / 32; ++g) {
+            const uint32_t* row = S + (g * 32 + lane) * kWP + wl;
+            uint32_t lo = row[0], hi = sh ? row[1] : 0u;
+            if (d.bit_order) {   // MSB-first bytes: reverse the bits of every byte first
+                lo = __byte_perm(__brev(lo), 0, 0x0123);
+                hi = __byte_perm(__brev(hi), 0, 0x0123);
+            }
+            const uint32_t col = warp_transpose32(__funnelshift_r(lo, hi, sh), lane);
+            cnt += __popc(col);
+            uint32_t o[8];
+#pragma unroll
+            for (int qq = 0; qq < 8; ++qq) {
+                const uint32_t nib = (col >> (4 * qq)) & 0xFu;
+                o[qq] = ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
+            }
+            uint4* dst = reinterpret_cast<uint4*>(st + lane * kStageRow + g * 32);
+            dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
+            dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
         }
-    }
-    part[warp][lane] = cnt;
-    __syncthreads();
-    if (warp == 0 && p < M) {
-        long long t = 0;
+        __syncwarp();
+        const int64_t p0 = y * d.width + 32 * (int64_t)xt;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) t += part[k][lane];
-        if (t) atomicAdd(reinterpret_cast<unsigned long long*>(s + p), (unsigned long long)t);
+        for (int k = 0; k < 32 * kFB / 16 / 32; ++k) {
+            const int idx = k * 32 + lane, r = idx / (kFB / 16), c16 = idx % (kFB / 16);
+            *reinterpret_cast<uint4*>(op + (p0 + r) * kstride_bytes + f0 + c16 * 16) =
+                *reinterpret_cast<const uint4*>(st + r * kStageRow + c16 * 16);
+        }
+        __syncwarp();
+        if (cnt) atomicAdd(reinterpret_cast<unsigned long long*>(s + p0 + lane), (unsigned long long)cnt);
     }
 }
 
@@ -251,6 +268,28 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
     const int64_t Ma = (int64_t)a.height * a.width, Mb = (int64_t)b.height * b.width;
     const int tiles_a = (int)((Ma + kIngestPixels - 1) / kIngestPixels);
     const int tiles_b = (int)((Mb + kIngestPixels - 1) / kIngestPixels);
+    if (!bf16 && bits_fast_ok(a) && bits_fast_ok(b) && kstride_bytes % kFB == 0) {
+        static bool attr[64] = {};
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (!attr[dev]) {
+            e = cudaFuncSetAttribute(ingest_bits_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kBitsSmem);
+            if (e != cudaSuccess) return e;
+            attr[dev] = true;
+        }
+        const int chunks_a = (int)((region_last_word(a) - region_first_word(a)) / kWC + 1);
+        const int chunks_b = (int)((region_last_word(b) - region_first_word(b)) / kWC + 1);
+        const int64_t blocks = kstride_bytes / kFB;   // one E4M3 byte per frame
+        for (int64_t y0 = 0; y0 < blocks; y0 += 65535) {   // grid.y limit
+            const int64_t ny = blocks - y0 < 65535 ? blocks - y0 : 65535;
+            ingest_bits_kernel<<<dim3((unsigned)(chunks_a + chunks_b), (unsigned)ny), 256, kBitsSmem, st>>>(
+                a, b, n_frames, y0 * kFB, kstride_bytes, op_a, op_b, s_a, s_b, chunks_a);
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     const int64_t frame_tiles = kstride_bytes / kIngestRowBytes;
     if (frame_tiles > 65535) {
         // grid.y limit: split the frame range over several launches
@@ -276,13 +315,6 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
         return cudaGetLastError();
     }
     dim3 grid(tiles_a + tiles_b, (unsigned)frame_tiles);
-    if (!bf16 && bits_fast_ok(a) && bits_fast_ok(b)) {
-        const int64_t gy = (kstride_bytes + 256 * kBitsRounds - 1) / (256 * kBitsRounds);
-        if (gy > 65535) return cudaErrorInvalidValue;
-        ingest_bits_kernel<<<dim3(tiles_a + tiles_b, (unsigned)gy), 256, 0, st>>>(
-            a, b, n_frames, kstride_bytes, op_a, op_b, s_a, s_b, tiles_a);
-        return cudaGetLastError();
-    }
     if (bf16)
         ingest_kernel<true><<<grid, 256, 0, st>>>(a, b, n_frames, kstride_bytes, op_a, op_b, s_a,
                                                   s_b, tiles_a, vmax);

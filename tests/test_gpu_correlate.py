@@ -275,3 +275,27 @@ def test_bit_layouts_match_oracle(bit_order, xa, xb, wa, wb):
     assert_exact(got, want)
     A = img[:, 0:H, xa:xa + wa].reshape(n, -1).astype(np.int64)
     assert np.array_equal(got["s_a"].numpy(), A.sum(0))
+
+
+@pytest.mark.parametrize("bit_order", [0, 1])
+def test_bit_regions_spanning_several_word_chunks(bit_order):
+    """Binary frames of 40 rows x 203 bits (254 words per frame): both regions
+    span several 64-word chunks of the word-staged ingest, with tiles whose two
+    words straddle a chunk edge; 700 frames (not a whole frame block)."""
+    rng = np.random.default_rng(40 + bit_order)
+    n, H, W = 700, 40, 203
+    img = (rng.random((n, H, W)) < 0.3).astype(np.uint8)
+    flat = torch.from_numpy(img.reshape(n, H * W))
+    pad = (-flat.shape[1]) % 32
+    flat = torch.cat([flat, torch.zeros((n, pad), dtype=torch.uint8)], 1)
+    packed = synth.pack_bits_lsb(flat)
+    if bit_order == 1:
+        lut = torch.tensor([int('{:08b}'.format(v)[::-1], 2) for v in range(256)], dtype=torch.uint8)
+        packed = lut[packed.long()]
+    fs = packed.shape[1]
+    fr = packed.contiguous().cuda()
+    la = dict(bits=1, height=H, width=64, x0=5, y0=0, row_stride=W, frame_stride_bytes=fs, bit_order=bit_order)
+    lb = dict(bits=1, height=H - 3, width=96, x0=90, y0=2, row_stride=W, frame_stride_bytes=fs, bit_order=bit_order)
+    got = gpu_correlate(fr, la, lb, n)
+    want = oracle_correlate(fr.cpu().numpy(), la, lb, n)
+    assert_exact(got, want)
