@@ -28,9 +28,9 @@
 //   warp 0   : TMA producer (128-byte swizzled tiles, 4-deep ring)
 //   warp 1   : tensor-memory allocator and single-thread MMA issuer
 //   warps 2-9: epilogue, tensor memory -> registers -> global (TMEM lanes 32*(w%4)..)
-// Binary frames: two TMEM accumulators let the epilogue of one unit overlap the
-// MMAs of the next.  8-bit frames: one FP32 accumulator (256 columns) and the
-// int32 running sums (256 columns).  Every barrier wait is bounded; on a
+// Two TMEM accumulators let the epilogue of one unit (binary frames) or one
+// exact FP32 segment (8-bit frames) overlap the MMAs of the next; the 8-bit
+// int32 running sums of a unit stay in the epilogue threads' registers.  Every barrier wait is bounded; on a
 // time-out the CTA records the error, drains its own copies and MMAs, frees its
 // tensor memory and returns.
 #include "kernels.cuh"
@@ -53,10 +53,10 @@ struct MomentsCfg {
     static constexpr int kMmaK = 32 / kElem;                  // 16 / 32 elements per MMA
     static constexpr int kABytes = kBlockM * kRowBytes;       // 16 KiB
     static constexpr int kBBytes = kBlockN * kRowBytes;       // 32 KiB
-    // tensor memory (2 x kBN columns): FP8, two FP32 accumulators; BF16, one FP32
-    // accumulator and the int32 running sums at column kBN
-    static constexpr int kAcc = kBf16 ? 1 : 2;
-    static constexpr uint32_t kSumCol = kBN;
+    // tensor memory (2 x kBN columns): two FP32 accumulators, so the epilogue of
+    // one unit (FP8) or segment (BF16) overlaps the MMAs of the next; the BF16
+    // int32 running sums live in the epilogue threads' registers
+    static constexpr int kAcc = 2;
     static constexpr uint32_t kTmemCols = 2 * kBN;
     static constexpr size_t kSmem = 1024 + (size_t)kStages * (kABytes + kBBytes) + 256;
 };
@@ -313,46 +313,49 @@ __global__ void __launch_bounds__(kThreads, 1)
                     acc_phase ^= 1;
                 }
             } else {
-                // Every segment: running sum (TMEM columns kSumCol..) += FP32
-                // segment sum (< 2^23, converted through its bit pattern); the
-                // last segment's totals go to the partial slot instead.
+                // Every segment: running sums (registers, int32) += the FP32
+                // segment sums (< 2^23, converted through their bit patterns);
+                // after the last segment they go to the partial slot.
                 const int seg = seg_kb[w.prob];
                 const int nseg = (kb1 - kb0 + seg - 1) / seg;
+                uint32_t run[kHalf / 16][16];
+#pragma unroll
+                for (int c = 0; c < kHalf / 16; ++c)
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) run[c][j] = 0u;
                 for (int sgm = 0; sgm < nseg; ++sgm) {
-                    if (!mbar_wait_bounded(&tfull[0], acc_phase, abort_flag, status, tmo)) {
+                    if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, status, tmo)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
-                    const bool last = sgm + 1 == nseg;
-#pragma unroll 1
-                    for (int c = 0; c < kHalf / 32; ++c) {
-                        const uint32_t col = lane_addr + col0 + (uint32_t)(c * 32);
-                        uint32_t r[32], run[32];
-                        tmem_ld_32x32b_x32(tmem_base + col, r);
-                        if (sgm > 0) tmem_ld_32x32b_x32(tmem_base + C::kSumCol + col, run);
+#pragma unroll
+                    for (int c = 0; c < kHalf / 16; ++c) {
+                        uint32_t r[16];
+                        tmem_ld_32x32b_x16(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN) + col0 + c * 16, r);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) {
-                            const uint32_t f = __float_as_uint(__fadd_rn(__uint_as_float(r[j]), 8388608.0f)) -
-                                               0x4B000000u;
-                            run[j] = (sgm > 0 ? run[j] : 0u) + f;
-                        }
-                        if (last) {
-                            int32_t v[32];
-#pragma unroll
-                            for (int j = 0; j < 32; ++j) v[j] = (int32_t)run[j];
-                            store_row_chunk(P, chunk, m, n0 + c * 32, v);
-                        } else {
-                            tmem_st_32x32b_x32(tmem_base + C::kSumCol + col, run);
-                        }
+                        for (int j = 0; j < 16; ++j)
+                            run[c][j] += __float_as_uint(__fadd_rn(__uint_as_float(r[j]), 8388608.0f)) - 0x4B000000u;
                     }
-                    if (!last) tmem_st_wait();
                     tc_fence_before();
-                    mbar_arrive(&tempty[0]);
-                    acc_phase ^= 1;
+                    mbar_arrive(&tempty[acc]);
+                    if (++acc == C::kAcc) {
+                        acc = 0;
+                        acc_phase ^= 1;
+                    }
                 }
                 if (!ok) break;
+#pragma unroll
+                for (int c = 0; c < kHalf / 32; ++c) {
+                    int32_t v[32];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        v[j] = (int32_t)run[2 * c][j];
+                        v[16 + j] = (int32_t)run[2 * c + 1][j];
+                    }
+                    store_row_chunk(P, chunk, m, n0 + c * 32, v);
+                }
             }
         }
     }
