@@ -930,46 +930,79 @@ def graph_leg(args, cpi, entry, flush, stream, dev):
 
 def e2e_run(args, cpi, fr, lay, n, stream, dev, planes, n_planes, ws, rws):
     """Same step through the public API with host buffers: pinned frames copied
-    in, Gamma (f64) and the refocused stack copied out, inside the timed region."""
+    in, Gamma (f64) and the refocused stack copied out, inside the timed region.
+    As an acquisition loop would run it: frames, Gamma and the stack are
+    double-buffered; step k's frames are copied in on an upload stream while step
+    k - 1 computes, and its results are copied out on a download stream while
+    step k refocuses and step k + 1 computes (step k + 2 waits for both before it
+    reuses the buffers)."""
     import torch
 
     la, lb = lay["a"], lay["b"]
     ha, wa, hb, wb = la["height"], la["width"], lb["height"], lb["width"]
     ma, mb = ha * wa, hb * wb
     host_in = fr.cpu().pin_memory()
-    dev_in = torch.empty_like(fr)
+    dev_in = [torch.empty_like(fr) for _ in range(2)]
     s_ab = torch.empty((ma, mb), dtype=torch.int64, device=dev)
     s_a = torch.empty(ma, dtype=torch.int64, device=dev)
     s_b = torch.empty(mb, dtype=torch.int64, device=dev)
-    gamma = torch.empty((ma, mb), dtype=torch.float64, device=dev)
     g32 = torch.empty((mb, ma), dtype=torch.float32, device=dev)
-    out = torch.empty((n_planes, ha, wa), dtype=torch.float32, device=dev)
-    host_g = torch.empty((ma, mb), dtype=torch.float64).pin_memory()
-    host_o = torch.empty((n_planes, ha, wa), dtype=torch.float32).pin_memory()
+    gamma = [torch.empty((ma, mb), dtype=torch.float64, device=dev) for _ in range(2)]
+    out = [torch.empty((n_planes, ha, wa), dtype=torch.float32, device=dev) for _ in range(2)]
+    host_g = [torch.empty((ma, mb), dtype=torch.float64).pin_memory() for _ in range(2)]
+    host_o = [torch.empty((n_planes, ha, wa), dtype=torch.float32).pin_memory() for _ in range(2)]
     mk = lambda t, l: cpi.frames(t, l["bits"], l["height"], l["width"], l["x0"], l["y0"],
                                  l["row_stride"], l["frame_stride_bytes"])
-    a, b = mk(dev_in, la), mk(dev_in, lb)
+    ab = [(mk(t, la), mk(t, lb)) for t in dev_in]
+    copy = torch.cuda.Stream(device=dev)
+    upload = torch.cuda.Stream(device=dev)
+    done = [torch.cuda.Event(), torch.cuda.Event()]       # buffer i's copies out finished
+    consumed = [torch.cuda.Event(), torch.cuda.Event()]   # frames buffer i read by its correlation
+    arrived = [torch.cuda.Event(), torch.cuda.Event()]    # frames buffer i copied in
+    for e in done:
+        e.record(copy)
+    for e in consumed:
+        e.record(stream)
 
-    def one():
-        dev_in.copy_(host_in, non_blocking=True)
-        cpi.cpi_correlate(a, b, n, s_ab, s_a, s_b, gamma, g32, ws, stream)
-        cpi.cpi_refocus(g32, ha, wa, hb, wb, planes, out, rws, stream)
-        host_g.copy_(gamma, non_blocking=True)
-        host_o.copy_(out, non_blocking=True)
+    def one(k):
+        i = k % 2
+        upload.wait_event(consumed[i])
+        with torch.cuda.stream(upload):
+            dev_in[i].copy_(host_in, non_blocking=True)
+        arrived[i].record(upload)
+        stream.wait_event(arrived[i])
+        stream.wait_event(done[i])
+        a, b = ab[i]
+        cpi.cpi_correlate(a, b, n, s_ab, s_a, s_b, gamma[i], g32, ws, stream)
+        consumed[i].record(stream)
+        ready_g = torch.cuda.Event()
+        ready_g.record(stream)
+        cpi.cpi_refocus(g32, ha, wa, hb, wb, planes, out[i], rws, stream)
+        ready_o = torch.cuda.Event()
+        ready_o.record(stream)
+        copy.wait_event(ready_g)
+        with torch.cuda.stream(copy):
+            host_g[i].copy_(gamma[i], non_blocking=True)
+            copy.wait_event(ready_o)
+            host_o[i].copy_(out[i], non_blocking=True)
+        done[i].record(copy)
 
-    for _ in range(max(1, args.warmup)):
-        one()
+    for k in range(max(1, args.warmup)):
+        one(k)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    k = max(1, args.steps)
+    steps = max(1, args.steps)
     e0.record(stream)
-    for _ in range(k):
-        one()
+    upload.wait_event(e0)          # every timed copy starts after e0
+    for k in range(steps):
+        one(k)
+    stream.wait_event(done[(steps - 1) % 2])
+    stream.wait_event(done[(steps - 2) % 2] if steps > 1 else done[0])
     e1.record(stream)
     torch.cuda.synchronize()
-    s = e0.elapsed_time(e1) / 1e3 / k
+    s = e0.elapsed_time(e1) / 1e3 / steps
     return {"s_per_step": s, "h2d": host_in.numel(),
-            "d2h": host_g.numel() * 8 + host_o.numel() * 4}
+            "d2h": host_g[0].numel() * 8 + host_o[0].numel() * 4}
 
 
 # ----------------------------------------------------------------------------- reference arm
