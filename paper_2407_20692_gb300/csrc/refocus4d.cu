@@ -87,73 +87,100 @@ __global__ void r4_tables_kernel(const Plane4Block co, int np, int ha, int wa, i
     }
 }
 
-// Stage 1: CTA (yb, ya); every plane of the chunk, G planes at a time; thread
-// w of a pass takes plane p0 + w / wa and column x_c = w % wa (so narrow images
-// still give every thread work).  sB holds the G planes' angular-column tables.
-template <bool kSmem>
-__global__ void __launch_bounds__(kR4Threads) r4_cols_kernel(const float* __restrict__ g, int np, int G, int ha,
-                                                             int wa, int hb, int wb, const long long* __restrict__ t,
-                                                             int64_t stride, float* __restrict__ c_hi,
-                                                             float* __restrict__ c_lo) {
+// Stage 1: CTA (yb, ya0 .. ya0 + K - 1): the K boxes of those row pairs; every
+// plane of the chunk, G planes at a time; thread w of a pass takes plane
+// p0 + w / wa and column x_c = w % wa (so narrow images still give every thread
+// work).  The taps of (plane, x_c, j_c) do not depend on the row pair, so each is
+// formed once and applied to all K boxes.  sB holds the G planes' angular-column
+// tables.
+constexpr int kColThreads = 512;
+template <bool kSmem, int K>
+__global__ void __launch_bounds__(kColThreads) r4_cols_kernel(const float* __restrict__ g, int np, int G, int ha,
+                                                              int wa, int hb, int wb, const long long* __restrict__ t,
+                                                              int64_t stride, float* __restrict__ c_hi,
+                                                              float* __restrict__ c_lo) {
     extern __shared__ __align__(16) float sm[];
-    const int yb = blockIdx.x, ya = blockIdx.y;
+    const int yb = blockIdx.x, ya0 = blockIdx.y * K;
+    const int nb = min(K, ha - ya0);                       // boxes of this CTA
     const int64_t ma = (int64_t)ha * wa;
     const int WP = wa + 2 * kPad, HP = wb + 2 * kPad;     // padded box: HP rows (xb) x WP columns (xa)
+    const int BS = HP * WP;
     long long* sB = reinterpret_cast<long long*>(sm);      // [G][2][wb]: TBx, TBbx of the pass's planes
-    float* box = reinterpret_cast<float*>(sB + 2 * (size_t)G * wb);
-    const float* gbase = g + ((int64_t)yb * wb) * ma + (int64_t)ya * wa;   // G[xb][xa] = gbase[xb*ma + xa]
+    float* box = reinterpret_cast<float*>(sB + 2 * (size_t)G * wb);   // [K][HP][WP]
     if constexpr (kSmem) {
-        for (int i = threadIdx.x; i < HP * WP; i += kR4Threads) {
-            const int r = i / WP, q = i - r * WP;
-            const int xb = r - kPad, xa = q - kPad;
-            box[i] = (xb >= 0 && xb < wb && xa >= 0 && xa < wa) ? g[(int64_t)(yb * wb + xb) * ma + ya * wa + xa] : 0.0f;
-        }
+        for (int k = 0; k < nb; ++k)
+            for (int i = threadIdx.x; i < BS; i += kColThreads) {
+                const int r = i / WP, q = i - r * WP;
+                const int xb = r - kPad, xa = q - kPad;
+                box[k * BS + i] = (xb >= 0 && xb < wb && xa >= 0 && xa < wa)
+                                      ? g[(int64_t)(yb * wb + xb) * ma + (int64_t)(ya0 + k) * wa + xa]
+                                      : 0.0f;
+            }
     }
     for (int p0 = 0; p0 < np; p0 += G) {
         const int gp = min(G, np - p0);
-        __syncthreads();   // box ready / previous pass's tables consumed
-        for (int i = threadIdx.x; i < gp * wb; i += kR4Threads) {
+        __syncthreads();   // boxes ready / previous pass's tables consumed
+        for (int i = threadIdx.x; i < gp * wb; i += kColThreads) {
             const int k = i / wb, j = i - k * wb;
             sB[(2 * k) * wb + j] = t[2 * stride + (int64_t)(p0 + k) * wb + j];
             sB[(2 * k + 1) * wb + j] = t[3 * stride + (int64_t)(p0 + k) * wb + j];
         }
         __syncthreads();
-        for (int w = threadIdx.x; w < gp * wa; w += kR4Threads) {
-            const int k = w / wa, xc = w - k * wa, p = p0 + k;
-            const long long* B = sB + 2 * k * wb;
+        for (int w = threadIdx.x; w < gp * wa; w += kColThreads) {
+            const int kp = w / wa, xc = w - kp * wa, p = p0 + kp;
+            const long long* B = sB + 2 * kp * wb;
             const long long ax = t[0 * stride + (int64_t)p * wa + xc];
             const long long abx = t[1 * stride + (int64_t)p * wa + xc];
-            float acc = 0.0f, cmp = 0.0f;
+            float acc[K], cmp[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k) acc[k] = cmp[k] = 0.0f;
             for (int jc = 0; jc < wb; ++jc) {
                 const R4Frac fa = r4_split(ax + B[jc]);
                 const R4Frac fb = r4_split(abx + B[wb + jc]);
-                float v;
+                const float ga = 1.0f - fa.f, gb = 1.0f - fb.f;
                 if constexpr (kSmem) {
                     const int xa = min(max(fa.i, -kPad), wa) + kPad;
                     const int xb = min(max(fb.i, -kPad), wb) + kPad;
                     const float* q0 = box + xb * WP + xa;
-                    const float top = __fmaf_rn(fa.f, q0[1], (1.0f - fa.f) * q0[0]);
-                    const float bot = __fmaf_rn(fa.f, q0[WP + 1], (1.0f - fa.f) * q0[WP]);
-                    v = __fmaf_rn(fb.f, bot, (1.0f - fb.f) * top);
-                } else {
-                    float s[2][2];
 #pragma unroll
-                    for (int db = 0; db < 2; ++db)
-#pragma unroll
-                        for (int da = 0; da < 2; ++da) {
-                            const int xa = fa.i + da, xb = fb.i + db;
-                            s[db][da] = (xa >= 0 && xa < wa && xb >= 0 && xb < wb) ? __ldg(gbase + (int64_t)xb * ma + xa)
-                                                                                 : 0.0f;
+                    for (int k = 0; k < K; ++k) {
+                        if (k < nb) {
+                            const float* q = q0 + k * BS;
+                            const float top = __fmaf_rn(fa.f, q[1], ga * q[0]);
+                            const float bot = __fmaf_rn(fa.f, q[WP + 1], ga * q[WP]);
+                            r4_kahan(acc[k], cmp[k], __fmaf_rn(fb.f, bot, gb * top));
                         }
-                    const float top = __fmaf_rn(fa.f, s[0][1], (1.0f - fa.f) * s[0][0]);
-                    const float bot = __fmaf_rn(fa.f, s[1][1], (1.0f - fa.f) * s[1][0]);
-                    v = __fmaf_rn(fb.f, bot, (1.0f - fb.f) * top);
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < K; ++k) {
+                        if (k < nb) {
+                            const float* gbase = g + ((int64_t)yb * wb) * ma + (int64_t)(ya0 + k) * wa;
+                            float s[2][2];
+#pragma unroll
+                            for (int db = 0; db < 2; ++db)
+#pragma unroll
+                                for (int da = 0; da < 2; ++da) {
+                                    const int xa = fa.i + da, xb = fb.i + db;
+                                    s[db][da] = (xa >= 0 && xa < wa && xb >= 0 && xb < wb)
+                                                    ? __ldg(gbase + (int64_t)xb * ma + xa)
+                                                    : 0.0f;
+                                }
+                            const float top = __fmaf_rn(fa.f, s[0][1], ga * s[0][0]);
+                            const float bot = __fmaf_rn(fa.f, s[1][1], ga * s[1][0]);
+                            r4_kahan(acc[k], cmp[k], __fmaf_rn(fb.f, bot, gb * top));
+                        }
+                    }
                 }
-                r4_kahan(acc, cmp, v);
             }
-            const int64_t o = (((int64_t)p * ha + ya) * hb + yb) * wa + xc;
-            c_hi[o] = acc;
-            c_lo[o] = -cmp;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if (k < nb) {
+                    const int64_t o = (((int64_t)p * ha + ya0 + k) * hb + yb) * wa + xc;
+                    c_hi[o] = acc[k];
+                    c_lo[o] = -cmp[k];
+                }
+            }
         }
     }
 }
@@ -238,18 +265,38 @@ Refocus4dLayout refocus4d_layout(int ha, int wa, int hb, int wb, int n_planes) {
 }
 
 namespace {
-// planes per pass of the column stage and the shared memory it takes
+// planes per pass of the column stage
 int r4_col_group(int wa, int wb, int np) {
-    int G = wa < kR4Threads ? kR4Threads / wa : 1;
+    int G = wa < kColThreads ? kColThreads / wa : 1;
     if (G > np) G = np;
     while (G > 1 && (size_t)G * 2 * wb * sizeof(long long) > 16 * 1024) --G;
     return G < 1 ? 1 : G;
 }
 size_t r4_box_bytes(int wa, int wb) { return sizeof(float) * (size_t)(wb + 2 * kPad) * (wa + 2 * kPad); }
+constexpr size_t kR4SmemCap = 200 * 1024;
+
+template <bool kSmem, int K>
+cudaError_t launch_cols(const float* g, int np, int G, int ha, int wa, int hb, int wb, const long long* t,
+                        int64_t stride, float* c_hi, float* c_lo, size_t smem, cudaStream_t st) {
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        if ((e = cudaFuncSetAttribute(r4_cols_kernel<kSmem, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)kR4SmemCap)) != cudaSuccess)
+            return e;
+        attr[dev] = true;
+    }
+    const dim3 grid((unsigned)hb, (unsigned)((ha + K - 1) / K));
+    r4_cols_kernel<kSmem, K><<<grid, kColThreads, smem, st>>>(g, np, G, ha, wa, hb, wb, t, stride, c_hi, c_lo);
+    return cudaGetLastError();
+}
 }  // namespace
 
 bool refocus4d_box_fits(int wa, int wb) {
-    return sizeof(long long) * 2 * (size_t)wb + r4_box_bytes(wa, wb) <= 200 * 1024;
+    return sizeof(long long) * 2 * (size_t)wb + r4_box_bytes(wa, wb) <= kR4SmemCap;
 }
 
 cudaError_t launch_refocus4d_chunk(const float* gamma_f32, int ha, int wa, int hb, int wb, const Plane4Block& coef,
@@ -260,27 +307,28 @@ cudaError_t launch_refocus4d_chunk(const float* gamma_f32, int ha, int wa, int h
     r4_tables_kernel<<<np, 128, 0, st>>>(coef, np, ha, wa, hb, wb, t, L.stride);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const dim3 g1((unsigned)hb, (unsigned)ha);
     int G = r4_col_group(wa, wb, np);
     if (refocus4d_box_fits(wa, wb)) {
-        while (G > 1 && sizeof(long long) * 2 * (size_t)G * wb + r4_box_bytes(wa, wb) > 200 * 1024) --G;
-        const size_t smem = sizeof(long long) * 2 * (size_t)G * wb + r4_box_bytes(wa, wb);
-        static bool attr[64] = {};
-        int dev = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-        if (!attr[dev]) {
-            if ((e = cudaFuncSetAttribute(r4_cols_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          200 * 1024)) != cudaSuccess)
-                return e;
-            attr[dev] = true;
-        }
-        r4_cols_kernel<true><<<g1, kR4Threads, smem, st>>>(gamma_f32, np, G, ha, wa, hb, wb, t, L.stride, c_hi, c_lo);
+        const size_t box = r4_box_bytes(wa, wb);
+        while (G > 1 && sizeof(long long) * 2 * (size_t)G * wb + box > kR4SmemCap) --G;
+        const size_t tab = sizeof(long long) * 2 * (size_t)G * wb;
+        // boxes per CTA: as many row pairs (4, 2, 1) as fit, while the grid
+        // keeps at least ~4 CTAs per SM of a 152-SM GPU
+        int K = 1;
+        for (int k : {4, 2})
+            if (tab + k * box <= kR4SmemCap && (int64_t)hb * ((ha + k - 1) / k) >= 4 * 152) {
+                K = k;
+                break;
+            }
+        const size_t smem = tab + K * box;
+        if (K == 4) e = launch_cols<true, 4>(gamma_f32, np, G, ha, wa, hb, wb, t, L.stride, c_hi, c_lo, smem, st);
+        else if (K == 2) e = launch_cols<true, 2>(gamma_f32, np, G, ha, wa, hb, wb, t, L.stride, c_hi, c_lo, smem, st);
+        else e = launch_cols<true, 1>(gamma_f32, np, G, ha, wa, hb, wb, t, L.stride, c_hi, c_lo, smem, st);
     } else {
-        r4_cols_kernel<false><<<g1, kR4Threads, sizeof(long long) * 2 * (size_t)G * wb, st>>>(
-            gamma_f32, np, G, ha, wa, hb, wb, t, L.stride, c_hi, c_lo);
+        e = launch_cols<false, 1>(gamma_f32, np, G, ha, wa, hb, wb, t, L.stride, c_hi, c_lo,
+                                  sizeof(long long) * 2 * (size_t)G * wb, st);
     }
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (e != cudaSuccess) return e;
     const int Gr = wa < kR4Threads ? kR4Threads / wa : 1;
     r4_rows_kernel<<<dim3((unsigned)((ha + Gr - 1) / Gr), (unsigned)np), kR4Threads, 0, st>>>(c_hi, c_lo, Gr, ha, wa,
                                                                                             hb, t, L.stride, out);

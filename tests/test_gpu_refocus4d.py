@@ -45,6 +45,8 @@ _CO = (np.array([0.6, 1.0, 1.3, 0.9, 1.0]), np.array([0.4, 0.0, -0.3, 0.25, 0.0]
     (33, 17, 3, 2),
     (12, 100, 5, 6),       # two planes per column pass, the last pass ragged
     (9, 300, 3, 4),        # wider than a CTA's threads: columns loop
+    (50, 12, 60, 10),      # four row pairs per CTA, the last group of two
+    (41, 9, 40, 7),        # two row pairs per CTA, the last group of one
 ])
 def test_refocus4d_random_gamma_matches_oracle(ha, wa, hb, wb):
     rng = np.random.default_rng(ha * 100 + wa)
