@@ -126,6 +126,27 @@ bool make_gamma_map(CUtensorMap* m, const float* g, int64_t elements) {
     return r == CUDA_SUCCESS;
 }
 
+}  // namespace
+
+bool make_bf16_map_sw64(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                        const uint32_t* box) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || rank < 3 || rank > 4) return false;
+    cuuint64_t d[4], st[3];
+    cuuint32_t bx[4], es[4] = {1, 1, 1, 1};
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+    }
+    for (int i = 0; i < rank - 1; ++i) st[i] = strides[i];
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), d, st, bx,
+                           es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+namespace {
+
 bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
 size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
@@ -891,7 +912,7 @@ cpi_status cpi_denoise(const float* model, const float* gamma_in, float* gamma_o
     if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t* ws = static_cast<uint8_t*>(workspace);
-    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, st);
+    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, dev->status, g_timeout_ns, st);
     if (e == cudaSuccess) e = denoise_output(ws, L, (int64_t)hb * wb * ha * wa, gamma_out, st);
     return cuda_status(e);
 }
@@ -907,7 +928,7 @@ cpi_status cpi_denoise_grad(const float* model, const float* gamma_in, const flo
     if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t* ws = static_cast<uint8_t*>(workspace);
-    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, st);
+    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, dev->status, g_timeout_ns, st);
     if (e == cudaSuccess) e = denoise_backward(model, gamma_target, ha, wa, hb, wb, ws, L, grad, loss, st);
     return cuda_status(e);
 }

@@ -27,6 +27,7 @@
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
+#include "ptx.cuh"
 
 namespace cpi {
 namespace {
@@ -190,6 +191,160 @@ __global__ void __launch_bounds__(kConvThreads)
             for (int co = 0; co < COUT; ++co) o[((int64_t)b * COUT + co) * HW + p] = acc[k][co];
         }
     }
+}
+
+// ------------------------------------------------------------------ tensor-core forward
+// Layers 0..2 (32 -> 32 channels; the 9-channel input is padded to 32 with zero
+// channels and zero weights) as implicit GEMMs on tcgen05, for image widths 32,
+// 64 and 128.  A CTA computes R = 256 / W output rows of one slice (two tiles of
+// M = 128 pixels) for the 32 output channels.  The layer input is channels-last
+// bf16 (64 bytes per pixel); TMA loads three copies of rows y0 - 1 .. y0 + R
+// with the columns shifted by -1, 0, +1 (zeros outside the image), 64-byte
+// swizzled, so that the A operand of tap (ky, kx) is copy kx from row ky on: an
+// 8-row aligned slice, as W is a multiple of 8.  Weights: bf16 [tap][Cout][Cin],
+// one TMA box.  Per tile 9 taps x 2 MMAs (M = 128, N = 32, K = 16) accumulate in
+// 32 TMEM columns (FP32 sums); the epilogue adds the bias, applies ReLU, rounds
+// to bf16 and writes channels-first (for the backward pass and the last layer)
+// and, if asked, channels-last (the next layer's input).  Waits are bounded; on
+// a time-out the CTA records it, drains its copies and MMAs and writes nothing.
+constexpr int kTcThreads = 128;
+constexpr int kTcWBytes = 9 * 32 * 64;     // weights of one layer, bf16
+
+inline int tc_rows(int W) { return 256 / W; }
+inline size_t tc_copy_stride(int W) { return ((size_t)(tc_rows(W) + 2) * W * 64 + 1023) / 1024 * 1024; }
+inline size_t tc_smem(int W) { return 1024 + 3 * tc_copy_stride(W) + kTcWBytes + 64; }
+
+__global__ void __launch_bounds__(kTcThreads) dn_conv_tc_kernel(const __grid_constant__ CUtensorMap in_map,
+                                                                const __grid_constant__ CUtensorMap w_map,
+                                                                const float* __restrict__ bias,
+                                                                __nv_bfloat16* __restrict__ out_cf,
+                                                                __nv_bfloat16* __restrict__ out_cl, int H, int W,
+                                                                unsigned int* status, unsigned long long timeout_ns) {
+    extern __shared__ uint8_t smem_tc[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~(uintptr_t)1023);
+    const int R = 256 / W;
+    const size_t cstride = ((size_t)(R + 2) * W * 64 + 1023) / 1024 * 1024;
+    const uint32_t copy_bytes = (uint32_t)((R + 2) * W * 64);
+    uint8_t* sw = sm + 3 * cstride;
+    uint64_t* load_bar = reinterpret_cast<uint64_t*>(sw + kTcWBytes);
+    uint64_t* mma_bar = load_bar + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_bar + 1);
+    int* flag = reinterpret_cast<int*>(tmem_slot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int b = blockIdx.y, y0 = blockIdx.x * R;
+
+    if (tid == 0) {
+        mbar_init(load_bar, 1);
+        mbar_init(mma_bar, 1);
+        fence_barrier_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(tmem_slot, 64);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (tid == 0) {
+        mbar_arrive_expect_tx(load_bar, 3 * copy_bytes + (uint32_t)kTcWBytes);
+#pragma unroll
+        for (int kx = 0; kx < 3; ++kx) tma_load_4d(sm + kx * cstride, &in_map, load_bar, 0, kx - 1, y0 - 1, b);
+        tma_load_3d(sw, &w_map, load_bar, 0, 0, 0);
+        bool ok = mbar_wait_bounded(load_bar, 0, nullptr, status, timeout_ns);
+        if (ok) {
+            tc_fence_after();
+            constexpr uint32_t idesc = idesc_f32acc<true>(128, 32);
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int ky = tap / 3, kx = tap % 3;
+                    const uint64_t a = sdesc_kmajor_sw64(smem_u32(sm + kx * cstride + (size_t)(ky * W + t * 128) * 64));
+                    const uint64_t bd = sdesc_kmajor_sw64(smem_u32(sw + tap * 32 * 64));
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)   // second half of the 64-byte rows: +32 bytes
+                        umma_f32<true>(tmem_base + (uint32_t)(t * 32), a + (uint64_t)(2 * h), bd + (uint64_t)(2 * h),
+                                       idesc, (tap | h) ? 1u : 0u);
+                }
+            umma_commit(mma_bar);
+            ok = mbar_wait_bounded(mma_bar, 0, nullptr, status, timeout_ns);
+            if (!ok) mbar_wait_bounded(mma_bar, 0, nullptr, nullptr, timeout_ns);   // drain the MMAs
+        } else {
+            mbar_wait_bounded(load_bar, 0, nullptr, nullptr, timeout_ns);           // drain the copies
+        }
+        *flag = ok ? 1 : 0;
+    }
+    __syncthreads();
+    if (*flag) {
+        tc_fence_after();
+        const int64_t HW = (int64_t)H * W;
+#pragma unroll 1
+        for (int t = 0; t < 2; ++t) {
+            uint32_t r[32];
+            tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * 32), r);
+            tmem_ld_wait();
+            const int pl = t * 128 + 32 * warp + lane;
+            const int y = y0 + pl / W, x = pl - (pl / W) * W;
+            if (y < H) {
+                const int64_t pix = (int64_t)y * W + x;
+                uint32_t pk[16];
+#pragma unroll
+                for (int co = 0; co < 32; co += 2) {
+                    const __nv_bfloat16 v0 = __float2bfloat16_rn(fmaxf(__uint_as_float(r[co]) + __ldg(bias + co), 0.0f));
+                    const __nv_bfloat16 v1 =
+                        __float2bfloat16_rn(fmaxf(__uint_as_float(r[co + 1]) + __ldg(bias + co + 1), 0.0f));
+                    out_cf[((int64_t)b * 32 + co) * HW + pix] = v0;
+                    out_cf[((int64_t)b * 32 + co + 1) * HW + pix] = v1;
+                    pk[co / 2] = (uint32_t)__bfloat16_as_ushort(v0) | ((uint32_t)__bfloat16_as_ushort(v1) << 16);
+                }
+                if (out_cl != nullptr) {
+                    uint4* dst = reinterpret_cast<uint4*>(out_cl + ((int64_t)b * HW + pix) * 32);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, 64);
+    }
+}
+
+// x (channels-first, 9 channels) -> channels-last with 32 channels (9..31 zero).
+__global__ void dn_x_to_cl_kernel(const __nv_bfloat16* __restrict__ x, int64_t HW, int64_t n_pix,
+                                  __nv_bfloat16* __restrict__ xc) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pix; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = i / HW, p = i - b * HW;
+        uint32_t pk[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) pk[c] = 0u;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) {
+            const uint32_t v = __bfloat16_as_ushort(x[(b * 9 + c) * HW + p]);
+            pk[c / 2] |= (c & 1) ? (v << 16) : v;
+        }
+        uint4* dst = reinterpret_cast<uint4*>(xc + i * 32);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
+    }
+}
+
+// Weights of layers 0..2 as bf16 [layer][tap][Cout][Cin = 32] (layer 0: Cin 9,
+// zero beyond).
+__global__ void dn_wprep_kernel(const float* __restrict__ model, int64_t w0, int64_t w1, int64_t w2,
+                                __nv_bfloat16* __restrict__ wt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * 9 * 32 * 32) return;
+    const int l = i / (9 * 32 * 32), rem = i - l * 9 * 32 * 32;
+    const int tap = rem / (32 * 32), co = (rem / 32) % 32, ci = rem % 32;
+    const int cin = l == 0 ? 9 : 32;
+    const int64_t base = l == 0 ? w0 : (l == 1 ? w1 : w2);
+    wt[i] = __float2bfloat16_rn(ci < cin ? model[base + ((int64_t)co * cin + ci) * 9 + tap] : 0.0f);
 }
 
 // ------------------------------------------------------------------ weight gradients
@@ -406,6 +561,13 @@ DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training) {
     L.a2 = take(2 * (size_t)(B * 32 * HW));
     L.a3 = take(2 * (size_t)(B * 32 * HW));
     L.y = take(4 * (size_t)(B * HW));
+    L.tc = (wa == 32 || wa == 64 || wa == 128) && B <= 65535 ? 1 : 0;
+    if (L.tc) {
+        L.xc = take(64 * (size_t)(B * HW));
+        L.c1 = take(64 * (size_t)(B * HW));
+        L.c2 = take(64 * (size_t)(B * HW));
+        L.wt = take(2 * (size_t)(3 * 9 * 32 * 32));
+    }
     if (training) {
         L.dy = take(4 * (size_t)(B * HW));
         L.d_hi = take(4 * (size_t)(B * 32 * HW));
@@ -416,8 +578,62 @@ DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training) {
     return L;
 }
 
+namespace {
+// Layers 0..2 on the tensor cores (x0 already stacked): a1, a2, a3 channels-first,
+// and the channels-last copies the next layer reads.
+cudaError_t forward_tc(const float* model, int ha, int wa, int B, uint8_t* ws, const DenoiseLayout& L,
+                       unsigned int* status, unsigned long long timeout_ns, cudaStream_t st) {
+    const int64_t HW = (int64_t)ha * wa;
+    auto* x0 = reinterpret_cast<const __nv_bfloat16*>(ws + L.x0);
+    auto* xc = reinterpret_cast<__nv_bfloat16*>(ws + L.xc);
+    auto* c1 = reinterpret_cast<__nv_bfloat16*>(ws + L.c1);
+    auto* c2 = reinterpret_cast<__nv_bfloat16*>(ws + L.c2);
+    auto* wt = reinterpret_cast<__nv_bfloat16*>(ws + L.wt);
+    __nv_bfloat16* acf[3] = {reinterpret_cast<__nv_bfloat16*>(ws + L.a1), reinterpret_cast<__nv_bfloat16*>(ws + L.a2),
+                             reinterpret_cast<__nv_bfloat16*>(ws + L.a3)};
+    const __nv_bfloat16* ins[3] = {xc, c1, c2};
+    __nv_bfloat16* outs_cl[3] = {c1, c2, nullptr};
+    const float* biases[3] = {model + kB0, model + kB1, model + kB2};
+    const int64_t n_pix = (int64_t)B * HW;
+    dn_x_to_cl_kernel<<<(unsigned)((n_pix + 255) / 256 < 4096 ? (n_pix + 255) / 256 : 4096), 256, 0, st>>>(x0, HW, n_pix,
+                                                                                                          xc);
+    dn_wprep_kernel<<<(3 * 9 * 32 * 32 + 255) / 256, 256, 0, st>>>(model, kW0, kW1, kW2, wt);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    static bool attr[64] = {};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const size_t smem = tc_smem(wa);
+    if (!attr[dev]) {
+        if ((e = cudaFuncSetAttribute(dn_conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)tc_smem(32) > (int)tc_smem(128) ? (int)tc_smem(32) : (int)tc_smem(128))) !=
+            cudaSuccess)
+            return e;
+        attr[dev] = true;
+    }
+    const int R = tc_rows(wa);
+    const uint64_t wdims[3] = {32, 32, 9}, wstr[2] = {64, 64 * 32};
+    const uint32_t wbox[3] = {32, 32, 9};
+    const uint64_t dims[4] = {32, (uint64_t)wa, (uint64_t)ha, (uint64_t)B};
+    const uint64_t str[3] = {64, (uint64_t)wa * 64, (uint64_t)HW * 64};
+    const uint32_t box[4] = {32, (uint32_t)wa, (uint32_t)(R + 2), 1};
+    for (int l = 0; l < 3; ++l) {
+        CUtensorMap in_map, w_map;
+        if (!make_bf16_map_sw64(&in_map, ins[l], 4, dims, str, box) ||
+            !make_bf16_map_sw64(&w_map, wt + (size_t)l * 9 * 32 * 32, 3, wdims, wstr, wbox))
+            return cudaErrorInvalidValue;
+        dn_conv_tc_kernel<<<dim3((unsigned)((ha + R - 1) / R), (unsigned)B), kTcThreads, smem, st>>>(
+            in_map, w_map, biases[l], acf[l], outs_cl[l], ha, wa, status, timeout_ns);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t denoise_forward(const float* model, const float* gamma_in, int ha, int wa, int hb, int wb,
-                            uint8_t* ws, const DenoiseLayout& L, cudaStream_t st) {
+                            uint8_t* ws, const DenoiseLayout& L, unsigned int* status,
+                            unsigned long long timeout_ns, cudaStream_t st) {
     const int B = hb * wb;
     const int64_t HW = (int64_t)ha * wa, n = (int64_t)B * HW;
     float* scale = reinterpret_cast<float*>(ws + L.scale);
@@ -433,9 +649,13 @@ cudaError_t denoise_forward(const float* model, const float* gamma_in, int ha, i
         gamma_in, scale, hb, wb, HW, x0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if ((e = conv<9, 32, kFwdHidden>(x0, nullptr, model + kW0, model + kB0, nullptr, a1, B, ha, wa, st)) != cudaSuccess) return e;
-    if ((e = conv<32, 32, kFwdHidden>(a1, nullptr, model + kW1, model + kB1, nullptr, a2, B, ha, wa, st)) != cudaSuccess) return e;
-    if ((e = conv<32, 32, kFwdHidden>(a2, nullptr, model + kW2, model + kB2, nullptr, a3, B, ha, wa, st)) != cudaSuccess) return e;
+    if (L.tc) {
+        if ((e = forward_tc(model, ha, wa, B, ws, L, status, timeout_ns, st)) != cudaSuccess) return e;
+    } else {
+        if ((e = conv<9, 32, kFwdHidden>(x0, nullptr, model + kW0, model + kB0, nullptr, a1, B, ha, wa, st)) != cudaSuccess) return e;
+        if ((e = conv<32, 32, kFwdHidden>(a1, nullptr, model + kW1, model + kB1, nullptr, a2, B, ha, wa, st)) != cudaSuccess) return e;
+        if ((e = conv<32, 32, kFwdHidden>(a2, nullptr, model + kW2, model + kB2, nullptr, a3, B, ha, wa, st)) != cudaSuccess) return e;
+    }
     return conv<32, 1, kFwdLast>(a3, nullptr, model + kW3, model + kB3, x0, y, B, ha, wa, st);
 }
 

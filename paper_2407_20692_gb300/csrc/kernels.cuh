@@ -149,12 +149,24 @@ cudaError_t launch_refocus4d_chunk(const float* gamma_f32, int ha, int wa, int h
 constexpr int kDenoiserParams = 21409;    // model blob floats
 constexpr int kDenoiseParts = 256;        // CTAs of a weight-gradient pass (fixed-order partials)
 struct DenoiseLayout {                    // byte offsets in the workspace
-    size_t scale, sums, x0, a1, a2, a3, y, dy, d_hi, d_lo, part, bytes;
+    size_t scale, sums, x0, a1, a2, a3, y, dy, d_hi, d_lo, part;
+    // tensor-core forward (widths 32, 64, 128): channels-last copies of x (padded
+    // to 32 channels), a1 and a2, and the bf16 weights of layers 0..2; tc = 0 if
+    // the width does not allow it
+    int tc;
+    size_t xc, c1, c2, wt, bytes;
 };
+// Tiled tensor map over a bfloat16 array of rank 3 or 4 with 64-byte swizzle
+// (box innermost extent 64 bytes); dims innermost first, strides in bytes for
+// dims 1..rank-1.  False if the driver rejects it.
+bool make_bf16_map_sw64(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                        const uint32_t* box);
 DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training);
-// scale, stacked input, activations and y of the network on gamma_in
+// scale, stacked input, activations and y of the network on gamma_in (status,
+// timeout_ns: the bounded waits of the tensor-core layers)
 cudaError_t denoise_forward(const float* model, const float* gamma_in, int ha, int wa, int hb, int wb,
-                            uint8_t* ws, const DenoiseLayout& L, cudaStream_t st);
+                            uint8_t* ws, const DenoiseLayout& L, unsigned int* status,
+                            unsigned long long timeout_ns, cudaStream_t st);
 cudaError_t denoise_output(const uint8_t* ws, const DenoiseLayout& L, int64_t n, float* gamma_out,
                            cudaStream_t st);
 // after denoise_forward: loss and gradient of the model blob

@@ -123,6 +123,24 @@ __device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* m
         : "memory");
 }
 
+// 3-D and 4-D tiled copies (same rules: x * element size a multiple of 16 bytes).
+__device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* m, uint64_t* bar, int32_t x,
+                                            int32_t y, int32_t z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void* smem_dst, const CUtensorMap* m, uint64_t* bar, int32_t x,
+                                            int32_t y, int32_t z, int32_t w) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5, %6}], [%2];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(m)), "r"(smem_u32(bar)), "r"(x), "r"(y), "r"(z), "r"(w)
+        : "memory");
+}
+
 // ---------------------------------------------------------------- tcgen05
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot_smem, uint32_t ncols) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -153,6 +171,20 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw128(uint32_t saddr) {
     d |= (uint64_t)(1024u >> 4) << 32;               // stride byte offset: next 8-row atom
     d |= (uint64_t)1u << 46;                         // descriptor version for tcgen05
     d |= (uint64_t)2u << 61;                         // swizzle mode: 128B
+    return d;
+}
+
+// K-major operand with 64-byte swizzle (rows of 64 bytes, 8-row atoms of 512
+// bytes); the start address may be any 8-row boundary of a 512-byte aligned
+// region, and advancing it by 32 bytes selects the row's second half (the next
+// 16 BF16 K-elements).
+__device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);        // start address (16-byte units)
+    d |= (uint64_t)1u << 16;                         // leading byte offset (unused here)
+    d |= (uint64_t)(512u >> 4) << 32;                // stride byte offset: next 8-row atom
+    d |= (uint64_t)1u << 46;                         // descriptor version for tcgen05
+    d |= (uint64_t)4u << 61;                         // swizzle mode: 64B
     return d;
 }
 

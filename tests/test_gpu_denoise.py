@@ -80,6 +80,41 @@ def test_denoise_forward_matches_oracle_on_sampled_slices_of_the_full_workload()
     assert d.mean() <= 2e-5 * ymax, d.mean() / ymax
 
 
+@pytest.mark.parametrize("hb,wb,ha,wa", [(2, 3, 10, 32), (2, 2, 5, 128)])
+def test_denoise_forward_tensor_core_widths_match_oracle(hb, wb, ha, wa):
+    """Widths 32 and 128 (the tensor-core layers; 64 is the workload test), with
+    row counts that leave the last row block of a slice ragged."""
+    blob = _model(12)
+    g = _gamma(13 + wa, hb, wb, ha, wa)
+    ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(_dev(g))
+    cpi.cpi_denoise(_dev(blob), _dev(g), out, ha, wa, hb, wb, ws)
+    torch.cuda.synchronize()
+    assert cpi.cpi_device_status() == 0
+    want = dn.denoise(blob, g.reshape(-1, ha, wa), hb, wb).reshape(hb * wb, -1)
+    s = dn.scale_of(g)
+    d = np.abs(out.cpu().numpy() - want) * s
+    ymax = np.abs(want).max() * s
+    assert d.max() <= 2e-3 * ymax, d.max() / ymax
+    assert d.mean() <= 2e-5 * ymax, d.mean() / ymax
+
+
+def test_denoise_gradient_through_tensor_core_forward_matches_oracle():
+    hb, wb, ha, wa = 2, 2, 8, 32
+    blob = _model(14)
+    g = _gamma(15, hb, wb, ha, wa)
+    t = _gamma(16, hb, wb, ha, wa) * 0.5 + g * 0.5
+    got, loss = _grad(blob, g, t, hb, wb, ha, wa)
+    want_loss, want = dn.loss_and_grad(blob, g.reshape(-1, ha, wa), t.reshape(-1, ha, wa), hb, wb)
+    assert abs(loss - want_loss) <= 1e-4 * want_loss
+    o = 0
+    for ci, co in dn.LAYERS:
+        n = co * ci * 9 + co
+        gl, wl = got[o:o + n], want[o:o + n]
+        assert np.abs(gl - wl).max() <= 2e-3 * np.abs(wl).max(), (ci, co, np.abs(gl - wl).max() / np.abs(wl).max())
+        o += n
+
+
 def _grad(blob, g, t, hb, wb, ha, wa):
     ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb, training=True), dtype=torch.uint8,
                      device="cuda")
