@@ -212,21 +212,30 @@ constexpr int kTcWBytes = 9 * 32 * 64;     // weights of one layer, bf16
 
 inline int tc_rows(int W) { return 256 / W; }
 inline size_t tc_copy_stride(int W) { return ((size_t)(tc_rows(W) + 2) * W * 64 + 1023) / 1024 * 1024; }
-inline size_t tc_smem(int W) { return 1024 + 3 * tc_copy_stride(W) + kTcWBytes + 64; }
+inline size_t tc_smem(int W) { return 1024 + 3 * tc_copy_stride(W) + kTcWBytes + 64; }   // NOUT <= 32
 
+// NOUT = 32: hidden layer (bias, ReLU, bf16 out).  NOUT = 16: the last layer
+// (32 -> 1, output channel 0 of 16; rows 1..15 of its weights are zero):
+// y = x0[centre channel] + sum + bias, float, channels-first.
+template <int NOUT>
 __global__ void __launch_bounds__(kTcThreads) dn_conv_tc_kernel(const __grid_constant__ CUtensorMap in_map,
                                                                 const __grid_constant__ CUtensorMap w_map,
                                                                 const float* __restrict__ bias,
                                                                 __nv_bfloat16* __restrict__ out_cf,
-                                                                __nv_bfloat16* __restrict__ out_cl, int H, int W,
+                                                                __nv_bfloat16* __restrict__ out_cl,
+                                                                const __nv_bfloat16* __restrict__ x0,
+                                                                float* __restrict__ y_out, int H, int W,
                                                                 unsigned int* status, unsigned long long timeout_ns) {
+    constexpr bool kLast = NOUT == 16;
+    constexpr int kWBytes = 9 * NOUT * 64;
+    constexpr uint32_t kCols = 2 * NOUT < 32 ? 32 : 2 * NOUT;   // TMEM allocation (power of 2, >= 32)
     extern __shared__ uint8_t smem_tc[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~(uintptr_t)1023);
     const int R = 256 / W;
     const size_t cstride = ((size_t)(R + 2) * W * 64 + 1023) / 1024 * 1024;
     const uint32_t copy_bytes = (uint32_t)((R + 2) * W * 64);
     uint8_t* sw = sm + 3 * cstride;
-    uint64_t* load_bar = reinterpret_cast<uint64_t*>(sw + kTcWBytes);
+    uint64_t* load_bar = reinterpret_cast<uint64_t*>(sw + kWBytes);
     uint64_t* mma_bar = load_bar + 1;
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_bar + 1);
     int* flag = reinterpret_cast<int*>(tmem_slot + 1);
@@ -239,7 +248,7 @@ __global__ void __launch_bounds__(kTcThreads) dn_conv_tc_kernel(const __grid_con
         fence_barrier_init();
     }
     if (warp == 0) {
-        tmem_alloc(tmem_slot, 64);
+        tmem_alloc(tmem_slot, kCols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -248,24 +257,24 @@ __global__ void __launch_bounds__(kTcThreads) dn_conv_tc_kernel(const __grid_con
     const uint32_t tmem_base = *tmem_slot;
 
     if (tid == 0) {
-        mbar_arrive_expect_tx(load_bar, 3 * copy_bytes + (uint32_t)kTcWBytes);
+        mbar_arrive_expect_tx(load_bar, 3 * copy_bytes + (uint32_t)kWBytes);
 #pragma unroll
         for (int kx = 0; kx < 3; ++kx) tma_load_4d(sm + kx * cstride, &in_map, load_bar, 0, kx - 1, y0 - 1, b);
         tma_load_3d(sw, &w_map, load_bar, 0, 0, 0);
         bool ok = mbar_wait_bounded(load_bar, 0, nullptr, status, timeout_ns);
         if (ok) {
             tc_fence_after();
-            constexpr uint32_t idesc = idesc_f32acc<true>(128, 32);
+            constexpr uint32_t idesc = idesc_f32acc<true>(128, NOUT);
 #pragma unroll
             for (int t = 0; t < 2; ++t)
 #pragma unroll
                 for (int tap = 0; tap < 9; ++tap) {
                     const int ky = tap / 3, kx = tap % 3;
                     const uint64_t a = sdesc_kmajor_sw64(smem_u32(sm + kx * cstride + (size_t)(ky * W + t * 128) * 64));
-                    const uint64_t bd = sdesc_kmajor_sw64(smem_u32(sw + tap * 32 * 64));
+                    const uint64_t bd = sdesc_kmajor_sw64(smem_u32(sw + tap * NOUT * 64));
 #pragma unroll
                     for (int h = 0; h < 2; ++h)   // second half of the 64-byte rows: +32 bytes
-                        umma_f32<true>(tmem_base + (uint32_t)(t * 32), a + (uint64_t)(2 * h), bd + (uint64_t)(2 * h),
+                        umma_f32<true>(tmem_base + (uint32_t)(t * NOUT), a + (uint64_t)(2 * h), bd + (uint64_t)(2 * h),
                                        idesc, (tap | h) ? 1u : 0u);
                 }
             umma_commit(mma_bar);
@@ -282,11 +291,22 @@ __global__ void __launch_bounds__(kTcThreads) dn_conv_tc_kernel(const __grid_con
         const int64_t HW = (int64_t)H * W;
 #pragma unroll 1
         for (int t = 0; t < 2; ++t) {
+            const int pl = t * 128 + 32 * warp + lane;
+            const int y = y0 + pl / W, x = pl - (pl / W) * W;
+            if constexpr (kLast) {
+                uint32_t r[16];
+                tmem_ld_32x32b_x16(tmem_base + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * NOUT), r);
+                tmem_ld_wait();
+                if (y < H) {
+                    const int64_t pix = (int64_t)y * W + x;
+                    const float xcen = __bfloat162float(x0[((int64_t)b * 9 + 4) * HW + pix]);
+                    y_out[(int64_t)b * HW + pix] = xcen + (__uint_as_float(r[0]) + __ldg(bias));
+                }
+                continue;
+            }
             uint32_t r[32];
             tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * 32), r);
             tmem_ld_wait();
-            const int pl = t * 128 + 32 * warp + lane;
-            const int y = y0 + pl / W, x = pl - (pl / W) * W;
             if (y < H) {
                 const int64_t pix = (int64_t)y * W + x;
                 uint32_t pk[16];
@@ -311,22 +331,31 @@ __global__ void __launch_bounds__(kTcThreads) dn_conv_tc_kernel(const __grid_con
     __syncthreads();
     if (warp == 0) {
         tc_fence_after();
-        tmem_dealloc(tmem_base, 64);
+        tmem_dealloc(tmem_base, kCols);
     }
 }
 
-// x (channels-first, 9 channels) -> channels-last with 32 channels (9..31 zero).
-__global__ void dn_x_to_cl_kernel(const __nv_bfloat16* __restrict__ x, int64_t HW, int64_t n_pix,
-                                  __nv_bfloat16* __restrict__ xc) {
+// The stacked input in both layouts, one thread per (slice, pixel):
+// x[b][c][p] = bf16(Gamma[nb(b, c)][p] * s) channels-first (9 channels) and
+// channels-last with 32 channels (9..31 zero).
+__global__ void dn_stack_both_kernel(const float* __restrict__ g, const float* __restrict__ scale, int hb, int wb,
+                                     int64_t HW, int64_t n_pix, __nv_bfloat16* __restrict__ x,
+                                     __nv_bfloat16* __restrict__ xc) {
+    const float s = *scale;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pix; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t b = i / HW, p = i - b * HW;
+        const int br = (int)(b / wb), bc = (int)(b - (int64_t)br * wb);
         uint32_t pk[16];
 #pragma unroll
         for (int c = 0; c < 16; ++c) pk[c] = 0u;
 #pragma unroll
         for (int c = 0; c < 9; ++c) {
-            const uint32_t v = __bfloat16_as_ushort(x[(b * 9 + c) * HW + p]);
-            pk[c / 2] |= (c & 1) ? (v << 16) : v;
+            const int r = br + c / 3 - 1, q = bc + c % 3 - 1;
+            const bool in = r >= 0 && r < hb && q >= 0 && q < wb;
+            const __nv_bfloat16 v = __float2bfloat16_rn(in ? g[(int64_t)(r * wb + q) * HW + p] * s : 0.0f);
+            x[(b * 9 + c) * HW + p] = v;
+            const uint32_t u = __bfloat16_as_ushort(v);
+            pk[c / 2] |= (c & 1) ? (u << 16) : u;
         }
         uint4* dst = reinterpret_cast<uint4*>(xc + i * 32);
 #pragma unroll
@@ -335,11 +364,17 @@ __global__ void dn_x_to_cl_kernel(const __nv_bfloat16* __restrict__ x, int64_t H
 }
 
 // Weights of layers 0..2 as bf16 [layer][tap][Cout][Cin = 32] (layer 0: Cin 9,
-// zero beyond).
-__global__ void dn_wprep_kernel(const float* __restrict__ model, int64_t w0, int64_t w1, int64_t w2,
+// zero beyond), then the last layer as [tap][16][32] (output channel 0 of 16).
+__global__ void dn_wprep_kernel(const float* __restrict__ model, int64_t w0, int64_t w1, int64_t w2, int64_t w3,
                                 __nv_bfloat16* __restrict__ wt) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 3 * 9 * 32 * 32) return;
+    if (i >= 3 * 9 * 32 * 32 + 9 * 16 * 32) return;
+    if (i >= 3 * 9 * 32 * 32) {   // last layer: [tap][16][32], output channel 0 only
+        const int rem = i - 3 * 9 * 32 * 32;
+        const int tap = rem / (16 * 32), co = (rem / 32) % 16, ci = rem % 32;
+        wt[i] = __float2bfloat16_rn(co == 0 ? model[w3 + (int64_t)ci * 9 + tap] : 0.0f);
+        return;
+    }
     const int l = i / (9 * 32 * 32), rem = i - l * 9 * 32 * 32;
     const int tap = rem / (32 * 32), co = (rem / 32) % 32, ci = rem % 32;
     const int cin = l == 0 ? 9 : 32;
@@ -566,7 +601,7 @@ DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training) {
         L.xc = take(64 * (size_t)(B * HW));
         L.c1 = take(64 * (size_t)(B * HW));
         L.c2 = take(64 * (size_t)(B * HW));
-        L.wt = take(2 * (size_t)(3 * 9 * 32 * 32));
+        L.wt = take(2 * (size_t)(3 * 9 * 32 * 32 + 9 * 16 * 32));
     }
     if (training) {
         L.dy = take(4 * (size_t)(B * HW));
@@ -579,52 +614,65 @@ DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training) {
 }
 
 namespace {
-// Layers 0..2 on the tensor cores (x0 already stacked): a1, a2, a3 channels-first,
-// and the channels-last copies the next layer reads.
-cudaError_t forward_tc(const float* model, int ha, int wa, int B, uint8_t* ws, const DenoiseLayout& L,
-                       unsigned int* status, unsigned long long timeout_ns, cudaStream_t st) {
+// The network on the tensor cores (scale already known): stacked input in both
+// layouts, layers 0..2 (a1, a2, a3 channels-first for the backward pass;
+// channels-last copies for the next layer, layer 2's into the input's buffer)
+// and the last layer into y.
+cudaError_t forward_tc(const float* model, const float* gamma_in, const float* scale, int ha, int wa, int hb,
+                       int wb, uint8_t* ws, const DenoiseLayout& L, unsigned int* status,
+                       unsigned long long timeout_ns, cudaStream_t st) {
+    const int B = hb * wb;
     const int64_t HW = (int64_t)ha * wa;
-    auto* x0 = reinterpret_cast<const __nv_bfloat16*>(ws + L.x0);
+    auto* x0 = reinterpret_cast<__nv_bfloat16*>(ws + L.x0);
     auto* xc = reinterpret_cast<__nv_bfloat16*>(ws + L.xc);
     auto* c1 = reinterpret_cast<__nv_bfloat16*>(ws + L.c1);
     auto* c2 = reinterpret_cast<__nv_bfloat16*>(ws + L.c2);
     auto* wt = reinterpret_cast<__nv_bfloat16*>(ws + L.wt);
+    float* y = reinterpret_cast<float*>(ws + L.y);
     __nv_bfloat16* acf[3] = {reinterpret_cast<__nv_bfloat16*>(ws + L.a1), reinterpret_cast<__nv_bfloat16*>(ws + L.a2),
                              reinterpret_cast<__nv_bfloat16*>(ws + L.a3)};
-    const __nv_bfloat16* ins[3] = {xc, c1, c2};
-    __nv_bfloat16* outs_cl[3] = {c1, c2, nullptr};
-    const float* biases[3] = {model + kB0, model + kB1, model + kB2};
+    const __nv_bfloat16* ins[4] = {xc, c1, c2, xc};
+    __nv_bfloat16* outs_cl[3] = {c1, c2, xc};
+    const float* biases[4] = {model + kB0, model + kB1, model + kB2, model + kB3};
     const int64_t n_pix = (int64_t)B * HW;
-    dn_x_to_cl_kernel<<<(unsigned)((n_pix + 255) / 256 < 4096 ? (n_pix + 255) / 256 : 4096), 256, 0, st>>>(x0, HW, n_pix,
-                                                                                                          xc);
-    dn_wprep_kernel<<<(3 * 9 * 32 * 32 + 255) / 256, 256, 0, st>>>(model, kW0, kW1, kW2, wt);
+    dn_stack_both_kernel<<<(unsigned)((n_pix + 255) / 256 < 4096 ? (n_pix + 255) / 256 : 4096), 256, 0, st>>>(
+        gamma_in, scale, hb, wb, HW, n_pix, x0, xc);
+    dn_wprep_kernel<<<(3 * 9 * 32 * 32 + 9 * 16 * 32 + 255) / 256, 256, 0, st>>>(model, kW0, kW1, kW2, kW3, wt);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     static bool attr[64] = {};
     int dev = 0;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
-    const size_t smem = tc_smem(wa);
+    const int smax = (int)(tc_smem(32) > tc_smem(128) ? tc_smem(32) : tc_smem(128));
     if (!attr[dev]) {
-        if ((e = cudaFuncSetAttribute(dn_conv_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)tc_smem(32) > (int)tc_smem(128) ? (int)tc_smem(32) : (int)tc_smem(128))) !=
-            cudaSuccess)
+        if ((e = cudaFuncSetAttribute(dn_conv_tc_kernel<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)) !=
+                cudaSuccess ||
+            (e = cudaFuncSetAttribute(dn_conv_tc_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax)) !=
+                cudaSuccess)
             return e;
         attr[dev] = true;
     }
+    const size_t smem = tc_smem(wa);
     const int R = tc_rows(wa);
-    const uint64_t wdims[3] = {32, 32, 9}, wstr[2] = {64, 64 * 32};
-    const uint32_t wbox[3] = {32, 32, 9};
+    const dim3 grid((unsigned)((ha + R - 1) / R), (unsigned)B);
     const uint64_t dims[4] = {32, (uint64_t)wa, (uint64_t)ha, (uint64_t)B};
     const uint64_t str[3] = {64, (uint64_t)wa * 64, (uint64_t)HW * 64};
     const uint32_t box[4] = {32, (uint32_t)wa, (uint32_t)(R + 2), 1};
-    for (int l = 0; l < 3; ++l) {
+    for (int l = 0; l < 4; ++l) {
+        const int nout = l < 3 ? 32 : 16;
+        const uint64_t wdims[3] = {32, (uint64_t)nout, 9}, wstr[2] = {64, 64 * (uint64_t)nout};
+        const uint32_t wbox[3] = {32, (uint32_t)nout, 9};
         CUtensorMap in_map, w_map;
         if (!make_bf16_map_sw64(&in_map, ins[l], 4, dims, str, box) ||
             !make_bf16_map_sw64(&w_map, wt + (size_t)l * 9 * 32 * 32, 3, wdims, wstr, wbox))
             return cudaErrorInvalidValue;
-        dn_conv_tc_kernel<<<dim3((unsigned)((ha + R - 1) / R), (unsigned)B), kTcThreads, smem, st>>>(
-            in_map, w_map, biases[l], acf[l], outs_cl[l], ha, wa, status, timeout_ns);
+        if (l < 3)
+            dn_conv_tc_kernel<32><<<grid, kTcThreads, smem, st>>>(in_map, w_map, biases[l], acf[l], outs_cl[l], nullptr,
+                                                                  nullptr, ha, wa, status, timeout_ns);
+        else
+            dn_conv_tc_kernel<16><<<grid, kTcThreads, smem, st>>>(in_map, w_map, biases[l], nullptr, nullptr, x0, y,
+                                                                  ha, wa, status, timeout_ns);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -645,17 +693,15 @@ cudaError_t denoise_forward(const float* model, const float* gamma_in, int ha, i
     float* y = reinterpret_cast<float*>(ws + L.y);
     dn_sumsq_kernel<<<kSumBlocks, 256, 0, st>>>(gamma_in, n, sums);
     dn_scale_kernel<<<1, 32, 0, st>>>(sums, kSumBlocks, n, scale);
-    dn_stack_kernel<<<dim3((unsigned)((HW + 255) / 256 < 64 ? (HW + 255) / 256 : 64), 9, (unsigned)B), 256, 0, st>>>(
-        gamma_in, scale, hb, wb, HW, x0);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (L.tc) {
-        if ((e = forward_tc(model, ha, wa, B, ws, L, status, timeout_ns, st)) != cudaSuccess) return e;
-    } else {
-        if ((e = conv<9, 32, kFwdHidden>(x0, nullptr, model + kW0, model + kB0, nullptr, a1, B, ha, wa, st)) != cudaSuccess) return e;
-        if ((e = conv<32, 32, kFwdHidden>(a1, nullptr, model + kW1, model + kB1, nullptr, a2, B, ha, wa, st)) != cudaSuccess) return e;
-        if ((e = conv<32, 32, kFwdHidden>(a2, nullptr, model + kW2, model + kB2, nullptr, a3, B, ha, wa, st)) != cudaSuccess) return e;
-    }
+    if (L.tc) return forward_tc(model, gamma_in, scale, ha, wa, hb, wb, ws, L, status, timeout_ns, st);
+    dn_stack_kernel<<<dim3((unsigned)((HW + 255) / 256 < 64 ? (HW + 255) / 256 : 64), 9, (unsigned)B), 256, 0, st>>>(
+        gamma_in, scale, hb, wb, HW, x0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = conv<9, 32, kFwdHidden>(x0, nullptr, model + kW0, model + kB0, nullptr, a1, B, ha, wa, st)) != cudaSuccess) return e;
+    if ((e = conv<32, 32, kFwdHidden>(a1, nullptr, model + kW1, model + kB1, nullptr, a2, B, ha, wa, st)) != cudaSuccess) return e;
+    if ((e = conv<32, 32, kFwdHidden>(a2, nullptr, model + kW2, model + kB2, nullptr, a3, B, ha, wa, st)) != cudaSuccess) return e;
     return conv<32, 1, kFwdLast>(a3, nullptr, model + kW3, model + kB3, x0, y, B, ha, wa, st);
 }
 
