@@ -678,6 +678,10 @@ def run_denoise(args, world, rank):
     step_s = train_ms / 1e3 / n_steps
     peak = SM_COUNT * 128 * 2 * _peaks()[0].get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     ach = flops / step_s / 1e12
+    # inference: the forward network on tcgen05 (widths 32/64/128), one Gamma
+    fwd_flops = 2.0 * hb * wb * ha * wa * 9 * (9 * 32 + 32 * 32 + 32 * 32 + 32)
+    tc_peak = _peaks()[0]["bf16_tflops"]
+    fwd_ach = fwd_flops / (infer_ms / 1e3) / 1e12
     if args.save_model:
         np.save(args.save_model, model.cpu().numpy())
     return {
@@ -701,10 +705,15 @@ def run_denoise(args, world, rank):
                      "loss_first_last": [float(lh[:16].mean()), float(lh[-16:].mean())],
                      "train_ms_per_step": train_ms / n_steps, "infer_ms_per_gamma": infer_ms,
                      "data_s": t_data},
-        "roofline": {"kernel": "denoiser training step (direct bf16/fp32 3x3 convolutions on the FP32 pipe)",
-                     "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                     "traffic": None, "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock",
-                     "work": "forward + input gradients + weight gradients of one Gamma (1024 slices)"},
+        "roofline": {"kernel": "denoiser inference (4 convolutions as tcgen05 implicit GEMMs, bf16 in, FP32 sums)",
+                     "bound": "tensor", "achieved": fwd_ach, "peak": tc_peak, "unit": "TFLOP/s",
+                     "frac": fwd_ach / tc_peak, "traffic": None, "peak_source": "measured bf16 burst",
+                     "work": "forward network of one Gamma (1024 slices of 64 x 64; MMA padding not counted)"},
+        "roofline_training": {"kernel": "denoiser training step (forward on tcgen05; backward: direct bf16/fp32 "
+                                        "3x3 convolutions on the FP32 pipe)",
+                              "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+                              "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock",
+                              "work": "forward + input gradients + weight gradients of one Gamma (1024 slices)"},
         "gpu_launches": None,
     }
 
