@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(kConvThreads)
 // ------------------------------------------------------------------ tensor-core forward
 // Layers 0..2 (32 -> 32 channels; the 9-channel input is padded to 32 with zero
 // channels and zero weights) as implicit GEMMs on tcgen05, for image widths 32,
-// 64 and 128.  A CTA computes R = 256 / W output rows of one slice (two tiles of
+// 64 and 128.  A unit is R = 256 / W output rows of one slice (two tiles of
 // M = 128 pixels) for the 32 output channels.  The layer input is channels-last
 // bf16 (64 bytes per pixel); TMA loads three copies of rows y0 - 1 .. y0 + R
 // with the columns shifted by -1, 0, +1 (zeros outside the image), 64-byte
@@ -205,49 +205,69 @@ __global__ void __launch_bounds__(kConvThreads)
 // one TMA box.  Per tile 9 taps x 2 MMAs (M = 128, N = 32, K = 16) accumulate in
 // 32 TMEM columns (FP32 sums); the epilogue adds the bias, applies ReLU, rounds
 // to bf16 and writes channels-first (for the backward pass and the last layer)
-// and, if asked, channels-last (the next layer's input).  Waits are bounded; on
-// a time-out the CTA records it, drains its copies and MMAs and writes nothing.
-constexpr int kTcThreads = 128;
+// and, if asked, channels-last (the next layer's input).  The last layer runs
+// the same kernel with 16 output columns.
 constexpr int kTcWBytes = 9 * 32 * 64;     // weights of one layer, bf16
 
 inline int tc_rows(int W) { return 256 / W; }
 inline size_t tc_copy_stride(int W) { return ((size_t)(tc_rows(W) + 2) * W * 64 + 1023) / 1024 * 1024; }
-inline size_t tc_smem(int W) { return 1024 + 3 * tc_copy_stride(W) + kTcWBytes + 64; }   // NOUT <= 32
+inline size_t tc_smem(int W) { return 1024 + 6 * tc_copy_stride(W) + kTcWBytes + 128; }   // 2 stages, NOUT <= 32
 
 // NOUT = 32: hidden layer (bias, ReLU, bf16 out).  NOUT = 16: the last layer
 // (32 -> 1, output channel 0 of 16; rows 1..15 of its weights are zero):
 // y = x0[centre channel] + sum + bias, float, channels-first.
+//
+// Persistent: one CTA per SM walks the units u = (slice, block of R rows).
+// Warp 0 (one thread) loads the weights once and then each unit's three copies
+// into one of two stages; warp 1 (one thread) issues the unit's MMAs into one
+// of two TMEM accumulators (2 tiles x NOUT columns each) and frees the stage;
+// warps 2..5 drain an accumulator (TMEM lane quarter = warp % 4) while the next
+// unit is loaded and multiplied.  Every wait is bounded; on a time-out the CTA
+// records it, drains its own copies and MMAs, frees its tensor memory and stops.
+constexpr int kTcThreadsP = 192;
 template <int NOUT>
-__global__ void __launch_bounds__(kTcThreads) dn_conv_tc_kernel(const __grid_constant__ CUtensorMap in_map,
-                                                                const __grid_constant__ CUtensorMap w_map,
-                                                                const float* __restrict__ bias,
-                                                                __nv_bfloat16* __restrict__ out_cf,
-                                                                __nv_bfloat16* __restrict__ out_cl,
-                                                                const __nv_bfloat16* __restrict__ x0,
-                                                                float* __restrict__ y_out, int H, int W,
-                                                                unsigned int* status, unsigned long long timeout_ns) {
+__global__ void __launch_bounds__(kTcThreadsP, 1) dn_conv_tc_kernel(const __grid_constant__ CUtensorMap in_map,
+                                                                   const __grid_constant__ CUtensorMap w_map,
+                                                                   const float* __restrict__ bias,
+                                                                   __nv_bfloat16* __restrict__ out_cf,
+                                                                   __nv_bfloat16* __restrict__ out_cl,
+                                                                   const __nv_bfloat16* __restrict__ x0,
+                                                                   float* __restrict__ y_out, int H, int W,
+                                                                   int n_slices, unsigned int* status,
+                                                                   unsigned long long timeout_ns) {
     constexpr bool kLast = NOUT == 16;
     constexpr int kWBytes = 9 * NOUT * 64;
-    constexpr uint32_t kCols = 2 * NOUT < 32 ? 32 : 2 * NOUT;   // TMEM allocation (power of 2, >= 32)
+    constexpr uint32_t kCols = 4 * NOUT;                        // 2 accumulators x 2 tiles x NOUT (64 or 128)
     extern __shared__ uint8_t smem_tc[];
     uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_tc) + 1023) & ~(uintptr_t)1023);
     const int R = 256 / W;
+    const int nrb = (H + R - 1) / R, n_units = nrb * n_slices;
     const size_t cstride = ((size_t)(R + 2) * W * 64 + 1023) / 1024 * 1024;
     const uint32_t copy_bytes = (uint32_t)((R + 2) * W * 64);
-    uint8_t* sw = sm + 3 * cstride;
-    uint64_t* load_bar = reinterpret_cast<uint64_t*>(sw + kWBytes);
-    uint64_t* mma_bar = load_bar + 1;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mma_bar + 1);
-    int* flag = reinterpret_cast<int*>(tmem_slot + 1);
+    uint8_t* sw = sm + 6 * cstride;                             // stages: [2][3 copies]
+    uint64_t* full = reinterpret_cast<uint64_t*>(sw + kWBytes);
+    uint64_t* empty = full + 2;
+    uint64_t* tfull = empty + 2;
+    uint64_t* tempty = tfull + 2;
+    uint64_t* wbar = tempty + 2;
+    uint64_t* drain = wbar + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int b = blockIdx.y, y0 = blockIdx.x * R;
 
     if (tid == 0) {
-        mbar_init(load_bar, 1);
-        mbar_init(mma_bar, 1);
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(&full[k], 1);
+            mbar_init(&empty[k], 1);
+            mbar_init(&tfull[k], 1);
+            mbar_init(&tempty[k], 128);
+        }
+        mbar_init(wbar, 1);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
         fence_barrier_init();
     }
-    if (warp == 0) {
+    if (warp == 1) {
         tmem_alloc(tmem_slot, kCols);
         tmem_relinquish();
     }
@@ -256,80 +276,140 @@ __global__ void __launch_bounds__(kTcThreads) dn_conv_tc_kernel(const __grid_con
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
 
-    if (tid == 0) {
-        mbar_arrive_expect_tx(load_bar, 3 * copy_bytes + (uint32_t)kWBytes);
+    if (warp == 0) {
+        if (lane == 0) {
+            // ------------------------------------------------------ producer
+            mbar_arrive_expect_tx(wbar, (uint32_t)kWBytes);
+            tma_load_3d(sw, &w_map, wbar, 0, 0, 0);
+            int stage = 0;
+            uint32_t phase = 0, issued = 0, issued_phase = 0;
+            for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+                const int b = u / nrb, y0 = (u - b * nrb) * R;
+                if (!mbar_wait_bounded(&empty[stage], phase ^ 1, abort_flag, status, timeout_ns)) break;
+                mbar_arrive_expect_tx(&full[stage], 3 * copy_bytes);
 #pragma unroll
-        for (int kx = 0; kx < 3; ++kx) tma_load_4d(sm + kx * cstride, &in_map, load_bar, 0, kx - 1, y0 - 1, b);
-        tma_load_3d(sw, &w_map, load_bar, 0, 0, 0);
-        bool ok = mbar_wait_bounded(load_bar, 0, nullptr, status, timeout_ns);
-        if (ok) {
-            tc_fence_after();
+                for (int kx = 0; kx < 3; ++kx)
+                    tma_load_4d(sm + (size_t)(stage * 3 + kx) * cstride, &in_map, &full[stage], 0, kx - 1, y0 - 1, b);
+                issued |= 1u << stage;
+                issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+                if (++stage == 2) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+            }
+            if (*abort_flag) {   // copies of this thread still in flight must land before the CTA ends
+                mbar_wait_bounded(wbar, 0, nullptr, nullptr, timeout_ns);
+                for (int k = 0; k < 2; ++k)
+                    if (issued & (1u << k)) mbar_wait_bounded(&full[k], (issued_phase >> k) & 1u, nullptr, nullptr, timeout_ns);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ------------------------------------------------------ MMA issuer
             constexpr uint32_t idesc = idesc_f32acc<true>(128, NOUT);
-#pragma unroll
-            for (int t = 0; t < 2; ++t)
-#pragma unroll
-                for (int tap = 0; tap < 9; ++tap) {
-                    const int ky = tap / 3, kx = tap % 3;
-                    const uint64_t a = sdesc_kmajor_sw64(smem_u32(sm + kx * cstride + (size_t)(ky * W + t * 128) * 64));
-                    const uint64_t bd = sdesc_kmajor_sw64(smem_u32(sw + tap * NOUT * 64));
-#pragma unroll
-                    for (int h = 0; h < 2; ++h)   // second half of the 64-byte rows: +32 bytes
-                        umma_f32<true>(tmem_base + (uint32_t)(t * NOUT), a + (uint64_t)(2 * h), bd + (uint64_t)(2 * h),
-                                       idesc, (tap | h) ? 1u : 0u);
+            bool ok = mbar_wait_bounded(wbar, 0, abort_flag, status, timeout_ns), any = false;
+            int stage = 0, acc = 0;
+            uint32_t phase = 0, acc_phase = 0;
+            for (int u = blockIdx.x; ok && u < n_units; u += gridDim.x) {
+                if (!mbar_wait_bounded(&tempty[acc], acc_phase ^ 1, abort_flag, status, timeout_ns) ||
+                    !mbar_wait_bounded(&full[stage], phase, abort_flag, status, timeout_ns)) {
+                    ok = false;
+                    break;
                 }
-            umma_commit(mma_bar);
-            ok = mbar_wait_bounded(mma_bar, 0, nullptr, status, timeout_ns);
-            if (!ok) mbar_wait_bounded(mma_bar, 0, nullptr, nullptr, timeout_ns);   // drain the MMAs
-        } else {
-            mbar_wait_bounded(load_bar, 0, nullptr, nullptr, timeout_ns);           // drain the copies
+                tc_fence_after();
+                const uint32_t d0 = tmem_base + (uint32_t)(acc * 2 * NOUT);
+#pragma unroll
+                for (int t = 0; t < 2; ++t)
+#pragma unroll
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int ky = tap / 3, kx = tap % 3;
+                        const uint64_t a = sdesc_kmajor_sw64(
+                            smem_u32(sm + (size_t)(stage * 3 + kx) * cstride + (size_t)(ky * W + t * 128) * 64));
+                        const uint64_t bd = sdesc_kmajor_sw64(smem_u32(sw + tap * NOUT * 64));
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)   // second half of the 64-byte rows: +32 bytes
+                            umma_f32<true>(d0 + (uint32_t)(t * NOUT), a + (uint64_t)(2 * h), bd + (uint64_t)(2 * h),
+                                           idesc, (tap | h) ? 1u : 0u);
+                    }
+                any = true;
+                umma_commit(&empty[stage]);
+                umma_commit(&tfull[acc]);
+                if (++stage == 2) {
+                    stage = 0;
+                    phase ^= 1;
+                }
+                if (++acc == 2) {
+                    acc = 0;
+                    acc_phase ^= 1;
+                }
+            }
+            if (!ok && any) {   // the MMAs issued must finish before the tensor memory is freed
+                umma_commit(drain);
+                mbar_wait_bounded(drain, 0, nullptr, nullptr, timeout_ns);
+            }
         }
-        *flag = ok ? 1 : 0;
-    }
-    __syncthreads();
-    if (*flag) {
-        tc_fence_after();
+    } else {
+        // ---------------------------------------------------------- epilogue
+        const int q = warp & 3;                                   // TMEM lane quarter
         const int64_t HW = (int64_t)H * W;
+        int acc = 0;
+        uint32_t acc_phase = 0;
+        for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+            const int b = u / nrb, y0 = (u - b * nrb) * R;
+            if (!mbar_wait_bounded(&tfull[acc], acc_phase, abort_flag, status, timeout_ns)) break;
+            tc_fence_after();
+            const uint32_t d0 = tmem_base + ((uint32_t)(32 * q) << 16) + (uint32_t)(acc * 2 * NOUT);
 #pragma unroll 1
-        for (int t = 0; t < 2; ++t) {
-            const int pl = t * 128 + 32 * warp + lane;
-            const int y = y0 + pl / W, x = pl - (pl / W) * W;
-            if constexpr (kLast) {
-                uint32_t r[16];
-                tmem_ld_32x32b_x16(tmem_base + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * NOUT), r);
-                tmem_ld_wait();
-                if (y < H) {
-                    const int64_t pix = (int64_t)y * W + x;
-                    const float xcen = __bfloat162float(x0[((int64_t)b * 9 + 4) * HW + pix]);
-                    y_out[(int64_t)b * HW + pix] = xcen + (__uint_as_float(r[0]) + __ldg(bias));
+            for (int t = 0; t < 2; ++t) {
+                const int pl = t * 128 + 32 * q + lane;
+                const int y = y0 + pl / W, x = pl - (pl / W) * W;
+                if constexpr (kLast) {
+                    uint32_t r[16];
+                    tmem_ld_32x32b_x16(d0 + (uint32_t)(t * NOUT), r);
+                    tmem_ld_wait();
+                    if (y < H) {
+                        const int64_t pix = (int64_t)y * W + x;
+                        const float xcen = __bfloat162float(x0[((int64_t)b * 9 + 4) * HW + pix]);
+                        y_out[(int64_t)b * HW + pix] = xcen + (__uint_as_float(r[0]) + __ldg(bias));
+                    }
+                } else {
+                    uint32_t r[32];
+                    tmem_ld_32x32b_x32(d0 + (uint32_t)(t * NOUT), r);
+                    tmem_ld_wait();
+                    if (y < H) {
+                        const int64_t pix = (int64_t)y * W + x;
+                        uint32_t pk[16];
+#pragma unroll
+                        for (int co = 0; co < 32; co += 2) {
+                            const __nv_bfloat16 v0 =
+                                __float2bfloat16_rn(fmaxf(__uint_as_float(r[co]) + __ldg(bias + co), 0.0f));
+                            const __nv_bfloat16 v1 =
+                                __float2bfloat16_rn(fmaxf(__uint_as_float(r[co + 1]) + __ldg(bias + co + 1), 0.0f));
+                            out_cf[((int64_t)b * 32 + co) * HW + pix] = v0;
+                            out_cf[((int64_t)b * 32 + co + 1) * HW + pix] = v1;
+                            pk[co / 2] = (uint32_t)__bfloat16_as_ushort(v0) | ((uint32_t)__bfloat16_as_ushort(v1) << 16);
+                        }
+                        if (out_cl != nullptr) {
+                            uint4* dst = reinterpret_cast<uint4*>(out_cl + ((int64_t)b * HW + pix) * 32);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k)
+                                dst[k] = make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+                        }
+                    }
                 }
-                continue;
             }
-            uint32_t r[32];
-            tmem_ld_32x32b_x32(tmem_base + ((uint32_t)(32 * warp) << 16) + (uint32_t)(t * 32), r);
-            tmem_ld_wait();
-            if (y < H) {
-                const int64_t pix = (int64_t)y * W + x;
-                uint32_t pk[16];
-#pragma unroll
-                for (int co = 0; co < 32; co += 2) {
-                    const __nv_bfloat16 v0 = __float2bfloat16_rn(fmaxf(__uint_as_float(r[co]) + __ldg(bias + co), 0.0f));
-                    const __nv_bfloat16 v1 =
-                        __float2bfloat16_rn(fmaxf(__uint_as_float(r[co + 1]) + __ldg(bias + co + 1), 0.0f));
-                    out_cf[((int64_t)b * 32 + co) * HW + pix] = v0;
-                    out_cf[((int64_t)b * 32 + co + 1) * HW + pix] = v1;
-                    pk[co / 2] = (uint32_t)__bfloat16_as_ushort(v0) | ((uint32_t)__bfloat16_as_ushort(v1) << 16);
-                }
-                if (out_cl != nullptr) {
-                    uint4* dst = reinterpret_cast<uint4*>(out_cl + ((int64_t)b * HW + pix) * 32);
-#pragma unroll
-                    for (int q = 0; q < 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
-                }
+            tc_fence_before();
+            mbar_arrive(&tempty[acc]);
+            if (++acc == 2) {
+                acc = 0;
+                acc_phase ^= 1;
             }
         }
     }
+
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) {
+    if (warp == 1) {
         tc_fence_after();
         tmem_dealloc(tmem_base, kCols);
     }
@@ -655,7 +735,10 @@ cudaError_t forward_tc(const float* model, const float* gamma_in, const float* s
     }
     const size_t smem = tc_smem(wa);
     const int R = tc_rows(wa);
-    const dim3 grid((unsigned)((ha + R - 1) / R), (unsigned)B);
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    const int64_t units = (int64_t)((ha + R - 1) / R) * B;
+    const dim3 grid((unsigned)(units < sms ? units : sms));
     const uint64_t dims[4] = {32, (uint64_t)wa, (uint64_t)ha, (uint64_t)B};
     const uint64_t str[3] = {64, (uint64_t)wa * 64, (uint64_t)HW * 64};
     const uint32_t box[4] = {32, (uint32_t)wa, (uint32_t)(R + 2), 1};
@@ -668,11 +751,11 @@ cudaError_t forward_tc(const float* model, const float* gamma_in, const float* s
             !make_bf16_map_sw64(&w_map, wt + (size_t)l * 9 * 32 * 32, 3, wdims, wstr, wbox))
             return cudaErrorInvalidValue;
         if (l < 3)
-            dn_conv_tc_kernel<32><<<grid, kTcThreads, smem, st>>>(in_map, w_map, biases[l], acf[l], outs_cl[l], nullptr,
-                                                                  nullptr, ha, wa, status, timeout_ns);
+            dn_conv_tc_kernel<32><<<grid, kTcThreadsP, smem, st>>>(in_map, w_map, biases[l], acf[l], outs_cl[l],
+                                                                   nullptr, nullptr, ha, wa, B, status, timeout_ns);
         else
-            dn_conv_tc_kernel<16><<<grid, kTcThreads, smem, st>>>(in_map, w_map, biases[l], nullptr, nullptr, x0, y,
-                                                                  ha, wa, status, timeout_ns);
+            dn_conv_tc_kernel<16><<<grid, kTcThreadsP, smem, st>>>(in_map, w_map, biases[l], nullptr, nullptr, x0, y,
+                                                                   ha, wa, B, status, timeout_ns);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
     return cudaSuccess;
