@@ -912,7 +912,7 @@ cpi_status cpi_denoise(const float* model, const float* gamma_in, float* gamma_o
     if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t* ws = static_cast<uint8_t*>(workspace);
-    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, dev->status, g_timeout_ns, st);
+    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, false, dev->status, g_timeout_ns, st);
     if (e == cudaSuccess) e = denoise_output(ws, L, (int64_t)hb * wb * ha * wa, gamma_out, st);
     return cuda_status(e);
 }
@@ -928,7 +928,7 @@ cpi_status cpi_denoise_grad(const float* model, const float* gamma_in, const flo
     if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t* ws = static_cast<uint8_t*>(workspace);
-    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, dev->status, g_timeout_ns, st);
+    cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, true, dev->status, g_timeout_ns, st);
     if (e == cudaSuccess) e = denoise_backward(model, gamma_target, ha, wa, hb, wb, ws, L, grad, loss, st);
     return cuda_status(e);
 }

@@ -205,8 +205,9 @@ __global__ void __launch_bounds__(kConvThreads)
 // one TMA box.  Per tile 9 taps x 2 MMAs (M = 128, N = 32, K = 16) accumulate in
 // 32 TMEM columns (FP32 sums); the epilogue adds the bias, applies ReLU, rounds
 // to bf16 and writes channels-first (for the backward pass and the last layer)
-// and, if asked, channels-last (the next layer's input).  The last layer runs
-// the same kernel with 16 output columns.
+// and channels-last (the next layer's input), each only if asked (inference
+// needs no channels-first activations).  The last layer runs the same kernel
+// with 16 output columns.
 constexpr int kTcWBytes = 9 * 32 * 64;     // weights of one layer, bf16
 
 inline int tc_rows(int W) { return 256 / W; }
@@ -224,7 +225,7 @@ inline size_t tc_smem(int W) { return 1024 + 6 * tc_copy_stride(W) + kTcWBytes +
 // warps 2..5 drain an accumulator (TMEM lane quarter = warp % 4) while the next
 // unit is loaded and multiplied.  Every wait is bounded; on a time-out the CTA
 // records it, drains its own copies and MMAs, frees its tensor memory and stops.
-constexpr int kTcThreadsP = 192;
+constexpr int kTcThreadsP = 192;          // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
 template <int NOUT>
 __global__ void __launch_bounds__(kTcThreadsP, 1) dn_conv_tc_kernel(const __grid_constant__ CUtensorMap in_map,
                                                                    const __grid_constant__ CUtensorMap w_map,
@@ -372,30 +373,29 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) dn_conv_tc_kernel(const __grid
                         const float xcen = __bfloat162float(x0[((int64_t)b * 9 + 4) * HW + pix]);
                         y_out[(int64_t)b * HW + pix] = xcen + (__uint_as_float(r[0]) + __ldg(bias));
                     }
-                } else {
-                    uint32_t r[32];
-                    tmem_ld_32x32b_x32(d0 + (uint32_t)(t * NOUT), r);
-                    tmem_ld_wait();
-                    if (y < H) {
-                        const int64_t pix = (int64_t)y * W + x;
-                        uint32_t pk[16];
+                    continue;
+                }
+                uint32_t r[32];
+                tmem_ld_32x32b_x32(d0 + (uint32_t)(t * NOUT), r);
+                tmem_ld_wait();
+                if (y >= H) continue;
+                const int64_t pix = (int64_t)y * W + x;
+                uint32_t pk[16];
 #pragma unroll
-                        for (int co = 0; co < 32; co += 2) {
-                            const __nv_bfloat16 v0 =
-                                __float2bfloat16_rn(fmaxf(__uint_as_float(r[co]) + __ldg(bias + co), 0.0f));
-                            const __nv_bfloat16 v1 =
-                                __float2bfloat16_rn(fmaxf(__uint_as_float(r[co + 1]) + __ldg(bias + co + 1), 0.0f));
-                            out_cf[((int64_t)b * 32 + co) * HW + pix] = v0;
-                            out_cf[((int64_t)b * 32 + co + 1) * HW + pix] = v1;
-                            pk[co / 2] = (uint32_t)__bfloat16_as_ushort(v0) | ((uint32_t)__bfloat16_as_ushort(v1) << 16);
-                        }
-                        if (out_cl != nullptr) {
-                            uint4* dst = reinterpret_cast<uint4*>(out_cl + ((int64_t)b * HW + pix) * 32);
-#pragma unroll
-                            for (int k = 0; k < 4; ++k)
-                                dst[k] = make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
-                        }
+                for (int co = 0; co < 32; co += 2) {
+                    const __nv_bfloat16 v0 = __float2bfloat16_rn(fmaxf(__uint_as_float(r[co]) + __ldg(bias + co), 0.0f));
+                    const __nv_bfloat16 v1 =
+                        __float2bfloat16_rn(fmaxf(__uint_as_float(r[co + 1]) + __ldg(bias + co + 1), 0.0f));
+                    if (out_cf != nullptr) {
+                        out_cf[((int64_t)b * 32 + co) * HW + pix] = v0;
+                        out_cf[((int64_t)b * 32 + co + 1) * HW + pix] = v1;
                     }
+                    pk[co / 2] = (uint32_t)__bfloat16_as_ushort(v0) | ((uint32_t)__bfloat16_as_ushort(v1) << 16);
+                }
+                if (out_cl != nullptr) {
+                    uint4* dst = reinterpret_cast<uint4*>(out_cl + ((int64_t)b * HW + pix) * 32);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) dst[k] = make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
                 }
             }
             tc_fence_before();
@@ -695,11 +695,11 @@ DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training) {
 
 namespace {
 // The network on the tensor cores (scale already known): stacked input in both
-// layouts, layers 0..2 (a1, a2, a3 channels-first for the backward pass;
-// channels-last copies for the next layer, layer 2's into the input's buffer)
-// and the last layer into y.
+// layouts, layers 0..2 (a1, a2, a3 channels-first for the backward pass when
+// keep_cf; channels-last copies for the next layer, layer 2's into the input's
+// buffer) and the last layer into y.
 cudaError_t forward_tc(const float* model, const float* gamma_in, const float* scale, int ha, int wa, int hb,
-                       int wb, uint8_t* ws, const DenoiseLayout& L, unsigned int* status,
+                       int wb, uint8_t* ws, const DenoiseLayout& L, bool keep_cf, unsigned int* status,
                        unsigned long long timeout_ns, cudaStream_t st) {
     const int B = hb * wb;
     const int64_t HW = (int64_t)ha * wa;
@@ -709,8 +709,9 @@ cudaError_t forward_tc(const float* model, const float* gamma_in, const float* s
     auto* c2 = reinterpret_cast<__nv_bfloat16*>(ws + L.c2);
     auto* wt = reinterpret_cast<__nv_bfloat16*>(ws + L.wt);
     float* y = reinterpret_cast<float*>(ws + L.y);
-    __nv_bfloat16* acf[3] = {reinterpret_cast<__nv_bfloat16*>(ws + L.a1), reinterpret_cast<__nv_bfloat16*>(ws + L.a2),
-                             reinterpret_cast<__nv_bfloat16*>(ws + L.a3)};
+    __nv_bfloat16* acf[3] = {keep_cf ? reinterpret_cast<__nv_bfloat16*>(ws + L.a1) : nullptr,
+                             keep_cf ? reinterpret_cast<__nv_bfloat16*>(ws + L.a2) : nullptr,
+                             keep_cf ? reinterpret_cast<__nv_bfloat16*>(ws + L.a3) : nullptr};
     const __nv_bfloat16* ins[4] = {xc, c1, c2, xc};
     __nv_bfloat16* outs_cl[3] = {c1, c2, xc};
     const float* biases[4] = {model + kB0, model + kB1, model + kB2, model + kB3};
@@ -763,7 +764,7 @@ cudaError_t forward_tc(const float* model, const float* gamma_in, const float* s
 }  // namespace
 
 cudaError_t denoise_forward(const float* model, const float* gamma_in, int ha, int wa, int hb, int wb,
-                            uint8_t* ws, const DenoiseLayout& L, unsigned int* status,
+                            uint8_t* ws, const DenoiseLayout& L, bool keep_cf, unsigned int* status,
                             unsigned long long timeout_ns, cudaStream_t st) {
     const int B = hb * wb;
     const int64_t HW = (int64_t)ha * wa, n = (int64_t)B * HW;
@@ -778,7 +779,7 @@ cudaError_t denoise_forward(const float* model, const float* gamma_in, int ha, i
     dn_scale_kernel<<<1, 32, 0, st>>>(sums, kSumBlocks, n, scale);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    if (L.tc) return forward_tc(model, gamma_in, scale, ha, wa, hb, wb, ws, L, status, timeout_ns, st);
+    if (L.tc) return forward_tc(model, gamma_in, scale, ha, wa, hb, wb, ws, L, keep_cf, status, timeout_ns, st);
     dn_stack_kernel<<<dim3((unsigned)((HW + 255) / 256 < 64 ? (HW + 255) / 256 : 64), 9, (unsigned)B), 256, 0, st>>>(
         gamma_in, scale, hb, wb, HW, x0);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

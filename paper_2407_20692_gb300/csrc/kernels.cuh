@@ -162,10 +162,11 @@ struct DenoiseLayout {                    // byte offsets in the workspace
 bool make_bf16_map_sw64(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
                         const uint32_t* box);
 DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training);
-// scale, stacked input, activations and y of the network on gamma_in (status,
+// scale, stacked input, activations and y of the network on gamma_in (keep_cf:
+// also the channels-first activations the backward pass reads; status,
 // timeout_ns: the bounded waits of the tensor-core layers)
 cudaError_t denoise_forward(const float* model, const float* gamma_in, int ha, int wa, int hb, int wb,
-                            uint8_t* ws, const DenoiseLayout& L, unsigned int* status,
+                            uint8_t* ws, const DenoiseLayout& L, bool keep_cf, unsigned int* status,
                             unsigned long long timeout_ns, cudaStream_t st);
 cudaError_t denoise_output(const uint8_t* ws, const DenoiseLayout& L, int64_t n, float* gamma_out,
                            cudaStream_t st);
