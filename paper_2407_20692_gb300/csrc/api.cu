@@ -513,60 +513,51 @@ cpi_status launch_batch_moments(const cpi_batch_item* items, const BatchPlan& bp
     return CPI_OK;
 }
 
-// The batch's refocusings are spread over kRefocusForks side streams (parallel
-// branches when captured into a graph), longest first, each to the branch with
-// the least work so far, so that one item's tail overlaps the others' work.
-constexpr int kRefocusForks = 4;
+// Independent per-item work of a batch is spread over kForks side streams
+// (parallel branches when captured into a graph), longest first, each item to
+// the branch with the least work so far, so that small launches overlap and one
+// item's tail overlaps the others' work.  Every branch joins the caller's stream
+// before the call returns.
+constexpr int kForks = 4;
 struct ForkStreams {
     std::mutex mu;
     bool ready[kMaxDevices] = {};
-    cudaStream_t side[kMaxDevices][kRefocusForks] = {};
+    cudaStream_t side[kMaxDevices][kForks] = {};
     cudaEvent_t fork[kMaxDevices] = {};
-    cudaEvent_t join[kMaxDevices][kRefocusForks] = {};
+    cudaEvent_t join[kMaxDevices][kForks] = {};
 };
 ForkStreams g_forks;
 
-cpi_status run_batch_refocus(const cpi_batch_item* items, const BatchPlan& bp, uint8_t* ws, cudaStream_t st) {
-    std::vector<int> rf;
-    for (int i = 0; i < (int)bp.it.size(); ++i)
-        if (items[i].n_planes > 0) rf.push_back(i);
-    auto one = [&](int i, cudaStream_t s) {
-        const cpi_batch_item& b = items[i];
-        return run_refocus(b.gamma_f32, b.a.height, b.a.width, b.b.height, b.b.width, b.planes, b.n_planes,
-                           b.refocus_out, ws + bp.it[i].rws_off, bp.it[i].rws_bytes, s);
-    };
-    if (rf.size() < 2) return rf.empty() ? CPI_OK : one(rf[0], st);
+template <class Cost, class One>
+cpi_status run_forked(std::vector<int> idx, Cost cost, One one, cudaStream_t st) {
+    if (idx.size() < 2) return idx.empty() ? CPI_OK : one(idx[0], st);
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CPI_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_forks.mu);
     if (!g_forks.ready[dev]) {
         if (cudaEventCreateWithFlags(&g_forks.fork[dev], cudaEventDisableTiming) != cudaSuccess) return CPI_ERR_CUDA;
-        for (int k = 0; k < kRefocusForks; ++k)
+        for (int k = 0; k < kForks; ++k)
             if (cudaStreamCreateWithFlags(&g_forks.side[dev][k], cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&g_forks.join[dev][k], cudaEventDisableTiming) != cudaSuccess)
                 return CPI_ERR_CUDA;
         g_forks.ready[dev] = true;
     }
-    auto cost = [&](int i) {
-        const cpi_batch_item& b = items[i];
-        return (double)b.n_planes * b.a.height * b.a.width * b.b.height * b.b.width;
-    };
-    std::stable_sort(rf.begin(), rf.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost(x) > cost(y); });
     if (cudaEventRecord(g_forks.fork[dev], st) != cudaSuccess) return CPI_ERR_CUDA;
-    for (int k = 0; k < kRefocusForks; ++k)
+    for (int k = 0; k < kForks; ++k)
         if (cudaStreamWaitEvent(g_forks.side[dev][k], g_forks.fork[dev], 0) != cudaSuccess) return CPI_ERR_CUDA;
-    double load[kRefocusForks] = {};
+    double load[kForks] = {};
     cpi_status result = CPI_OK;
-    for (int i : rf) {
+    for (int i : idx) {
         int k = 0;
-        for (int q = 1; q < kRefocusForks; ++q)
+        for (int q = 1; q < kForks; ++q)
             if (load[q] < load[k]) k = q;
         load[k] += cost(i);
         result = one(i, g_forks.side[dev][k]);
         if (result != CPI_OK) break;
     }
     // join every branch, also after an error (a capture must not end with a branch open)
-    for (int k = 0; k < kRefocusForks; ++k)
+    for (int k = 0; k < kForks; ++k)
         if (cudaEventRecord(g_forks.join[dev][k], g_forks.side[dev][k]) != cudaSuccess ||
             cudaStreamWaitEvent(st, g_forks.join[dev][k], 0) != cudaSuccess)
             result = CPI_ERR_CUDA;
@@ -576,21 +567,36 @@ cpi_status run_batch_refocus(const cpi_batch_item* items, const BatchPlan& bp, u
 cpi_status run_batch(const cpi_batch_item* items, const BatchPlan& bp, uint8_t* ws, DeviceInfo* dev,
                      cudaStream_t st) {
     const int n = (int)bp.it.size();
-    for (int i = 0; i < n; ++i) {
-        const cpi_batch_item& b = items[i];
-        cpi_status s = run_stage(CPI_STAGE_INGEST, bp.it[i].pl, &b.a, &b.b, 0, b.s_ab, b.s_a, b.s_b,
-                                 b.gamma, b.gamma_f32, ws + bp.it[i].ws_off, dev, st);
-        if (s != CPI_OK) return s;
-    }
-    cpi_status s = launch_batch_moments(items, bp, ws, dev, st);
+    std::vector<int> all(n);
+    for (int i = 0; i < n; ++i) all[i] = i;
+    // ingest of every item (forked), the grouped raw-moment launches, then per
+    // item its fold and refocusing (forked)
+    cpi_status s = run_forked(
+        all, [&](int i) { return (double)(bp.it[i].pl.Ma + bp.it[i].pl.Mb) * (double)bp.it[i].pl.n; },
+        [&](int i, cudaStream_t cs) {
+            const cpi_batch_item& b = items[i];
+            return run_stage(CPI_STAGE_INGEST, bp.it[i].pl, &b.a, &b.b, 0, b.s_ab, b.s_a, b.s_b, b.gamma,
+                             b.gamma_f32, ws + bp.it[i].ws_off, dev, cs);
+        },
+        st);
     if (s != CPI_OK) return s;
-    for (int i = 0; i < n; ++i) {
-        const cpi_batch_item& b = items[i];
-        s = run_stage(CPI_STAGE_FOLD, bp.it[i].pl, &b.a, &b.b, 0, b.s_ab, b.s_a, b.s_b, b.gamma,
-                      b.gamma_f32, ws + bp.it[i].ws_off, dev, st);
-        if (s != CPI_OK) return s;
-    }
-    return run_batch_refocus(items, bp, ws, st);
+    s = launch_batch_moments(items, bp, ws, dev, st);
+    if (s != CPI_OK) return s;
+    return run_forked(
+        all,
+        [&](int i) {
+            const cpi_batch_item& b = items[i];
+            return (double)bp.it[i].pl.Ma * (double)bp.it[i].pl.Mb * (6.0 + (double)b.n_planes);
+        },
+        [&](int i, cudaStream_t cs) {
+            const cpi_batch_item& b = items[i];
+            cpi_status r = run_stage(CPI_STAGE_FOLD, bp.it[i].pl, &b.a, &b.b, 0, b.s_ab, b.s_a, b.s_b, b.gamma,
+                                     b.gamma_f32, ws + bp.it[i].ws_off, dev, cs);
+            if (r != CPI_OK || b.n_planes == 0) return r;
+            return run_refocus(b.gamma_f32, b.a.height, b.a.width, b.b.height, b.b.width, b.planes, b.n_planes,
+                               b.refocus_out, ws + bp.it[i].rws_off, bp.it[i].rws_bytes, cs);
+        },
+        st);
 }
 
 uint64_t fnv(uint64_t h, const void* p, size_t n) {
