@@ -313,11 +313,7 @@ def run_native(args, world, rank, local):
                   "u8 -> bf16 tensor-core (exact fp32 partials folded every 256 frames), int64 sums, "
                   "f64 Gamma, f32 refocus"),
         "data": "synthetic (seeded chaotic-light source model; stand-in for the SwissSPAD2 dataset)",
-        "config": {"workload": f"{args.workload}: spatial {ha}x{wa} vs angular {hb}x{wb}, "
-                               f"{'binary bit-packed' if acq.bits == 1 else 'uint8'} frames side by side, "
-                               f"N={n}, {n_planes} refocus planes",
-                   "M_a": ma, "M_b": mb, "N": n, "planes": n_planes,
-                   "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) between steps"},
+        "config": single_config(args.workload, acq, ha, wa, hb, wb, n_planes, world),
         "parts_ms": {"ingest": ingest_ms, "moments": moments_ms, "fold": fold_ms, "refocus": refocus_ms},
         "gamma_tops": ops / ((ingest_ms + moments_ms + fold_ms) / 1e3) / 1e12,
         "refocus_planes_per_s": n_planes / (refocus_ms / 1e3),
@@ -365,6 +361,15 @@ def _traffic(kernel_key, workload):
     if h.hexdigest() != ent["sha256"]:
         return None
     return ent["dram_bytes_per_launch"]
+
+
+def single_config(workload, acq, ha, wa, hb, wb, n_planes, world):
+    """The `config` object of a single-acquisition workload (both arms print it)."""
+    return {"workload": f"{workload}: spatial {ha}x{wa} vs angular {hb}x{wb}, "
+                        f"{'binary bit-packed' if acq.bits == 1 else 'uint8'} frames side by side, "
+                        f"N={acq.n_frames}, {n_planes} refocus planes",
+            "M_a": ha * wa, "M_b": hb * wb, "N": acq.n_frames, "planes": n_planes,
+            "parallelism": f"replicas x{world}", "l2": "flushed (512 MiB write) between steps"}
 
 
 def rooflines(ma, mb, n, n_planes, bits, ms, workload):
@@ -1053,7 +1058,8 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8/int64/f64 (CPU oracle)",
         "data": "synthetic (seeded chaotic-light source model)",
-        "config": {"workload": args.workload, "M_a": ma, "M_b": mb, "N": acq.n_frames, "planes": n_planes},
+        "config": single_config(args.workload, acq, lay["a"]["height"], lay["a"]["width"], lay["b"]["height"],
+                                lay["b"]["width"], n_planes, world),
         "cpu_baseline": {"value": value, "unit": "TOPS (int8-equivalent)", "cores": cores,
                          "kind": "oracle", "sample": desc},
         "e2e": {"value": value, "unit": "TOPS (int8-equivalent)", "h2d_bytes_per_step": 0,
