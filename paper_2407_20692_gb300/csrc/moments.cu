@@ -50,7 +50,6 @@ struct MomentsCfg {
     static constexpr int kStages = kBN == 256 ? 4 : 6;
     static constexpr int kElem = kBf16 ? 2 : 1;
     static constexpr int kKPerBlock = kRowBytes / kElem;     // 64 / 128 elements
-    static constexpr int kMmaK = 32 / kElem;                  // 16 / 32 elements per MMA
     static constexpr int kABytes = kBlockM * kRowBytes;       // 16 KiB
     static constexpr int kBBytes = kBlockN * kRowBytes;       // 32 KiB
     // tensor memory (2 x kBN columns): two FP32 accumulators, so the epilogue of

@@ -89,15 +89,6 @@ __device__ __forceinline__ void kahan_add(float& acc, float& cmp, float v) {
     acc = t;
 }
 
-__device__ __forceinline__ void named_bar_sync(int id, int n) {
-    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
 __device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* m, uint64_t* bar, int32_t x) {
     asm volatile(
         "cp.async.bulk.tensor.1d.shared::cluster.global.mbarrier::complete_tx::bytes"
@@ -615,12 +606,6 @@ size_t pipe_smem(int ha, int wa, int wb, const PipeCfg& c) {
 }
 
 int rows_per_thread(int ha, int wa) { return wa <= kThreads ? row_split(ha, wa).NK : 1 << 30; }
-
-int pow2_at_least(int v, int lo) {
-    int k = lo;
-    while (k < v) k *= 2;
-    return k;
-}
 
 template <int KR, int PB, int NSTEP, int kST, bool kPad, bool kTable, int kWA = 0, int kHA = 0>
 cudaError_t launch_pipe(const CUtensorMap* tm, const RefocusGeom& geo, const PlaneBlock& pl, float* partial,
