@@ -63,3 +63,40 @@ def test_workspace_query_host_logic():
     assert cpi.cpi_correlate_workspace_size(outside, b8, 10) == 0
     assert cpi.cpi_refocus_workspace_size(64, 64, 32, 32, 32) > 0
     assert cpi.cpi_refocus_workspace_size(0, 64, 32, 32, 32) == 0
+
+
+def test_refocus_workspace_holds_a_row_padded_copy_for_unaligned_widths():
+    """Widths that are not a multiple of 4 stage from a copy of Gamma with rows
+    padded to a multiple of 4 floats, kept after the partial images."""
+    for ha, wa, hb, wb, P in [(33, 70, 7, 5, 7), (46, 95, 4, 4, 3), (17, 33, 5, 3, 2)]:
+        wa4 = (wa + 3) // 4 * 4
+        ws = cpi.cpi_refocus_workspace_size(ha, wa, hb, wb, P)
+        # one partial image per angular row and plane, then the padded copy
+        partial = -(-hb * P * ha * wa * 4 // 256) * 256
+        assert ws == partial + -(-hb * wb * ha * wa4 * 4 // 256) * 256, (ha, wa)
+    # aligned widths need no copy
+    assert cpi.cpi_refocus_workspace_size(64, 64, 32, 32, 32) == 32 * 32 * 64 * 64 * 4
+
+
+def test_denoise_workspace_has_channels_last_buffers_for_tensor_core_widths():
+    """Inference layout: scale, sums, x (9 channels), a1..a3 (32 channels, bf16),
+    y (float), each rounded up to 256 bytes; widths 32, 64 and 128 (the
+    tensor-core layers) add three channels-last copies of 64 bytes per pixel and
+    the bf16 weights of the four layers."""
+    up = lambda n: -(-n // 256) * 256
+    for ha, wa, hb, wb in [(16, 32, 4, 4), (8, 64, 2, 3), (5, 128, 2, 2), (16, 40, 4, 4), (12, 20, 3, 4)]:
+        B, HW = hb * wb, ha * wa
+        want = up(4) + up(8 * 256) + up(2 * B * 9 * HW) + 3 * up(2 * B * 32 * HW) + up(4 * B * HW)
+        if wa in (32, 64, 128):
+            want += 3 * up(64 * B * HW) + up(2 * (3 * 9 * 32 * 32 + 9 * 16 * 32))
+        assert cpi.cpi_denoise_workspace_size(ha, wa, hb, wb) == want, (ha, wa, hb, wb)
+
+
+def test_refocus4d_workspace_chunks_planes():
+    """Up to 64 planes per chunk, fewer when a chunk's column sums would pass 4 GB."""
+    small = cpi.cpi_refocus4d_workspace_size(16, 16, 8, 8, 10)
+    more = cpi.cpi_refocus4d_workspace_size(16, 16, 8, 8, 500)
+    assert 0 < small < more
+    assert more == cpi.cpi_refocus4d_workspace_size(16, 16, 8, 8, 64)   # one 64-plane chunk is reused
+    big = cpi.cpi_refocus4d_workspace_size(256, 256, 256, 256, 100)
+    assert big <= (4 << 30) + (1 << 24)
