@@ -100,8 +100,10 @@ CPI_API int32_t cpi_abi_version(void);
  * inside the correlation path.)
  *
  * Shapes: M_a = a->height * a->width, M_b = b->height * b->width.
- *   s_ab  : int64 [M_a][M_b] row-major (required)
- *   s_a   : int64 [M_a] (required),  s_b : int64 [M_b] (required)
+ *   s_ab  : int64 [M_a][M_b] row-major; may be NULL (not written) when gamma or
+ *           gamma_f32 is given, except for accumulating calls
+ *   s_a   : int64 [M_a],  s_b : int64 [M_b]; may be NULL (then kept in the
+ *           workspace), except for accumulating calls
  *   gamma : double [M_a][M_b] row-major, or NULL to skip
  *   gamma_f32 : float [M_b][M_a] ("slice-major": one M_a image per angular
  *           pixel, the input layout of cpi_refocus), or NULL to skip

@@ -187,7 +187,7 @@ struct CorrPlan {
     int64_t kstride_bytes;     // operand row length in bytes (frames padded to the ingest tile)
     int k_blocks, kb_per_chunk, n_chunks;
     int block_n, tiles_m, tiles_n, n_units;
-    size_t off_a, off_b, off_part, off_vmax, ws_bytes;
+    size_t off_a, off_b, off_part, off_vmax, off_sa, off_sb, ws_bytes;   // off_sa/off_sb: S_a, S_b when the caller passes none
 };
 
 // split == 0: single correlation (more frame chunks when the tiles alone cannot
@@ -241,7 +241,9 @@ cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm
     p.off_b = round_up(p.off_a + (size_t)p.Ma * (size_t)p.kstride_bytes, 1024);
     p.off_part = round_up(p.off_b + (size_t)p.Mb * (size_t)p.kstride_bytes, 1024);
     p.off_vmax = round_up(p.off_part + (size_t)p.n_chunks * (size_t)p.Ma * (size_t)p.Mb * 4, 256);
-    p.ws_bytes = round_up(p.off_vmax + 2 * sizeof(uint32_t), 1024);
+    p.off_sa = round_up(p.off_vmax + 2 * sizeof(uint32_t), 256);
+    p.off_sb = round_up(p.off_sa + (size_t)p.Ma * 8, 256);
+    p.ws_bytes = round_up(p.off_sb + (size_t)p.Mb * 8, 1024);
     *pl = p;
     return CPI_OK;
 }
@@ -272,6 +274,8 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
     uint8_t* op_b = w + pl.off_b;
     int32_t* part = reinterpret_cast<int32_t*>(w + pl.off_part);
     uint32_t* vmax = reinterpret_cast<uint32_t*>(w + pl.off_vmax);
+    if (s_a == nullptr) s_a = reinterpret_cast<int64_t*>(w + pl.off_sa);
+    if (s_b == nullptr) s_b = reinterpret_cast<int64_t*>(w + pl.off_sb);
     if (stage == CPI_STAGE_INGEST) {
         if (!accumulate) {
             cudaError_t e = cudaMemsetAsync(s_a, 0, (size_t)pl.Ma * 8, st);
@@ -299,8 +303,8 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
         return cuda_status(launch_moments(pl.bf16, pl.block_n, L, dev->sm_count, st));
     }
     if (stage == CPI_STAGE_FOLD) {
-        return cuda_status(launch_fold(part, pl.n_chunks, pl.Ma, pl.Mb, s_ab, accumulate, 1, s_a,
-                                       s_b, pl.n, gamma, gamma_f32, st));
+        return cuda_status(launch_fold(part, pl.n_chunks, pl.Ma, pl.Mb, s_ab, accumulate, s_ab != nullptr ? 1 : 0,
+                                       s_a, s_b, pl.n, gamma, gamma_f32, st));
     }
     return CPI_ERR_INVALID_ARG;
 }
@@ -314,7 +318,11 @@ cpi_status correlate_common(const int32_t* stages, int n_stages, const cpi_frame
     CorrPlan pl;
     cpi_status s = make_plan(a, b, n_frames, dev->sm_count, &pl);
     if (s != CPI_OK) return s;
-    if (!s_ab || !s_a || !s_b || !aligned(s_ab, 16) || !aligned(s_a, 16) || !aligned(s_b, 16))
+    // accumulating calls need the caller's sums; otherwise S_a, S_b may live in
+    // the workspace and S_ab may be skipped when a Gamma output is asked for
+    if (accumulate && (!s_ab || !s_a || !s_b)) return CPI_ERR_INVALID_ARG;
+    if (!s_ab && !gamma && !gamma_f32) return CPI_ERR_INVALID_ARG;
+    if ((s_ab && !aligned(s_ab, 16)) || (s_a && !aligned(s_a, 16)) || (s_b && !aligned(s_b, 16)))
         return CPI_ERR_INVALID_ARG;
     if ((gamma && !aligned(gamma, 16)) || (gamma_f32 && !aligned(gamma_f32, 16)))
         return CPI_ERR_INVALID_ARG;

@@ -299,3 +299,29 @@ def test_bit_regions_spanning_several_word_chunks(bit_order):
     got = gpu_correlate(fr, la, lb, n)
     want = oracle_correlate(fr.cpu().numpy(), la, lb, n)
     assert_exact(got, want)
+
+
+@pytest.mark.parametrize("counts", ["bernoulli", "poisson8"])
+def test_sums_may_stay_in_the_workspace(counts):
+    """Without caller buffers for S_ab, S_a, S_b the marginals live in the
+    workspace and S_ab is not written; Gamma (both layouts) is bit-identical to
+    the call that returns every sum.  Accumulating calls still need the sums."""
+    acq = synth.Acquisition(24, 12, 2500, 2.0 if counts == "poisson8" else 0.4, counts, seed=41)
+    fr, lay = make_frames(acq)
+    full = gpu_correlate(fr, lay["a"], lay["b"], 2500)
+    a, b = desc(fr, lay["a"]), desc(fr, lay["b"])
+    ma, mb = 24 * 24, 12 * 12
+    ws = torch.empty(cpi.cpi_correlate_workspace_size(a, b, 2500), dtype=torch.uint8, device="cuda")
+    g = torch.empty((ma, mb), dtype=torch.float64, device="cuda")
+    g32 = torch.empty((mb, ma), dtype=torch.float32, device="cuda")
+    cpi.cpi_correlate(a, b, 2500, None, None, None, g, g32, ws)
+    torch.cuda.synchronize()
+    assert torch.equal(g.cpu(), full["gamma"])
+    assert torch.equal(g32, full["gamma_f32"])
+    with pytest.raises(cpi.CpiError) as e:      # nothing to return
+        cpi.cpi_correlate(a, b, 2500, None, None, None, None, None, ws)
+    assert e.value.code == 1
+    s = torch.zeros((ma, mb), dtype=torch.int64, device="cuda")
+    with pytest.raises(cpi.CpiError) as e:      # accumulating into missing sums
+        cpi.cpi_correlate_accumulate(a, b, 2500, s, None, None, ws)
+    assert e.value.code == 1
