@@ -147,7 +147,7 @@ cudaError_t launch_refocus4d_chunk(const float* gamma_f32, int ha, int wa, int h
 
 // ------------------------------------------------------------------ denoiser
 constexpr int kDenoiserParams = 21409;    // model blob floats
-constexpr int kDenoiseParts = 256;        // CTAs of a weight-gradient pass (fixed-order partials)
+constexpr int kDenoiseParts = 456;        // CTAs of a weight-gradient pass (fixed-order partials; 3 x 152 SMs)
 struct DenoiseLayout {                    // byte offsets in the workspace
     size_t scale, sums, x0, a1, a2, a3, y, dy, d_hi, d_lo, part;
     // tensor-core forward (widths 32, 64, 128): channels-last copies of x (padded
