@@ -192,6 +192,7 @@ struct CorrPlan {
 
 // split == 0: single correlation (more frame chunks when the tiles alone cannot
 // fill the GPU); split >= 1: member of a batch, split x the minimum chunk count.
+// block_n: output tile width (256; batches may choose 128).
 cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm_count,
                      CorrPlan* pl, int split = 0, int block_n = 256) {
     cpi_status s = check_frames(a);
@@ -417,10 +418,10 @@ cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
 // ------------------------------------------------------------------ batches
 // A batch of independent correlations (and refocusings): every item gets its
 // own region of the workspace; the items' ingest, fold and refocus kernels are
-// launched per item, and the raw-moment units of all items of one operand kind
-// run in persistent grouped launches of up to kMaxGroup problems, larger units
-// first.  The whole sequence can be captured once into a CUDA graph and
-// replayed.
+// launched per item on forked streams, and the raw-moment units of all items of
+// one operand kind run in persistent grouped launches of up to kMaxGroup
+// problems, larger units first.  The whole sequence can be captured once into a
+// CUDA graph and replayed.
 struct BatchItemPlan {
     CorrPlan pl;
     size_t ws_off = 0, rws_off = 0, rws_bytes = 0;
