@@ -25,9 +25,7 @@
 // (Kahan-compensated) by a second kernel, so the result is deterministic.
 //
 // Layout: Gamma arrives slice-major, float [Mb][Ma]; slice b is one contiguous
-// spatial image.  It is staged into shared memory by 1-D TMA boxes of 256
-// elements, starting at the 16-byte boundary at or below the slice (the slice
-// then sits 0-3 elements into the buffer).
+// spatial image, staged into shared memory by TMA (see the pipelined kernel).
 //
 // This file is compiled without FMA contraction: the Kahan steps depend on the
 // written rounding order; the products use explicit fmaf.
@@ -108,20 +106,22 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const CUtensorMap* m, uin
 // buffers, one TMA copy (group) each, completion counted on full[stage].  The
 // last warp to finish with a buffer (a shared counter per stage) issues the copy
 // of the slice kStages further on into it, so no thread ever waits for a free
-// buffer.  Staging: a 2-D box of (wa4 + 8) x ha from column -4, wa4 = wa
+// buffer.  Staging: a 2-D box of (wa4 + 8) x R*NK rows from column -4, wa4 = wa
 // rounded up to a multiple of 4 (columns outside 0 .. wa-1 come back as zeros:
-// the out-of-grid taps), when wa4 + 8 <= 256 and ha <= 256.  A Gamma whose rows
-// are not 16-byte multiples is first copied with its rows padded to wa4 floats
-// (refocus_repack_kernel).  Wider slices: 1-D boxes of 256 elements from the
-// 16-byte boundary at or below the slice.
+// the out-of-grid taps), when wa4 + 8 <= 256 and R*NK <= 256; rows past the
+// slice's ha are the next slice's (or zeros past Gamma's end).  A Gamma whose
+// rows are not 16-byte multiples is first copied with its rows padded to wa4
+// floats (refocus_repack_kernel).  Wider slices: 1-D boxes of 256 elements from
+// the 16-byte boundary at or below the slice (which then sits 0-3 elements in).
 //
-// Thread t owns column c = t % wa and rows rp + R*k (R = kThreads / wa).  For
-// each staged slice and each plane of the unit it reads its x taps (from a
-// per-plane-block table when it fits in shared memory, else computes them),
-// adds NSTEP slices with fused multiply-adds and Kahan-adds the step's sum into
-// its U values.  After the unit's last slice each plane's U image in turn goes
-// to shared memory and is interpolated along y; this angular row's contribution
-// to each output pixel is written to partial[br][plane][pixel].
+// Thread t owns column c = t % wa and rows rp + R*k, k < NK (row_split below).
+// For each step of NSTEP staged slices it reads the x taps of a group of 2 or 4
+// planes (from a per-plane-block table when it fits in shared memory, else
+// computes them), then, rows outer and planes inner, adds the step's slices with
+// fused multiply-adds and Kahan-adds the sum into its U values.  After the
+// unit's last slice each plane's U image in turn goes to shared memory and is
+// interpolated along y; this angular row's contribution to each output pixel is
+// written to partial[br][plane][pixel].
 //
 // Every wait is bounded (the device status word records a time out).  A slice
 // that never arrives stops every thread at that same slice, so no barrier is
