@@ -16,12 +16,14 @@
 // master weights are float32.  Training minimises mean((y - s Gamma_target)^2)
 // with Adam.
 //
-// Kernels are direct convolutions on the FP32 pipe: a CTA computes a tile of
-// 8 x 32 output pixels of one slice for every output channel, each thread two
-// pixels (rows r and r + 4 of its column) times all output channels, the input
-// tile (with its 1-pixel halo) and the bf16-rounded weights staged in shared
-// memory ([Cin][tap][Cout], so the output channels of one tap are read as
-// broadcast vectors).  Weight gradients are summed per CTA over a fixed range
+// The forward network runs on the tensor cores for image widths 32, 64 and 128
+// (dn_conv_tc_kernel: implicit GEMMs over channels-last activations, below).
+// Other widths and the backward pass use direct convolutions on the FP32 pipe:
+// a CTA computes a tile of 8 x 32 output pixels of one slice for every output
+// channel, each thread two pixels (rows r and r + 4 of its column) times all
+// output channels, the input tile (with its 1-pixel halo) and the bf16-rounded
+// weights staged in shared memory ([Cin][tap][Cout], so the output channels of
+// one tap are read as broadcast vectors).  Weight gradients are summed per CTA over a fixed range
 // of slices and the per-CTA partials added in a fixed order, so every result is
 // deterministic.
 #include <cuda_bf16.h>
