@@ -23,9 +23,9 @@
 // channel, each thread two pixels (rows r and r + 4 of its column) times all
 // output channels, the input tile (with its 1-pixel halo) and the bf16-rounded
 // weights staged in shared memory ([Cin][tap][Cout], so the output channels of
-// one tap are read as broadcast vectors).  Weight gradients are summed per CTA over a fixed range
-// of slices and the per-CTA partials added in a fixed order, so every result is
-// deterministic.
+// one tap are read as broadcast vectors).  Weight gradients are summed per CTA
+// over a fixed range of slices and the per-CTA partials added in a fixed order,
+// so every result is deterministic.
 #include <cuda_bf16.h>
 
 #include "kernels.cuh"
