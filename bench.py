@@ -591,7 +591,7 @@ def run_denoise(args, world, rank):
     torch.cuda.synchronize()
     t_data = time.time() - t0
     # ---------------------------------------------------------------- training
-    model = torch.tensor(cpi.denoiser_init(seed0), device=dev)
+    model = torch.tensor(synth.denoiser_init(seed0), device=dev)
     m = torch.zeros_like(model)
     v = torch.zeros_like(model)
     grad = torch.empty_like(model)

@@ -122,18 +122,21 @@ CPI_API cpi_status cpi_correlate(const cpi_frames *a, const cpi_frames *b, int64
                          cpi_stream stream);
 
 /* Streaming form (the paper processes the acquisition in blocks of files):
- * ADDS this block's sums into s_ab, s_a, s_b.  Call cpi_correlate_finalize with
- * the total frame count once every block has been added.  The running sums are
- * the complete state of a correlation, so saving them checkpoints it. */
+ * ADDS this block's sums into s_ab, s_a, s_b (all three required).  Call
+ * cpi_correlate_finalize with the total frame count once every block has been
+ * added.  The running sums are the complete state of a correlation, so saving
+ * them checkpoints it. */
 CPI_API cpi_status cpi_correlate_accumulate(const cpi_frames *a, const cpi_frames *b, int64_t n_frames,
                                     int64_t *s_ab, int64_t *s_a, int64_t *s_b, void *workspace,
                                     size_t workspace_bytes, cpi_stream stream);
 
-/* Gamma from accumulated sums: n_total frames in all (1 <= n_total < 2^31);
- * m_a x m_b entries.  The caller guarantees that n_total * s_ab and s_a * s_b
- * fit in int64 (true for sums produced by this library, which checks
- * N^2 max(A) max(B) < 2^63).  gamma and/or gamma_f32 (layouts as above) may be
- * NULL, not both. */
+/* Gamma from accumulated sums: n_total frames in all (1 <= n_total < 2^31,
+ * else CPI_ERR_OVERFLOW); m_a x m_b entries; any int64 sums.  The numerator
+ * n_total * s_ab - s_a * s_b is formed exactly in 128 bits (sums added over many
+ * blocks can make the products leave int64 although each block passed the
+ * per-call check), rounded once to double and divided by RN(n_total^2):
+ * bit-identical to the exact-numerator formula whenever the numerator fits
+ * int64.  gamma and/or gamma_f32 (layouts as above) may be NULL, not both. */
 CPI_API cpi_status cpi_correlate_finalize(const int64_t *s_ab, const int64_t *s_a, const int64_t *s_b,
                                   int64_t m_a, int64_t m_b, int64_t n_total, double *gamma,
                                   float *gamma_f32, cpi_stream stream);
@@ -147,7 +150,9 @@ CPI_API cpi_status cpi_correlate_finalize(const int64_t *s_ab, const int64_t *s_
  *                      int32 partial sums per frame chunk (in the workspace);
  *   CPI_STAGE_FOLD   : partial sums -> s_ab (int64), then gamma / gamma_f32 if
  *                      non-NULL (with N = n_frames).
- * accumulate != 0 adds into s_ab, s_a, s_b instead of overwriting them. */
+ * accumulate != 0 adds into s_ab, s_a, s_b instead of overwriting them; such a
+ * call writes no Gamma (gamma and gamma_f32 must be NULL, else
+ * CPI_ERR_INVALID_ARG): use cpi_correlate_finalize with the total frame count. */
 enum { CPI_STAGE_INGEST = 1, CPI_STAGE_MOMENTS = 2, CPI_STAGE_FOLD = 3 };
 CPI_API cpi_status cpi_correlate_stage(int32_t stage, const cpi_frames *a, const cpi_frames *b,
                                int64_t n_frames, int32_t accumulate, int64_t *s_ab, int64_t *s_a,
@@ -259,7 +264,7 @@ CPI_API cpi_status cpi_batch_correlate(const cpi_batch_item *items, int32_t n_it
                                        size_t workspace_bytes, int32_t flags, cpi_stream stream);
 
 /* --------------------------------------------------------------------------
- * Eq. (1) without a caller workspace (the paper has no counterpart).
+ * Correlation without a caller workspace.
  *
  * For callers that cannot allocate device memory: a real-time acquisition loop
  * for which cudaMalloc's implicit device synchronisation and unbounded latency

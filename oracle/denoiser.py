@@ -60,19 +60,6 @@ def pack(params):
     return np.concatenate([np.concatenate([w.reshape(-1), b]) for w, b in params])
 
 
-def init_blob(seed: int):
-    """He-normal weights (std sqrt(2 / fan_in)), zero biases; the last layer
-    scaled by 0.1 so that the network starts close to the identity."""
-    rng = np.random.Generator(np.random.Philox(seed))
-    parts = []
-    for l, (ci, co) in enumerate(LAYERS):
-        w = rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (ci * 9))
-        if l == len(LAYERS) - 1:
-            w *= 0.1
-        parts += [w.reshape(-1), np.zeros(co)]
-    return np.concatenate(parts).astype(np.float32)
-
-
 def scale_of(gamma):
     """s = 1 / rms(Gamma), in float64, then float32 (the kernels use a float32 s)."""
     g = np.asarray(gamma, dtype=np.float64)

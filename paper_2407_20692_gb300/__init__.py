@@ -21,7 +21,7 @@ __all__ = [
     "CPI_STAGE_INGEST", "CPI_STAGE_MOMENTS", "CPI_STAGE_FOLD", "EXPORTED", "cpi_correlate_noalloc",
     "NOALLOC_SCRATCH_BYTES", "cpi_batch_item", "batch_items", "CPI_BATCH_GRAPH", "CPI_BATCH_TUNE", "CPI_BATCH_N128",
     "cpi_batch_workspace_size", "cpi_batch_correlate", "cpi_denoise_workspace_size", "cpi_denoise_grad",
-    "cpi_denoise_adam", "DENOISER_PARAMS", "denoiser_init", "cpi_plane4", "plane4_array",
+    "cpi_denoise_adam", "DENOISER_PARAMS", "cpi_plane4", "plane4_array",
     "cpi_refocus4d_workspace_size", "cpi_refocus4d",
 ]
 CPI_BATCH_GRAPH, CPI_BATCH_TUNE, CPI_BATCH_N128 = 1, 2, 4
@@ -253,25 +253,6 @@ def cpi_refocus(gamma_f32, ha, wa, hb, wb, planes, out, workspace, stream=None):
                               _stream(stream)), "cpi_refocus")
 
 
-def denoiser_init(seed: int):
-    """Initial model blob (numpy float32 [DENOISER_PARAMS], the layout of include/cpi.h):
-    He-normal weights (std sqrt(2 / fan_in)), zero biases, the last layer scaled by
-    0.1 so that the network starts close to the identity."""
-    import numpy as np
-
-    rng = np.random.Generator(np.random.Philox(int(seed)))
-    layers = [(9, 32), (32, 32), (32, 32), (32, 1)]
-    parts = []
-    for l, (ci, co) in enumerate(layers):
-        w = rng.standard_normal((co, ci, 3, 3)) * np.sqrt(2.0 / (ci * 9))
-        if l == len(layers) - 1:
-            w *= 0.1
-        parts += [w.reshape(-1), np.zeros(co)]
-    blob = np.concatenate(parts).astype(np.float32)
-    assert blob.size == DENOISER_PARAMS
-    return blob
-
-
 def cpi_denoise_workspace_size(ha, wa, hb, wb, training=False) -> int:
     return load().cpi_denoise_workspace_size(ha, wa, hb, wb, 1 if training else 0)
 
@@ -302,8 +283,8 @@ def cpi_set_wait_timeout_ns(ns: int) -> None:
 
 
 def cpi_correlate_noalloc(a, b, n_frames, s_ab, s_a, s_b, gamma, gamma_f32, stream=None):
-    """Eq. (1) using the library's built-in scratch instead of a caller workspace,
-    for callers that cannot allocate device memory (see include/cpi.h)."""
+    """Correlation using the library's built-in scratch instead of a caller
+    workspace, for callers that cannot allocate device memory (see include/cpi.h)."""
     _check(load().cpi_correlate_noalloc(ctypes.byref(a), ctypes.byref(b), n_frames, _ptr(s_ab),
                                         _ptr(s_a), _ptr(s_b), _ptr(gamma), _ptr(gamma_f32),
                                         _stream(stream)), "cpi_correlate_noalloc")

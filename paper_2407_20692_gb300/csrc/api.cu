@@ -322,6 +322,9 @@ cpi_status correlate_common(const int32_t* stages, int n_stages, const cpi_frame
     // accumulating calls need the caller's sums; otherwise S_a, S_b may live in
     // the workspace and S_ab may be skipped when a Gamma output is asked for
     if (accumulate && (!s_ab || !s_a || !s_b)) return CPI_ERR_INVALID_ARG;
+    // an accumulating call has no total frame count: Gamma comes from
+    // cpi_correlate_finalize once every block has been added
+    if (accumulate && (gamma || gamma_f32)) return CPI_ERR_INVALID_ARG;
     if (!s_ab && !gamma && !gamma_f32) return CPI_ERR_INVALID_ARG;
     if ((s_ab && !aligned(s_ab, 16)) || (s_a && !aligned(s_a, 16)) || (s_b && !aligned(s_b, 16)))
         return CPI_ERR_INVALID_ARG;
@@ -780,7 +783,7 @@ cpi_status cpi_correlate_finalize(const int64_t* s_ab, const int64_t* s_a, const
     if (n_total > ((int64_t)1 << 31) - 1) return CPI_ERR_OVERFLOW;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     return cuda_status(launch_fold(nullptr, 0, m_a, m_b, const_cast<int64_t*>(s_ab), 1, 0, s_a, s_b,
-                                   n_total, gamma, gamma_f32, st));
+                                   n_total, gamma, gamma_f32, st, 1));
 }
 
 size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb,

@@ -15,7 +15,9 @@
 // last bit exactly with 128-bit integer arithmetic: q = M * 2^E is the
 // correctly rounded A / D iff (2M - 1) D <= 2 A 2^-E <= (2M + 1) D, ties to even.
 // Numerators of 2^53 or more (possible only for very long acquisitions) take
-// the IEEE division.
+// the IEEE division.  Sums handed to cpi_correlate_finalize may come from many
+// accumulating calls, so there (wide != 0) the numerator is formed in 128 bits;
+// one that does not fit int64 is rounded once to double and divided the same way.
 //
 // The optional FP32 copy is written slice-major ([b][a]) for the refocusing
 // step, through a shared-memory transpose.
@@ -32,7 +34,8 @@ __global__ void __launch_bounds__(256) fold_kernel(const int32_t* __restrict__ p
                                                    int64_t* s_ab, int accumulate, int write_sab,
                                                    const int64_t* __restrict__ s_a,
                                                    const int64_t* __restrict__ s_b,
-                                                   const GammaDiv gd, double* gamma, float* gamma_f32) {
+                                                   const GammaDiv gd, int wide, double* gamma,
+                                                   float* gamma_f32) {
     __shared__ float tile[kTile][kTile + 1];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8
     const int64_t b = (int64_t)blockIdx.x * kTile + tx;
@@ -50,8 +53,9 @@ __global__ void __launch_bounds__(256) fold_kernel(const int32_t* __restrict__ p
                 for (int c = 0; c < n_chunks; ++c) s += (int64_t)__ldg(partial + (int64_t)c * plane + idx);
                 if (write_sab) s_ab[idx] = s;
                 if (want_g) {
-                    const int64_t num = gd.n * s - __ldg(s_a + a) * __ldg(s_b + b);
-                    const double g = gamma_from_num(num, gd);
+                    const int64_t sa = __ldg(s_a + a), sb = __ldg(s_b + b);
+                    const double g =
+                        wide ? gamma_from_sums_wide(s, sa, sb, gd) : gamma_from_num(gd.n * s - sa * sb, gd);
                     if (gamma) gamma[idx] = g;
                     tile[ty + 8 * k][tx] = double_to_float_rn(g);
                 }
@@ -76,12 +80,12 @@ __global__ void __launch_bounds__(256) fold_kernel(const int32_t* __restrict__ p
 cudaError_t launch_fold(const int32_t* partial, int n_chunks, int64_t M, int64_t N,
                         int64_t* s_ab, int accumulate, int write_sab, const int64_t* s_a,
                         const int64_t* s_b, int64_t n_frames, double* gamma, float* gamma_f32,
-                        cudaStream_t st) {
+                        cudaStream_t st, int wide) {
     const int64_t gx = (N + kTile - 1) / kTile, gy = (M + kTile - 1) / kTile;
     const unsigned gyl = (unsigned)(gy < 65535 ? gy : 65535);
     fold_kernel<<<dim3((unsigned)gx, gyl), 256, 0, st>>>(partial, n_chunks, M, N, s_ab, accumulate,
                                                          write_sab, s_a, s_b,
-                                                         make_gamma_div(n_frames), gamma, gamma_f32);
+                                                         make_gamma_div(n_frames), wide, gamma, gamma_f32);
     return cudaGetLastError();
 }
 

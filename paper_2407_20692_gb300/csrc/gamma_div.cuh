@@ -135,6 +135,42 @@ inline GammaDiv make_gamma_div(int64_t n_frames) {
     return g;
 }
 
+// Round-to-nearest-even double of a signed 128-bit integer (hi, lo), built from
+// its bits: the leading 53 bits, then the next bit and a sticky bit of the rest.
+__device__ __forceinline__ double i128_to_double_rn(int64_t hi, uint64_t lo) {
+    const bool neg = hi < 0;
+    uint64_t H = (uint64_t)hi, L = lo;
+    if (neg) {                                                   // |x|: two's complement negation
+        L = ~L + 1ull;
+        H = ~H + (L == 0 ? 1ull : 0ull);
+    }
+    if (H == 0 && L == 0) return 0.0;
+    int e;                                                      // position of the leading one
+    uint64_t top, rest;                                         // leading 64 bits from the one; bits below
+    if (H != 0) {
+        const int z = __clzll((long long)H);
+        e = 127 - z;
+        top = z == 0 ? H : (H << z) | (L >> (64 - z));
+        rest = z == 0 ? L : (L << z);
+    } else {
+        const int z = __clzll((long long)L);
+        e = 63 - z;
+        top = L << z;
+        rest = 0;
+    }
+    uint64_t m = top >> 11;                                     // 53 bits, leading one at bit 52
+    const uint64_t r = top & 0x7ffull;                          // the 11 bits below the mantissa
+    const bool sticky = (r & 0x3ffull) != 0 || rest != 0;
+    if ((r & 0x400ull) && (sticky || (m & 1ull))) {
+        if (++m == (1ull << 53)) {
+            m >>= 1;
+            ++e;
+        }
+    }
+    const uint64_t bits = ((uint64_t)(e + 1023) << 52) | (m & ((1ull << 52) - 1)) | (neg ? (1ull << 63) : 0ull);
+    return __longlong_as_double((long long)bits);
+}
+
 // Gamma from the exact numerator num = N S_ab - S_a S_b.
 __device__ __forceinline__ double gamma_from_num(int64_t num, const GammaDiv& gd) {
     if (num == 0) return 0.0;
@@ -146,6 +182,21 @@ __device__ __forceinline__ double gamma_from_num(int64_t num, const GammaDiv& gd
         return __longlong_as_double((long long)bits);
     }
     return __ddiv_rn(__ll2double_rn(num), gd.d);
+}
+
+// Gamma from arbitrary int64 sums (cpi_correlate_finalize: sums accumulated over
+// many calls, whose products may leave int64): num = N S_ab - S_a S_b formed
+// exactly in 128 bits.  A numerator that fits int64 takes gamma_from_num; a wider
+// one is rounded once to double and divided by RN(N * N), the same two
+// round-to-nearest operations as in the narrow case.
+__device__ __forceinline__ double gamma_from_sums_wide(int64_t s_ab, int64_t s_a, int64_t s_b, const GammaDiv& gd) {
+    const uint64_t lo1 = (uint64_t)gd.n * (uint64_t)s_ab, lo2 = (uint64_t)s_a * (uint64_t)s_b;
+    const int64_t hi1 = __mul64hi((long long)gd.n, (long long)s_ab);
+    const int64_t hi2 = __mul64hi((long long)s_a, (long long)s_b);
+    const uint64_t lo = lo1 - lo2;
+    const int64_t hi = hi1 - hi2 - (lo1 < lo2 ? 1 : 0);
+    if (hi == ((int64_t)lo >> 63)) return gamma_from_num((int64_t)lo, gd);
+    return __ddiv_rn(i128_to_double_rn(hi, lo), gd.d);
 }
 
 }  // namespace cpi

@@ -79,7 +79,9 @@ cudaError_t launch_moments_group(bool bf16, int block_n, const MomentsLaunch<kMa
 cudaError_t launch_fold(const int32_t* partial, int n_chunks, int64_t M, int64_t N,
                         int64_t* s_ab, int accumulate, int write_sab, const int64_t* s_a,
                         const int64_t* s_b, int64_t n_frames, double* gamma, float* gamma_f32,
-                        cudaStream_t st);
+                        cudaStream_t st, int wide = 0);
+// wide != 0: the numerator N S_ab - S_a S_b is formed in 128 bits (sums from
+// accumulating calls, which the per-call overflow check does not bound).
 
 // ------------------------------------------------------------------ refocus
 constexpr int kRefocusMaxPlanesPerLaunch = 128;

@@ -19,3 +19,4 @@ from .frames import (  # noqa: F401
     pack_side_by_side,
     uniform_planes,
 )
+from .model_init import DENOISER_PARAMS, denoiser_init  # noqa: F401,E402

@@ -233,6 +233,12 @@ def test_argument_errors_are_reported_before_launch():
     with pytest.raises(cpi.CpiError) as e:       # missing model and Gamma buffers
         cpi.cpi_denoise(None, None, None, 4, 4, 4, 4, ws)
     assert e.value.code == 1
+    g = torch.zeros((16, 16), dtype=torch.float64, device="cuda")
+    for stage in (cpi.CPI_STAGE_INGEST, cpi.CPI_STAGE_MOMENTS, cpi.CPI_STAGE_FOLD):
+        # an accumulating call has no total frame count: it must not write Gamma
+        with pytest.raises(cpi.CpiError) as e:
+            cpi.cpi_correlate_stage(stage, a, a, 16, 1, s, v, v, g, None, ws)
+        assert e.value.code == 1
 
 
 def test_wait_timeout_is_reported_and_context_survives():

@@ -14,6 +14,7 @@ import pytest
 import torch
 
 import paper_2407_20692_gb300 as cpi
+import synth
 from oracle import denoiser as dn
 
 pytestmark = pytest.mark.gpu
@@ -26,7 +27,7 @@ def _ready(cuda_ready):
 
 def _model(seed, noise=0.05):
     rng = np.random.default_rng(seed)
-    blob = dn.init_blob(seed).astype(np.float64) + noise * rng.standard_normal(dn.N_PARAMS)
+    blob = synth.denoiser_init(seed).astype(np.float64) + noise * rng.standard_normal(dn.N_PARAMS)
     return blob.astype(np.float32)
 
 
@@ -171,7 +172,7 @@ def test_training_steps_reduce_the_loss():
     rng = np.random.default_rng(9)
     clean = _gamma(10, hb, wb, ha, wa)
     noisy = (clean + 0.01 * rng.standard_normal(clean.shape)).astype(np.float32)
-    model = _dev(dn.init_blob(11))
+    model = _dev(synth.denoiser_init(11))
     m = torch.zeros_like(model)
     v = torch.zeros_like(model)
     ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb, training=True), dtype=torch.uint8,

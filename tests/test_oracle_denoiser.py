@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 import torch
 
+import synth
 from oracle import denoiser as dn
 
 
@@ -52,7 +53,7 @@ def test_stack_takes_the_3x3_angular_neighbourhood_with_zero_fill():
 def _tiny(seed):
     rng = np.random.default_rng(seed)
     hb, wb, ha, wa = 2, 3, 5, 4
-    blob = dn.init_blob(seed).astype(np.float64)
+    blob = synth.denoiser_init(seed).astype(np.float64)
     blob += 0.05 * rng.standard_normal(blob.size)      # non-zero biases, a non-trivial last layer
     x = rng.standard_normal((hb * wb, 9, ha, wa))
     t = rng.standard_normal((hb * wb, ha, wa))
