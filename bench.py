@@ -1,10 +1,13 @@
 """Benchmark of the CPI hot path on GB300.
 
 One step = one pass of the whole path over one acquisition of synthetic frames
-already resident in HBM: ingest (bit-unpack + transpose + marginal sums), the
-raw-moment tensor-core contraction, the int64 fold + FP64 Gamma of Eq. (1), and
-refocusing into P planes.  Default workload: 64x64 spatial vs 32x32 angular
-binary SPAD frames, N = 20000 bit-packed side by side, 32 refocusing planes.
+already resident in HBM: ingest (transpose + marginal sums; bit-unpack for
+binary frames), the raw-moment tensor-core contraction, the int64 fold + FP64
+Gamma of Eq. (1), and refocusing into P planes.  Default workload: 128x128
+spatial vs 64x64 angular uint8 counts (sums of 255 binary sub-frames),
+N = 50000 frames side by side, 128 refocusing planes; the line also carries the
+64x64 vs 32x32 binary workload, the batch of 64 uneven acquisitions and the
+denoiser's frames saved under "workloads".
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
@@ -12,7 +15,8 @@ Prints one JSON line (rank 0).  `value` is the whole-step throughput in
 int8-equivalent tera-operations per second, 2 * M_a * M_b * N / t_step, summed
 over ranks for N > 1 (independent replicas, one per GPU: the correlation of one
 acquisition needs no exchange between GPUs).  `--impl reference` times the CPU
-oracle (plain C, OpenMP) on a bounded sample of the same workload instead.
+oracle (plain C, OpenMP): the whole step, or for the default workload a
+proportional sample of it (see ORACLE_SAMPLE_IMAGE_ROWS).
 """
 
 from __future__ import annotations
@@ -155,56 +159,176 @@ def replica_throughput(world: int, work_per_rank: float, seconds: float):
     return world * work_per_rank / t_max / 1e12, t_max
 
 
-# ----------------------------------------------------------------------------- CPU oracle
+# ----------------------------------------------------------------------------- CPU oracle leg
+# Everything below that calls the oracle runs outside the GPU arm's timed region,
+# on rank 0 only: the CPU baseline (and the reference arm, which is the same
+# oracle step) and the error check of the GPU results against it.
 
-def oracle_sample(acq, planes, frames_host, lay, n_rows: int, n_planes: int):
-    """Time the oracle on a bounded sample and extrapolate one full step.
-    Returns (seconds per full step, cores, description)."""
+# Sample of one oracle step per workload: None = the whole step (Gamma of every
+# row, every plane); k = the Gamma rows of the first k rows of the spatial image
+# (k * W_a of the M_a rows) and the same fraction of the planes, so that the
+# sample holds the correlation and refocusing work of the step in proportion.
+ORACLE_SAMPLE_IMAGE_ROWS = {"small_u8": None, "spad_1bit": None, "large_u8": 1}
+
+
+def oracle_step(acq, planes, frames_host, lay, image_rows, gamma_refocus=None):
+    """One step (or its proportional sample) of the CPU oracle on the workload's
+    frames: Eq. (1) then refocusing.  Returns (seconds, ops of the sample,
+    description, oracle result of the correlation, refocused planes)."""
+    import oracle
+
+    oracle.build()
+    la, lb = lay["a"], lay["b"]
+    ha, wa, hb, wb = la["height"], la["width"], lb["height"], lb["width"]
+    alpha, beta = planes
+    P = len(alpha)
+    n = acq.n_frames
+    if image_rows is None:
+        t0 = time.perf_counter()
+        r = oracle.correlate(frames_host, la, frames_host, lb, n)
+        ref = oracle.refocus(r["gamma"], ha, wa, hb, wb, alpha, beta)
+        dt = time.perf_counter() - t0
+        return dt, 2.0 * ha * wa * hb * wb * n, "the whole step: Eq. (1) for every entry, every plane", r, ref
+    k = int(image_rows)
+    q = max(1, round(P * k / ha))
+    sub = dict(la, height=k)             # Gamma rows 0 .. k * wa - 1
+    if gamma_refocus is None:
+        gamma_refocus = synth_gamma(ha * wa, hb * wb)
+    t0 = time.perf_counter()
+    r = oracle.correlate(frames_host, sub, frames_host, lb, n)
+    ref = oracle.refocus(gamma_refocus, ha, wa, hb, wb, alpha[:q], beta[:q])
+    dt = time.perf_counter() - t0
+    desc = (f"Eq. (1) for the Gamma rows of spatial image row(s) 0..{k - 1} ({k * wa} of {ha * wa} rows, all "
+            f"{n} frames) and {q} of {P} planes (a seeded stand-in Gamma of the full shape): {k}/{ha} of "
+            f"the step's correlation and refocusing work")
+    return dt, 2.0 * k * wa * hb * wb * n, desc, r, ref
+
+
+def synth_gamma(ma, mb, seed=20692):
+    import synth
+
+    return synth.random_gamma(ma, mb, seed)
+
+
+def oracle_leg(workload, acq, planes, frames_host, lay, reps, cpi_refocus_fn, gpu_gamma_rows):
+    """The CPU baseline (`reps` oracle steps or samples) and the error of the GPU
+    results against the oracle: Gamma bit for bit on the rows the oracle computed
+    (with S_a, S_b in full), refocusing against FP64 on sampled planes."""
     import numpy as np
 
     import oracle
 
-    oracle.build()
-    ma = lay["a"]["height"] * lay["a"]["width"]
-    mb = lay["b"]["height"] * lay["b"]["width"]
-    n = acq.n_frames
-    t0 = time.perf_counter()
-    oracle.unpack(frames_host, lay["a"], n)
-    oracle.unpack(frames_host, lay["b"], n)
-    t_unpack = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    r = oracle.correlate(frames_host, lay["a"], frames_host, lay["b"], n, rows=(0, n_rows))
-    t_rows = time.perf_counter() - t0
-    per_row = max(t_rows - t_unpack, 1e-9) / n_rows
-    t_corr = t_unpack + per_row * ma
-    ha, wa = lay["a"]["height"], lay["a"]["width"]
-    hb, wb = lay["b"]["height"], lay["b"]["width"]
+    la, lb = lay["a"], lay["b"]
+    ha, wa, hb, wb = la["height"], la["width"], lb["height"], lb["width"]
+    ma, mb = ha * wa, hb * wb
     alpha, beta = planes
-    g = r["gamma"]
-    t0 = time.perf_counter()
-    oracle.refocus(g, ha, wa, hb, wb, alpha[:n_planes], beta[:n_planes])
-    t_ref = (time.perf_counter() - t0) * len(alpha) / n_planes
-    desc = (f"Eq.(1) rows 0..{n_rows} of {ma} (all {n} frames, unpack timed separately) and "
-            f"{n_planes} of {len(alpha)} planes; extrapolated linearly to one full step")
-    _ = np, mb
-    return t_corr + t_ref, oracle.threads(), desc
+    P = len(alpha)
+    k = ORACLE_SAMPLE_IMAGE_ROWS[workload]
+    g_ref = synth_gamma(ma, mb) if k is not None else None
+    times = []
+    for _ in range(reps):
+        dt, ops, desc, r, _ = oracle_step(acq, planes, frames_host, lay, k, g_ref)
+        times.append(dt)
+    t = statistics.median(times)
+    cpu = {"value": ops / t / 1e12, "unit": "TOPS (int8-equivalent)", "cores": oracle.threads(), "kind": "oracle",
+           "sample": desc, "s_per_sample": t, "samples_timed": reps}
+    if k is not None:
+        cpu["s_per_full_step_extrapolated"] = t * ha / k
+    # ---------------------------------------------------------------- Gamma
+    if k is None:
+        rows = [(0, ma)]
+    else:     # a block at the start and one at a seeded position
+        blk = max(1, min(128, ma // 2))
+        r0 = int(np.random.default_rng(7).integers(blk, ma - blk + 1))
+        rows = [(0, blk), (r0, r0 + blk)]
+    checked = mism = 0
+    sums_exact = True
+    for (r0, r1) in rows:
+        if k is None:
+            want = r
+        else:
+            want = oracle.correlate_rows(frames_host, la, frames_host, lb, acq.n_frames, r0, r1)
+        got = gpu_gamma_rows(r0, r1)
+        wg = want["gamma"] if k is not None else want["gamma"][r0:r1]
+        ws_ab = want["s_ab"] if k is not None else want["s_ab"][r0:r1]
+        mism += int((got["gamma"].view(np.int64) != wg.view(np.int64)).sum())
+        mism += int((got["s_ab"] != ws_ab).sum())
+        checked += wg.size
+        sums_exact &= bool(np.array_equal(got["s_a"], want["s_a"]) and np.array_equal(got["s_b"], want["s_b"]))
+    # ---------------------------------------------------------------- refocus
+    if k is None:
+        g64 = r["gamma"]
+        src = "the oracle's FP64 Gamma of this acquisition (GPU: its FP32 rounding)"
+        pidx = list(range(P))
+    else:
+        g64 = g_ref
+        src = "a seeded stand-in Gamma of the full shape, standard normal values (GPU: the same FP32 values)"
+        pidx = sorted({0, P // 2 - 1, P // 2, P - 1})
+    out = cpi_refocus_fn(g64)                                  # GPU, all P planes, as the step runs it
+    ref = oracle.refocus(g64, ha, wa, hb, wb, alpha[pidx], beta[pidx])
+    ones = oracle.refocus(np.ones((ma, mb)), ha, wa, hb, wb, alpha[pidx], beta[pidx])
+    err = np.abs(out[pidx] - ref)
+    gmax = float(np.abs(g64).max())
+    errors = {
+        "gamma": {"entries_checked": int(checked), "mismatches": mism, "bit_exact": mism == 0 and sums_exact,
+                  "rows": [list(x) for x in rows], "marginals_exact": sums_exact,
+                  "against": "oracle int64 sums and exact-numerator FP64 Gamma"},
+        "refocus": {"planes_checked": pidx, "max_abs_err_over_max_gamma": float(err.max() / gmax),
+                    "max_err_over_max_gamma_times_weight": float((err / np.maximum(1e-6 * gmax * ones, 1e-300)).max()
+                                                                 * 1e-6),
+                    "target": "1e-6 (literal: max|R - R_fp64| / max|Gamma|)", "input": src,
+                    "against": "oracle refocusing in FP64"},
+    }
+    return cpu, errors
 
 
 # ----------------------------------------------------------------------------- GPU arm
 
 def run_native(args, world, rank, local):
+    line = measure_single(args, args.workload, world, rank, with_cpu=not args.no_cpu_baseline)
+    if args.workload == "large_u8" and not args.no_extras:
+        # the other configurations, each measured the same way, as extra keys
+        extra = {}
+        for name, fn in (("spad_1bit", lambda: measure_single(args, "spad_1bit", world, rank, with_cpu=False,
+                                                              with_errors=True, light=True)),
+                         ("batched", lambda: run_batched(args, world, rank)),
+                         ("denoise", lambda: denoise_frames_saved(args, world, rank))):
+            t0 = time.time()
+            r = fn()
+            if r is not None:
+                r["wall_s"] = time.time() - t0
+                extra[name] = r
+        if line is not None:
+            line["workloads"] = extra
+    return line
+
+
+def _dtype(bits):
+    if bits == 1:
+        return "u1 -> e4m3 tensor-core (exact fp32 partials), int64 sums, f64 Gamma, f32 refocus"
+    return ("u8 -> bf16 tensor-core (exact fp32 partials folded into int32 every S frames, S certified from the "
+            "recorded maxima), int64 sums, f64 Gamma, f32 refocus")
+
+
+def measure_single(args, workload, world, rank, with_cpu=True, with_errors=True, light=False):
+    """One single-acquisition workload: the timed step, its stage breakdown and
+    rooflines, e2e through the C ABI, the graph-replayed step, and (rank 0, one
+    GPU) the oracle leg: CPU baseline and errors against the oracle."""
     import torch
 
     import paper_2407_20692_gb300 as cpi
     import synth
 
     cpi.load()
-    key, n_planes = WORKLOADS[args.workload]
+    key, n_planes = WORKLOADS[workload]
     acq = synth.frames.replace(synth.CONFIGS[key], seed=1000 + rank)
     dev = torch.device("cuda", torch.cuda.current_device())
+    t_gen = time.time()
     A, B = synth.generate(acq, dev)
     fr, lay = synth.pack_side_by_side(A, B, acq.bits)
     del A, B
+    torch.cuda.synchronize()
+    t_gen = time.time() - t_gen
     la, lb = lay["a"], lay["b"]
     ha, wa, hb, wb = la["height"], la["width"], lb["height"], lb["width"]
     ma, mb, n = ha * wa, hb * wb, acq.n_frames
@@ -270,7 +394,7 @@ def run_native(args, world, rank, local):
 
     # ---------------------------------------------------------------- roofline
     roofs = rooflines(ma, mb, n, n_planes, acq.bits, dict(ingest=ingest_ms, moments=moments_ms,
-                                                          fold=fold_ms, refocus=refocus_ms), args.workload)
+                                                          fold=fold_ms, refocus=refocus_ms), workload)
     dominant = max(roofs, key=lambda k: roofs[k]["ms"])
     roof = dict(roofs[dominant])
     # ---------------------------------------------------------------- e2e through the C ABI
@@ -285,13 +409,31 @@ def run_native(args, world, rank, local):
                                          gamma_f32=g32, planes=planes, refocus_out=out), flush, stream, dev)
     graph_ms = _max_over_ranks(world, graph_ms / 1e3) * 1e3
 
-    # ---------------------------------------------------------------- CPU baseline (rank 0)
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    # ---------------------------------------------------------------- oracle leg (rank 0, one GPU)
+    # One last plain step so that the outputs checked below are the timed path's.
+    step()
+    torch.cuda.synchronize()
+    cpu = errors = None
+    if rank == 0 and world == 1 and (with_cpu or with_errors):
         host = fr.cpu().numpy()
-        t_cpu, cores, desc = oracle_sample(acq, (alpha, beta), host, lay, args.cpu_rows, args.cpu_planes)
-        cpu = {"value": ops / t_cpu / 1e12, "unit": "TOPS (int8-equivalent)", "cores": cores,
-               "kind": "oracle", "sample": desc, "s_per_step_extrapolated": t_cpu}
+
+        def gamma_rows(r0, r1):
+            return {"gamma": gamma[r0:r1].cpu().numpy(), "s_ab": s_ab[r0:r1].cpu().numpy(),
+                    "s_a": s_a.cpu().numpy(), "s_b": s_b.cpu().numpy()}
+
+        def refocus_fn(g64):
+            gg = torch.tensor(g64.T.astype("float32"), device=dev).contiguous()
+            o = torch.empty((n_planes, ha, wa), dtype=torch.float32, device=dev)
+            cpi.cpi_refocus(gg, ha, wa, hb, wb, planes, o, rws, stream)
+            torch.cuda.synchronize()
+            r = o.cpu().double().numpy()
+            del gg, o
+            return r
+
+        cpu, errors = oracle_leg(workload, acq, (alpha, beta), host, lay, args.cpu_reps if with_cpu else 1,
+                                 refocus_fn, gamma_rows)
+        if not with_cpu:
+            cpu = None
 
     if rank != 0:
         return None
@@ -308,12 +450,9 @@ def run_native(args, world, rank, local):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": ("u1 -> e4m3 tensor-core (exact fp32 partials), int64 sums, f64 Gamma, f32 refocus"
-                  if acq.bits == 1 else
-                  "u8 -> bf16 tensor-core (exact fp32 partials folded every 256 frames), int64 sums, "
-                  "f64 Gamma, f32 refocus"),
+        "dtype": _dtype(acq.bits),
         "data": "synthetic (seeded chaotic-light source model; stand-in for the SwissSPAD2 dataset)",
-        "config": single_config(args.workload, acq, ha, wa, hb, wb, n_planes, world),
+        "config": single_config(workload, acq, ha, wa, hb, wb, n_planes, world),
         "parts_ms": {"ingest": ingest_ms, "moments": moments_ms, "fold": fold_ms, "refocus": refocus_ms},
         "gamma_tops": ops / ((ingest_ms + moments_ms + fold_ms) / 1e3) / 1e12,
         "refocus_planes_per_s": n_planes / (refocus_ms / 1e3),
@@ -325,13 +464,24 @@ def run_native(args, world, rank, local):
         "graph_replay": {"ms_per_step": graph_ms, "value": world * ops / (graph_ms / 1e3) / 1e12,
                          "unit": "TOPS (int8-equivalent)",
                          "call": "cpi_batch_correlate, one item, CPI_BATCH_GRAPH | CPI_BATCH_TUNE"},
-        "gpu_launches": 5 * args.steps,
+        "gpu_launches": KERNELS_PER_STEP * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
+        "input_generation_s": t_gen,
     }
+    if errors is not None:
+        line["errors"] = errors
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if light:
+        for k in ("rooflines_all", "graph_replay"):
+            line.pop(k, None)
     return line
+
+
+# Kernels one step launches: ingest, raw-moment GEMM, fold, refocusing pass (one
+# per 128 planes; every workload here has at most 128), angular-row reduction.
+KERNELS_PER_STEP = 5
 
 
 SM_COUNT = 152
@@ -503,7 +653,7 @@ def run_batched(args, world, rank):
         "value": value, "unit": "TOPS (int8-equivalent, sum of 2*Ma*Mb*N per step)", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(step_ms) / len(step_ms),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u8 -> bf16 tensor-core (exact fp32 partials folded every 256 frames), int64, f64, f32",
+        "dtype": _dtype(8),
         "data": "synthetic (seeded chaotic-light source model)",
         "config": {"workload": "batched: 64 acquisitions, side_a ~ U{32..96}, side_b ~ U{16..48}, "
                                "N ~ U{5000..40000}, uint8 Poisson counts (mean 1-4), 256 planes each",
@@ -560,6 +710,113 @@ def _gamma_prefixes(cpi, acq, dev, prefixes):
         cpi.cpi_correlate(a, b, k, s_ab, s_a, s_b, g64, g32, ws)
         out.append(g32)
     return out
+
+
+def denoise_eval(cpi, model, dev, seeds):
+    """Errors relative to the closed-form expected Gamma, of Gamma itself and of
+    its refocused stack (32 uniform planes), on held-out seeds: the plain estimate
+    at every N of DENOISE["n_eval"], the denoised one at DENOISE["n_den"], and
+    the best scalar multiple of the plain estimate (uses the truth; shrinkage);
+    zeros have relative error 1.  Frames saved: N_equiv / N_in with the plain
+    error fitted as c / sqrt(N)."""
+    import numpy as np
+    import torch
+
+    import synth
+
+    d = DENOISE
+    ha = wa = d["side_a"]
+    hb = wb = d["side_b"]
+    alpha, beta = synth.uniform_planes(d["planes"])
+    planes = cpi.plane_array(alpha, beta)
+    rws = torch.empty(cpi.cpi_refocus_workspace_size(ha, wa, hb, wb, d["planes"]), dtype=torch.uint8, device=dev)
+    wsi = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb), dtype=torch.uint8, device=dev)
+
+    def refocused(g):
+        r = torch.empty((d["planes"], ha, wa), dtype=torch.float32, device=dev)
+        cpi.cpi_refocus(g, ha, wa, hb, wb, planes, r, rws)
+        return r.double()
+
+    def rel(x, ref):
+        return float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
+
+    keys = ("plain", "denoised", "shrink")
+    err = {k: {n: [] for n in d["n_eval"]} for k in keys}
+    err_r = {k: {n: [] for n in d["n_eval"]} for k in keys}
+    for seed in seeds:
+        acq = _denoise_acq(seed, max(d["n_eval"]))
+        ref = synth.expected_gamma_counts(acq, dev, n_frames=10 ** 12).t().contiguous().to(torch.float32)
+        ref_d, ref_r = ref.double(), refocused(ref)
+        for n, g in zip(d["n_eval"], _gamma_prefixes(cpi, acq, dev, list(d["n_eval"]))):
+            gd = g.double()
+            a = float((gd * ref_d).sum() / (gd * gd).sum())
+            rg = refocused(g)
+            ar = float((rg * ref_r).sum() / (rg * rg).sum())
+            err["plain"][n].append(rel(gd, ref_d))
+            err["shrink"][n].append(rel(a * gd, ref_d))
+            err_r["plain"][n].append(rel(rg, ref_r))
+            err_r["shrink"][n].append(rel(ar * rg, ref_r))
+            if n in d["n_den"]:
+                out = torch.empty_like(g)
+                cpi.cpi_denoise(model, g, out, ha, wa, hb, wb, wsi)
+                err["denoised"][n].append(rel(out.double(), ref_d))
+                err_r["denoised"][n].append(rel(refocused(out), ref_r))
+    mean = lambda e: {k: {n: float(np.mean(v)) for n, v in e[k].items() if v} for k in keys}
+    E, ER = mean(err), mean(err_r)
+
+    def fit_c(ep):   # plain error = c / sqrt(N)
+        return math.exp(float(np.mean([math.log(ep[n]) + 0.5 * math.log(n) for n in ep])))
+
+    c, cr = fit_c(E["plain"]), fit_c(ER["plain"])
+    n_equiv = {n: (c / E["denoised"][n]) ** 2 for n in d["n_den"]}
+    n_equiv_r = {n: (cr / ER["denoised"][n]) ** 2 for n in d["n_den"]}
+    return {"E": E, "ER": ER, "c": c, "cr": cr, "n_equiv": n_equiv, "n_equiv_r": n_equiv_r, "keys": keys,
+            "saved": {n: n_equiv[n] / n for n in d["n_den"]}, "saved_r": {n: n_equiv_r[n] / n for n in d["n_den"]}}
+
+
+COMMITTED_MODEL = os.path.join(ROOT, "paper_2407_20692_gb300", "models", "denoiser_64x64_32x32_n1000.npy")
+
+
+def denoise_frames_saved(args, world, rank):
+    """Frames saved by the committed denoiser (trained by `--workload denoise`) on
+    held-out seeds, and its inference time per Gamma: the denoiser term of the
+    headline metric without retraining."""
+    import numpy as np
+    import torch
+
+    import paper_2407_20692_gb300 as cpi
+
+    cpi.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    d = DENOISE
+    ha = wa = d["side_a"]
+    hb = wb = d["side_b"]
+    model = torch.tensor(np.load(COMMITTED_MODEL), device=dev)
+    seeds = [100000 + 500000 + j for j in range(d["eval_seeds"])]        # held out from training
+    ev = denoise_eval(cpi, model, dev, seeds)
+    probe = _gamma_prefixes(cpi, _denoise_acq(seeds[0], d["n_in"]), dev, [d["n_in"]])[0]
+    out = torch.empty_like(probe)
+    wsi = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb), dtype=torch.uint8, device=dev)
+    for _ in range(3):
+        cpi.cpi_denoise(model, probe, out, ha, wa, hb, wb, wsi)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(10):
+        cpi.cpi_denoise(model, probe, out, ha, wa, hb, wb, wsi)
+    e1.record()
+    torch.cuda.synchronize()
+    if cpi.cpi_device_status() != 0:
+        raise RuntimeError("device status error in the denoiser evaluation")
+    if rank != 0:
+        return None
+    return {"metric": "frames saved by the denoiser at equal error of the refocused stack (N_equiv / N_in)",
+            "value": ev["saved_r"][d["n_head"]], "unit": "x", "n_in": d["n_head"],
+            "model": os.path.relpath(COMMITTED_MODEL, ROOT), "eval_seeds": len(seeds),
+            "frames_saved_refocused": {str(k): v for k, v in ev["saved_r"].items()},
+            "frames_saved_gamma": {str(k): v for k, v in ev["saved"].items()},
+            "refocused_error": {k: {str(n): v for n, v in ev["ER"][k].items()} for k in ev["keys"]},
+            "infer_ms_per_gamma": e0.elapsed_time(e1) / 10}
 
 
 def run_denoise(args, world, rank):
@@ -627,53 +884,10 @@ def run_denoise(args, world, rank):
     torch.cuda.synchronize()
     infer_ms = e0.elapsed_time(e1) / args.steps
     # ---------------------------------------------------------------- evaluation
-    # Errors relative to the closed-form expectation, of Gamma itself and of its
-    # refocused stack (32 uniform planes): the plain estimate at every N, the
-    # denoised one, and two reference points: zeros (relative error 1) and the
-    # best scalar multiple of the plain estimate (uses the truth; shrinkage).
-    alpha, beta = synth.uniform_planes(d["planes"])
-    planes = cpi.plane_array(alpha, beta)
-    rws = torch.empty(cpi.cpi_refocus_workspace_size(ha, wa, hb, wb, d["planes"]), dtype=torch.uint8, device=dev)
-
-    def refocused(g):
-        r = torch.empty((d["planes"], ha, wa), dtype=torch.float32, device=dev)
-        cpi.cpi_refocus(g, ha, wa, hb, wb, planes, r, rws)
-        return r.double()
-
-    def rel(x, ref):
-        return float(torch.linalg.vector_norm(x - ref) / torch.linalg.vector_norm(ref))
-
-    keys = ("plain", "denoised", "shrink")
-    err = {k: {n: [] for n in d["n_eval"]} for k in keys}
-    err_r = {k: {n: [] for n in d["n_eval"]} for k in keys}
-    for j in range(d["eval_seeds"]):
-        acq = _denoise_acq(seed0 + 500000 + j, max(d["n_eval"]))
-        ref = synth.expected_gamma_counts(acq, dev, n_frames=10 ** 12).t().contiguous().to(torch.float32)
-        ref_d, ref_r = ref.double(), refocused(ref)
-        for n, g in zip(d["n_eval"], _gamma_prefixes(cpi, acq, dev, list(d["n_eval"]))):
-            gd = g.double()
-            a = float((gd * ref_d).sum() / (gd * gd).sum())
-            rg = refocused(g)
-            ar = float((rg * ref_r).sum() / (rg * rg).sum())
-            err["plain"][n].append(rel(gd, ref_d))
-            err["shrink"][n].append(rel(a * gd, ref_d))
-            err_r["plain"][n].append(rel(rg, ref_r))
-            err_r["shrink"][n].append(rel(ar * rg, ref_r))
-            if n in d["n_den"]:
-                cpi.cpi_denoise(model, g, out, ha, wa, hb, wb, wsi)
-                err["denoised"][n].append(rel(out.double(), ref_d))
-                err_r["denoised"][n].append(rel(refocused(out), ref_r))
-    mean = lambda e: {k: {n: float(np.mean(v)) for n, v in e[k].items() if v} for k in keys}
-    E, ER = mean(err), mean(err_r)
-
-    def fit_c(ep):   # plain error = c / sqrt(N)
-        return math.exp(float(np.mean([math.log(ep[n]) + 0.5 * math.log(n) for n in ep])))
-
-    c, cr = fit_c(E["plain"]), fit_c(ER["plain"])
-    n_equiv = {n: (c / E["denoised"][n]) ** 2 for n in d["n_den"]}
-    n_equiv_r = {n: (cr / ER["denoised"][n]) ** 2 for n in d["n_den"]}
-    saved = {n: n_equiv[n] / n for n in d["n_den"]}
-    saved_r = {n: n_equiv_r[n] / n for n in d["n_den"]}
+    ev = denoise_eval(cpi, model, dev, [seed0 + 500000 + j for j in range(d["eval_seeds"])])
+    E, ER, c, cr = ev["E"], ev["ER"], ev["c"], ev["cr"]
+    n_equiv, n_equiv_r, saved, saved_r = ev["n_equiv"], ev["n_equiv_r"], ev["saved"], ev["saved_r"]
+    keys = ev["keys"]
     if rank != 0:
         return None
     flops = 2.0 * hb * wb * ha * wa * 9 * (
@@ -1022,35 +1236,45 @@ def e2e_run(args, cpi, fr, lay, n, stream, dev, planes, n_planes, ws, rws):
 # ----------------------------------------------------------------------------- reference arm
 
 def run_reference(args, world, rank):
-    """The CPU oracle as it stands, on a bounded sample of each step (rank 0 only)."""
+    """The CPU oracle as it stands, one oracle step per timed step (rank 0 only):
+    the whole step where it fits a few seconds (small_u8, spad_1bit), else a
+    proportional sample of it (large_u8: ORACLE_SAMPLE_IMAGE_ROWS).  `steps` and
+    `ms_per_step` are what was timed; `value` is the sample's own throughput."""
     if rank != 0:
         return None
     import torch
 
+    import oracle
     import synth
 
     key, n_planes = WORKLOADS[args.workload]
     if key is None:
         return {"impl": "reference", "unavailable": "the oracle arm is defined for the single-acquisition "
                                                     "workloads (spad_1bit, small_u8, large_u8)"}
-    acq = synth.CONFIGS[key]
+    acq = synth.frames.replace(synth.CONFIGS[key], seed=1000)
     A, B = synth.generate(acq, "cuda" if torch.cuda.is_available() else "cpu")
     fr, lay = synth.pack_side_by_side(A, B, acq.bits)
+    del A, B
     host = fr.cpu().numpy()
     alpha, beta = synth.uniform_planes(n_planes)
-    ma = lay["a"]["height"] * lay["a"]["width"]
-    mb = lay["b"]["height"] * lay["b"]["width"]
-    ops = 2.0 * ma * mb * acq.n_frames
+    la, lb = lay["a"], lay["b"]
+    ha, wa, hb, wb = la["height"], la["width"], lb["height"], lb["width"]
+    k = ORACLE_SAMPLE_IMAGE_ROWS[args.workload]
+    g_ref = synth_gamma(ha * wa, hb * wb) if k is not None else None
     for _ in range(args.warmup):
-        oracle_sample(acq, (alpha, beta), host, lay, 8, 1)
+        oracle_step(acq, (alpha, beta), host, lay, k, g_ref)
     times = []
-    desc, cores = "", 1
+    ops = desc = None
+    t_region = time.perf_counter()
     for _ in range(args.steps):
-        t, cores, desc = oracle_sample(acq, (alpha, beta), host, lay, args.cpu_rows, args.cpu_planes)
+        t, ops, desc, _, _ = oracle_step(acq, (alpha, beta), host, lay, k, g_ref)
         times.append(t)
+    t_region = time.perf_counter() - t_region
     s = sum(times) / len(times)
     value = ops / s / 1e12
-    return {
+    cpu = {"value": value, "unit": "TOPS (int8-equivalent)", "cores": oracle.threads(), "kind": "oracle",
+           "sample": desc}
+    line = {
         "impl": "reference",
         "metric": "Gamma int8-equivalent TOPS per whole step (ingest + raw-moment GEMM + fold/FP64 "
                   "Gamma + refocus)",
@@ -1058,13 +1282,18 @@ def run_reference(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": s * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8/int64/f64 (CPU oracle)",
         "data": "synthetic (seeded chaotic-light source model)",
-        "config": single_config(args.workload, acq, lay["a"]["height"], lay["a"]["width"], lay["b"]["height"],
-                                lay["b"]["width"], n_planes, world),
-        "cpu_baseline": {"value": value, "unit": "TOPS (int8-equivalent)", "cores": cores,
-                         "kind": "oracle", "sample": desc},
+        "config": single_config(args.workload, acq, ha, wa, hb, wb, n_planes, world),
+        "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": "TOPS (int8-equivalent)", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
+        "wall_s_timed_region": t_region,
     }
+    if k is not None:
+        line["sampled"] = {"fraction_of_step": k / ha,
+                           "s_per_full_step_extrapolated": s * ha / k,
+                           "note": "each timed step is the proportional sample described in cpu_baseline.sample; "
+                                   "the full step is not run (extrapolated linearly, for context only)"}
+    return line
 
 
 def main():
@@ -1073,10 +1302,11 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="spad_1bit")
-    ap.add_argument("--cpu-rows", type=int, default=256)
-    ap.add_argument("--cpu-planes", type=int, default=2)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large_u8")
+    ap.add_argument("--cpu-reps", type=int, default=3, help="oracle steps (or samples) timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="large_u8: skip the other workloads' keys (spad_1bit, batched, denoise)")
     ap.add_argument("--denoise-train-seeds", type=int, default=None)
     ap.add_argument("--denoise-epochs", type=int, default=None)
     ap.add_argument("--save-model", default=None)

@@ -17,6 +17,7 @@ from .frames import (  # noqa: F401
     expected_gamma_counts,
     pack_bits_lsb,
     pack_side_by_side,
+    random_gamma,
     uniform_planes,
 )
 from .model_init import DENOISER_PARAMS, denoiser_init  # noqa: F401,E402

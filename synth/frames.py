@@ -374,3 +374,12 @@ def bin_file_layout(height: int = 256, width: int = 512):
 
 def with_seed(acq: Acquisition, seed: int) -> Acquisition:
     return replace(acq, seed=seed)
+
+
+def random_gamma(ma: int, mb: int, seed: int) -> np.ndarray:
+    """A seeded stand-in correlation function for refocusing checks: float64
+    [ma][mb] (row = spatial pixel, column = angular pixel), i.i.d. standard
+    normal values rounded to float32 (so that the FP32 copy a GPU path reads is
+    the same data).  Refocusing cost does not depend on the values."""
+    rng = np.random.Generator(np.random.Philox(int(seed)))
+    return rng.standard_normal((ma, mb), dtype=np.float32).astype(np.float64)

@@ -82,3 +82,16 @@ def refocus_tolerance(gamma64, ha, wa, hb, wb, alpha, beta):
     ones = np.ones((ha * wa, hb * wb))
     W = oracle.refocus(ones, ha, wa, hb, wb, alpha, beta)
     return 1e-6 * np.abs(gamma64).max() * W
+
+
+def refocus_errors(out, ref, gamma64, ha, wa, hb, wb, alpha, beta):
+    """Errors of a refocused stack against the FP64 oracle, in both readings of the
+    refocusing target: the literal ratio max|R - R_fp64| / max|Gamma| and the
+    per-unit-weight ratio max(|R - R_fp64| / (max|Gamma| W_p(x))) (<= 1 passes).
+    Returns (literal, per_weight, tolerance array)."""
+    tol = refocus_tolerance(gamma64, ha, wa, hb, wb, alpha, beta)
+    err = np.abs(np.asarray(out, dtype=np.float64) - ref)
+    gmax = np.abs(gamma64).max()
+    literal = float(err.max() / gmax) if gmax > 0 else 0.0
+    per_w = float((err / np.maximum(tol, 1e-300)).max())
+    return literal, per_w, tol

@@ -9,7 +9,8 @@ import torch
 
 import paper_2407_20692_gb300 as cpi
 import synth
-from gpu_util import assert_exact, desc, oracle_correlate
+import oracle
+from gpu_util import assert_exact, desc, oracle_correlate, refocus_errors
 
 pytestmark = pytest.mark.gpu
 
@@ -93,16 +94,91 @@ def test_batch_equals_individual_calls_and_replays():
         _check(items, keep)
 
 
-def test_batch_item_against_oracle():
+def test_batch_every_item_against_oracle():
+    """Every item of a graph-replayed batch, Gamma and its refocused stack, against
+    the oracle on the same frames (not against the library's own single calls):
+    sums and Gamma bit for bit, the refocused stack within the refocusing
+    tolerance of the FP64 oracle refocusing the oracle's Gamma."""
     items, keep = _make(300)
     arr = cpi.batch_items(items)
     ws = torch.empty(cpi.cpi_batch_workspace_size(arr), dtype=torch.uint8, device="cuda")
     cpi.cpi_batch_correlate(arr, ws)
     torch.cuda.synchronize()
-    for e, (fr, lay, acq) in list(zip(items, keep))[:3]:
+    assert cpi.cpi_device_status() == 0
+    alpha, beta = synth.uniform_planes(6)
+    for e, (fr, lay, acq) in zip(items, keep):
         want = oracle_correlate(fr.cpu().numpy(), lay["a"], lay["b"], acq.n_frames)
         got = {k: e[k].cpu() for k in ("s_ab", "s_a", "s_b", "gamma")}
         assert_exact(got, want)
+        ha, wa, hb, wb = lay["a"]["height"], lay["a"]["width"], lay["b"]["height"], lay["b"]["width"]
+        ref = oracle.refocus(want["gamma"], ha, wa, hb, wb, alpha, beta)
+        out = e["refocus_out"].cpu().double().numpy()
+        literal, per_w, tol = refocus_errors(out, ref, want["gamma"], ha, wa, hb, wb, alpha, beta)
+        assert (np.abs(out - ref) <= tol).all(), (acq, per_w)
+        assert literal <= 1e-6, (acq, literal)
+
+
+def test_batch_of_64_uneven_acquisitions_sampled_against_oracle():
+    """The benchmark's batch itself: 64 acquisitions of uneven size
+    (synth.batched_acquisitions(64, seed=1234)), 256 planes each, one
+    graph-captured, tuned cpi_batch_correlate call.  The oracle checks a seeded
+    sample: the four smallest items in full (sums, Gamma, and four refocused
+    planes), and four more items on two blocks of rows (the first 64 and 32 from
+    a seeded position) of S_ab and Gamma, with all of S_a and S_b."""
+    acqs = synth.batched_acquisitions(64, seed=1234)
+    alpha, beta = synth.uniform_planes(256)
+    planes = cpi.plane_array(alpha, beta)
+    entries, keep = [], []
+    for acq in acqs:
+        A, B = synth.generate(acq, "cuda")
+        fr, lay = synth.pack_side_by_side(A, B, 8)
+        del A, B
+        ma, mb = acq.side_a ** 2, acq.side_b ** 2
+        entries.append(dict(a=desc(fr, lay["a"]), b=desc(fr, lay["b"]), n_frames=acq.n_frames,
+                            s_ab=torch.empty((ma, mb), dtype=torch.int64, device="cuda"),
+                            s_a=torch.empty(ma, dtype=torch.int64, device="cuda"),
+                            s_b=torch.empty(mb, dtype=torch.int64, device="cuda"),
+                            gamma=torch.empty((ma, mb), dtype=torch.float64, device="cuda"),
+                            gamma_f32=torch.empty((mb, ma), dtype=torch.float32, device="cuda"),
+                            planes=planes,
+                            refocus_out=torch.empty((256, acq.side_a, acq.side_a), dtype=torch.float32,
+                                                    device="cuda")))
+        keep.append((fr, lay, acq))
+    arr = cpi.batch_items(entries)
+    ws = torch.empty(cpi.cpi_batch_workspace_size(arr), dtype=torch.uint8, device="cuda")
+    cpi.cpi_batch_correlate(arr, ws)
+    cpi.cpi_batch_correlate(arr, ws)          # replay of the captured graph
+    torch.cuda.synchronize()
+    assert cpi.cpi_device_status() == 0
+    mac = [a.side_a ** 2 * a.side_b ** 2 * a.n_frames for a in acqs]
+    order = np.argsort(mac)
+    small = [int(i) for i in order[:4]]
+    rng = np.random.default_rng(1234)
+    large = [int(i) for i in rng.choice(order[4:], 4, replace=False)]
+    pidx = [0, 127, 128, 255]
+    for i in small:
+        e, (fr, lay, acq) = entries[i], keep[i]
+        want = oracle_correlate(fr.cpu().numpy(), lay["a"], lay["b"], acq.n_frames)
+        assert_exact({k: e[k].cpu() for k in ("s_ab", "s_a", "s_b", "gamma")}, want)
+        ha, hb = acq.side_a, acq.side_b
+        ref = oracle.refocus(want["gamma"], ha, ha, hb, hb, alpha[pidx], beta[pidx])
+        out = e["refocus_out"][pidx].cpu().double().numpy()
+        literal, per_w, tol = refocus_errors(out, ref, want["gamma"], ha, ha, hb, hb, alpha[pidx], beta[pidx])
+        assert (np.abs(out - ref) <= tol).all(), (acq, per_w)
+        assert literal <= 1e-6, (acq, literal)
+    for i in large:
+        e, (fr, lay, acq) = entries[i], keep[i]
+        host = fr.cpu().numpy()
+        ma = acq.side_a ** 2
+        r0 = int(rng.integers(64, ma - 32))
+        rows = [(0, 64), (r0, r0 + 32)]
+        for r0, r1 in rows:
+            want = oracle.correlate_rows(host, lay["a"], host, lay["b"], acq.n_frames, r0, r1)
+            assert np.array_equal(e["s_ab"][r0:r1].cpu().numpy(), want["s_ab"]), (acq, r0)
+            assert np.array_equal(e["gamma"][r0:r1].cpu().numpy().view(np.int64), want["gamma"].view(np.int64)), \
+                (acq, r0)
+        assert np.array_equal(e["s_a"].cpu().numpy(), want["s_a"])
+        assert np.array_equal(e["s_b"].cpu().numpy(), want["s_b"])
 
 
 def test_batch_rejects_bad_items():
