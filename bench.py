@@ -554,14 +554,15 @@ def rooflines(ma, mb, n, n_planes, bits, ms, workload):
                    "work": "24 B per Gamma entry"}
     # Refocus, as the workload's metric defines it: per-plane Gamma FP32 traffic
     # (P planes x Ma x Mb x 4 B, what an unfused per-plane gather reads) per
-    # second against the HBM copy peak.  The kernel reads Gamma from HBM once
-    # per pass of 4 planes and is bound on chip by shared-memory loads, given
-    # as "lsu" (8 B of loads per plane, row, column and angular pixel).
+    # second against the HBM copy peak.  The x stage stages each band of Gamma
+    # rows once per block of 4 planes and is bound on chip by shared-memory
+    # loads, given as "lsu" (8 B of loads per plane, row, column and angular
+    # pixel: the two taps of one sample).
     eff = n_planes * ma * mb * 4.0 / (ms["refocus"] / 1e3) / 1e9
     smem = n_planes * ma * mb * 8.0
     smem_peak = SM_COUNT * SMEM_BYTES_PER_CLK * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
     a = smem / (ms["refocus"] / 1e3) / 1e9
-    out["refocus"] = {"kernel": "refocus (pipelined bilinear shift-and-sum, 4 planes per Gamma pass, + row reduce)",
+    out["refocus"] = {"kernel": "refocus (row-band x stage, 4 planes per staged slice band, + y stage over angular rows)",
                       "bound": "hbm", "achieved": eff, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                       "frac": eff / peaks["hbm_gbs"], "traffic": _traffic("refocus", workload),
                       "peak_source": f"{src} hbm copy", "ms": ms["refocus"],

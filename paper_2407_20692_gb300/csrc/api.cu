@@ -96,36 +96,6 @@ bool make_operand_map(CUtensorMap* m, void* base, bool bf16, int64_t rows, int64
     return r == CUDA_SUCCESS;
 }
 
-// Slice-major FP32 Gamma as [Mb * ha rows][wa columns], rows pitch floats apart
-// (a multiple of 4); box (wa4 + 8) x box_rows starting at column -4 (wa4 = wa rounded
-// up to a multiple of 4) returns each slice with zeros in every column outside
-// 0 .. wa-1 (box_rows: the slice's ha rows and a few of the next slice's).
-bool make_slice_map(CUtensorMap* m, const float* g, int ha, int wa, int64_t mb, int pitch, int box_rows) {
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return false;
-    cuuint64_t dims[2] = {(cuuint64_t)wa, (cuuint64_t)(mb * ha)};
-    cuuint64_t strides[1] = {(cuuint64_t)pitch * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)(((wa + 3) & ~3) + 8), (cuuint32_t)box_rows};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(g), dims, strides, box,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
-bool make_gamma_map(CUtensorMap* m, const float* g, int64_t elements) {
-    EncodeTiledFn enc = encode_fn();
-    if (!enc) return false;
-    cuuint64_t dims[1] = {(cuuint64_t)elements};
-    cuuint64_t strides[1] = {0};
-    cuuint32_t box[1] = {256};
-    cuuint32_t estr[1] = {1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 1, const_cast<float*>(g), dims, strides, box,
-                     estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
-}
-
 }  // namespace
 
 bool make_bf16_map_sw64(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
@@ -142,6 +112,23 @@ bool make_bf16_map_sw64(CUtensorMap* m, const void* base, int rank, const uint64
     const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), d, st, bx,
                            es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool make_f32_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                  const uint32_t* box) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || rank < 1 || rank > 3) return false;
+    cuuint64_t d[3], st[2];
+    cuuint32_t bx[3], es[3] = {1, 1, 1};
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+    }
+    for (int i = 0; i < rank - 1; ++i) st[i] = strides[i];
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, (cuuint32_t)rank, const_cast<void*>(base), d, st, bx,
+                           es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
 }
 
@@ -340,13 +327,9 @@ cpi_status correlate_common(const int32_t* stages, int n_stages, const cpi_frame
     return CPI_OK;
 }
 
-size_t refocus_ws_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb, int32_t n_planes, int sm) {
+size_t refocus_ws_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb, int32_t n_planes) {
     if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || n_planes < 1) return 0;
-    const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
-    const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, sm);
-    const size_t partial = round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(float), 256);
-    const int pitch = refocus_pitch(ha, wa, wb);
-    return partial + round_up((size_t)hb * wb * ha * (size_t)pitch * sizeof(float), 256);
+    return refocus_ws_bytes(ha, wa, hb, wb, n_planes);
 }
 
 cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,
@@ -355,66 +338,21 @@ cpi_status run_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t h
     if (!gamma_f32 || !planes || !out || n_planes < 1) return CPI_ERR_INVALID_ARG;
     if (ha < 1 || wa < 1 || hb < 1 || wb < 1 || wa > 512) return CPI_ERR_INVALID_ARG;
     if ((int64_t)hb * wb > kMaxPixels) return CPI_ERR_INVALID_ARG;
-    if (refocus_smem_bytes(ha, wa, wb) > 220 * 1024) return CPI_ERR_UNSUPPORTED;
+    if (!refocus_supported(ha, wa, hb, wb)) return CPI_ERR_UNSUPPORTED;
     if (!aligned(gamma_f32, 16) || !aligned(out, 4)) return CPI_ERR_INVALID_ARG;
-    for (int i = 0; i < n_planes; ++i)
+    std::vector<double> alpha(n_planes), beta(n_planes);
+    for (int i = 0; i < n_planes; ++i) {
         if (!(std::fabs(planes[i].alpha) <= kRefocusMaxCoef) || !(std::fabs(planes[i].beta) <= kRefocusMaxCoef))
             return CPI_ERR_INVALID_ARG;
+        alpha[i] = planes[i].alpha;
+        beta[i] = planes[i].beta;
+    }
     DeviceInfo* dev = nullptr;
     if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
-    const size_t need = refocus_ws_size(ha, wa, hb, wb, n_planes, dev->sm_count);
+    const size_t need = refocus_ws_size(ha, wa, hb, wb, n_planes);
     if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return CPI_ERR_WORKSPACE;
-    const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
-    const int ranges = refocus_ranges(ha, wa, hb, wb, per_launch, dev->sm_count);
-    float* partial = static_cast<float*>(workspace);
-    CUtensorMap tm;
-    const int staging = refocus_staging(ha, wa, wb);
-    const bool pipe = staging != 0;
-    const int64_t elements = (int64_t)hb * wb * ha * wa;
-    if (pipe && elements >= ((int64_t)1 << 31) - 1024) return CPI_ERR_UNSUPPORTED;
-    if (staging == 1 && !make_gamma_map(&tm, gamma_f32, elements)) return CPI_ERR_CUDA;
-    if (staging == 2) {
-        // rows that are not 16-byte multiples: stage from a copy with padded rows
-        const int pitch = refocus_pitch(ha, wa, wb);
-        const float* src = gamma_f32;
-        if (pitch != 0) {
-            const size_t part_bytes =
-                round_up((size_t)ranges * (size_t)n_planes * (size_t)ha * (size_t)wa * sizeof(float), 256);
-            float* copy = reinterpret_cast<float*>(static_cast<uint8_t*>(workspace) + part_bytes);
-            const cudaError_t e =
-                launch_refocus_repack(gamma_f32, copy, (int64_t)hb * wb * ha, wa, pitch, dev->sm_count, st);
-            if (e != cudaSuccess) return CPI_ERR_CUDA;
-            src = copy;
-        }
-        if (!make_slice_map(&tm, src, ha, wa, (int64_t)hb * wb, pitch != 0 ? pitch : wa, refocus_box_rows(ha, wa)))
-            return CPI_ERR_CUDA;
-    }
-    PlaneBlock pb;
-    for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {
-        const int np = n_planes - p0 < kRefocusMaxPlanesPerLaunch ? n_planes - p0
-                                                                  : kRefocusMaxPlanesPerLaunch;
-        std::memset(&pb, 0, sizeof(pb));
-        for (int i = 0; i < np; ++i) {
-            pb.alpha[i] = planes[p0 + i].alpha;
-            pb.beta[i] = planes[p0 + i].beta;
-        }
-        RefocusGeom g{};
-        g.ha = ha;
-        g.wa = wa;
-        g.hb = hb;
-        g.wb = wb;
-        g.n_ranges = ranges;
-        g.b_per_range = refocus_range_size(ha, wa, hb, wb, ranges);
-        g.n_planes = np;
-        g.plane_offset = p0;
-        g.total_planes = n_planes;
-        g.status = dev->status;
-        g.timeout_ns = g_timeout_ns;
-        cudaError_t e = launch_refocus(gamma_f32, pipe ? &tm : nullptr, g, pb, partial, dev->sm_count, st);
-        if (e != cudaSuccess) return CPI_ERR_CUDA;
-    }
-    return cuda_status(
-        launch_refocus_reduce(partial, ranges, (int64_t)n_planes * ha * wa, out, st));
+    return cuda_status(refocus_run(gamma_f32, ha, wa, hb, wb, alpha.data(), beta.data(), n_planes, out, workspace,
+                                   dev->sm_count, dev->status, g_timeout_ns, st));
 }
 
 
@@ -449,8 +387,8 @@ cpi_status check_batch_item(const cpi_batch_item& b) {
     if (b.n_planes < 0) return CPI_ERR_INVALID_ARG;
     if (b.n_planes > 0) {
         if (!b.planes || !b.refocus_out || !b.gamma_f32) return CPI_ERR_INVALID_ARG;
-        if (b.a.width > 512 || refocus_smem_bytes(b.a.height, b.a.width, b.b.width) > 220 * 1024)
-            return CPI_ERR_UNSUPPORTED;
+        if (b.a.width > 512) return CPI_ERR_INVALID_ARG;
+        if (!refocus_supported(b.a.height, b.a.width, b.b.height, b.b.width)) return CPI_ERR_UNSUPPORTED;
         for (int i = 0; i < b.n_planes; ++i)
             if (!(std::fabs(b.planes[i].alpha) <= kRefocusMaxCoef) || !(std::fabs(b.planes[i].beta) <= kRefocusMaxCoef))
                 return CPI_ERR_INVALID_ARG;
@@ -473,7 +411,7 @@ cpi_status make_batch_plan(const cpi_batch_item* items, int n, int sm, BatchShap
         ip.ws_off = off;
         off = round_up(off + ip.pl.ws_bytes, 1024);
         if (b.n_planes > 0) {
-            ip.rws_bytes = refocus_ws_size(b.a.height, b.a.width, b.b.height, b.b.width, b.n_planes, sm);
+            ip.rws_bytes = refocus_ws_size(b.a.height, b.a.width, b.b.height, b.b.width, b.n_planes);
             ip.rws_off = off;
             off = round_up(off + ip.rws_bytes, 1024);
         }
@@ -788,10 +726,7 @@ cpi_status cpi_correlate_finalize(const int64_t* s_ab, const int64_t* s_a, const
 
 size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb,
                                   int32_t n_planes) {
-    DeviceInfo* dev = nullptr;
-    int sm = 152;
-    if (device_info(&dev) == cudaSuccess) sm = dev->sm_count;
-    return refocus_ws_size(ha, wa, hb, wb, n_planes, sm);
+    return refocus_ws_size(ha, wa, hb, wb, n_planes);
 }
 
 cpi_status cpi_refocus(const float* gamma_f32, int32_t ha, int32_t wa, int32_t hb, int32_t wb,

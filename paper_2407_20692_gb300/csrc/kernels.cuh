@@ -89,47 +89,28 @@ struct PlaneBlock {
     double alpha[kRefocusMaxPlanesPerLaunch];
     double beta[kRefocusMaxPlanesPerLaunch];
 };
-struct RefocusGeom {
-    int32_t ha, wa, hb, wb;
-    int32_t n_ranges, b_per_range;   // ranges, and angular rows (or pixels) per range
-    int32_t n_planes;        // planes in this launch
-    int32_t plane_offset;    // index of this launch's first plane in the partial buffer
-    int32_t total_planes;
-    int32_t boxes;           // 256-element boxes per slice, 1-D staging (set by launch_refocus)
-    int32_t slice_f;         // floats per shared-memory stage buffer (set by launch_refocus)
-    int32_t stages;          // shared-memory stage buffers (set by launch_refocus)
-    unsigned int* status;           // device status word (bounded waits)
-    unsigned long long timeout_ns;
-};
 // Planes with |alpha| or |beta| above this are rejected (coordinates are formed
 // in 32.32 fixed point).
 constexpr double kRefocusMaxCoef = 1.0e6;
-size_t refocus_smem_bytes(int ha, int wa, int wb);
-// Pipelined kernel (TMA-staged slices).  refocus_staging: 0 = direct kernel (no
-// tensor map), 1 = 1-D tensor map over all Mb*ha*wa elements with a 256-element
-// box, 2 = 2-D map over [Mb*ha rows][wa columns] (row stride refocus_pitch()
-// floats when that is non-zero, else wa) with a (wa4 + 8) x ha box, wa4 = wa
-// rounded up to a multiple of 4.
-bool refocus_pipelined(int ha, int wa, int wb);
-int refocus_staging(int ha, int wa, int wb);
-// Row pitch (floats) of the padded copy of Gamma that 2-D staging needs when wa
-// is not a multiple of 4, else 0 (Gamma is staged from the caller's buffer).
-int refocus_pitch(int ha, int wa, int wb);
-// Rows of one staged slice box (the slice's ha rows and up to NK - 1 more).
-int refocus_box_rows(int ha, int wa);
-// dst[r * pitch + c] = gamma_f32[r * wa + c] for rows r < rows, c < wa.
-cudaError_t launch_refocus_repack(const float* gamma_f32, float* dst, int64_t rows, int wa, int pitch,
-                                  int sm_count, cudaStream_t st);
-// Number of ranges the angular pixels are split into (one partial image each),
-// and the size of one range (angular rows for the pipelined kernel, angular
-// pixels for the direct one).
-int refocus_ranges(int ha, int wa, int hb, int wb, int n_planes, int sm_count);
-int refocus_range_size(int ha, int wa, int hb, int wb, int n_ranges);
-// tm: the tensor map refocus_staging() asks for (unused by the direct kernel).
-cudaError_t launch_refocus(const float* gamma_f32, const CUtensorMap* tm, const RefocusGeom& g,
-                           const PlaneBlock& pl, float* partial, int sm_count, cudaStream_t st);
-cudaError_t launch_refocus_reduce(const float* partial, int n_ranges, int64_t per_range,
-                                  float* out, cudaStream_t st);
+// Shapes the refocusing kernels take: wa <= 512 and hb small enough for the y
+// taps of one output row to fit a CTA (hb <= 12800).
+bool refocus_supported(int ha, int wa, int hb, int wb);
+// Workspace bytes: the x-stage images of up to kRefocusMaxPlanesPerLaunch planes
+// ([planes][hb][ha][wa] floats), plus a row-padded copy of Gamma when its rows
+// do not meet the staging alignment.  0 if unsupported.
+size_t refocus_ws_bytes(int ha, int wa, int hb, int wb, int n_planes);
+// Kernel launches of one refocusing call.
+int refocus_launches(int ha, int wa, int n_planes);
+// Whole refocusing of gamma_f32 (slice-major [hb*wb][ha*wa]) into out
+// ([n_planes][ha][wa]); alpha, beta: host arrays of n_planes coefficients.
+cudaError_t refocus_run(const float* gamma_f32, int ha, int wa, int hb, int wb, const double* alpha,
+                        const double* beta, int n_planes, float* out, void* workspace, int sm_count,
+                        unsigned int* status, unsigned long long timeout_ns, cudaStream_t st);
+// Tiled tensor map over a float32 array of rank 2 or 3 (no swizzle); dims
+// innermost first, strides in bytes for dims 1..rank-1.  False if the driver
+// rejects it.
+bool make_f32_map(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                  const uint32_t* box);
 
 // ------------------------------------------------------------------ 4-D refocus
 constexpr int kRefocus4dChunk = 64;        // planes per launch chunk (at most)

@@ -65,17 +65,24 @@ def test_workspace_query_host_logic():
     assert cpi.cpi_refocus_workspace_size(0, 64, 32, 32, 32) == 0
 
 
-def test_refocus_workspace_holds_a_row_padded_copy_for_unaligned_widths():
-    """Widths that are not a multiple of 4 stage from a copy of Gamma with rows
-    padded to a multiple of 4 floats, kept after the partial images."""
-    for ha, wa, hb, wb, P in [(33, 70, 7, 5, 7), (46, 95, 4, 4, 3), (17, 33, 5, 3, 2)]:
-        wa4 = (wa + 3) // 4 * 4
+def test_refocus_workspace_layout():
+    """The x stage's images [planes][hb][ha][wa] for up to 128 planes (larger
+    stacks run in chunks of 128 that reuse them), then, when Gamma's rows do not
+    meet the staging alignment, a copy of Gamma with padded rows: to a multiple
+    of 4 floats for rows up to 248 wide (2-D staging), of 16 floats above
+    (3-D staging in 16-float chunks)."""
+    up = lambda n: -(-n // 256) * 256
+    for ha, wa, hb, wb, P in [(33, 70, 7, 5, 7), (46, 95, 4, 4, 3), (17, 33, 5, 3, 2), (64, 64, 32, 32, 32),
+                              (128, 128, 64, 64, 128), (12, 10, 3, 4, 200), (5, 300, 3, 2, 7), (9, 256, 2, 2, 3),
+                              (256, 256, 4, 4, 100), (3, 512, 2, 2, 2), (4, 249, 2, 2, 1)]:
         ws = cpi.cpi_refocus_workspace_size(ha, wa, hb, wb, P)
-        # one partial image per angular row and plane, then the padded copy
-        partial = -(-hb * P * ha * wa * 4 // 256) * 256
-        assert ws == partial + -(-hb * wb * ha * wa4 * 4 // 256) * 256, (ha, wa)
-    # aligned widths need no copy
-    assert cpi.cpi_refocus_workspace_size(64, 64, 32, 32, 32) == 32 * 32 * 64 * 64 * 4
+        want = up(min(P, 128) * hb * ha * wa * 4)
+        pitch = (wa + 3) // 4 * 4 if wa <= 248 else (wa + 15) // 16 * 16
+        if pitch != wa:
+            want += up(hb * wb * ha * pitch * 4)
+        assert ws == want, (ha, wa, hb, wb, P, ws, want)
+    # rows wider than 512 are refused (0)
+    assert cpi.cpi_refocus_workspace_size(4, 513, 2, 2, 1) == 0
 
 
 def test_denoise_workspace_has_channels_last_buffers_for_tensor_core_widths():

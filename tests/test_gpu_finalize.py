@@ -95,6 +95,8 @@ def test_finalize_sums_beyond_int64_products(n):
     ma, mb = 24, 40
     s_a = rng.integers(200 * n // 2, 255 * n, size=ma, dtype=np.int64)
     s_b = rng.integers(100 * n // 2, 255 * n, size=mb, dtype=np.int64)
+    s_a[0] = 255 * n                        # the largest sums: S_a S_b = 65025 n^2 >= 2^63 for n >= 1.2e7
+    s_b[0] = 255 * n
     s_ab = np.empty((ma, mb), dtype=np.int64)
     for i in range(ma):
         for j in range(mb):
@@ -103,7 +105,7 @@ def test_finalize_sums_beyond_int64_products(n):
                 s_ab[i, j] = prod // n + (j % 5) - 2
             else:          # correlated sums: S_ab above the product of the means
                 s_ab[i, j] = min(prod // n + int(rng.integers(0, 1 << 40)), (1 << 62))
-    assert any(abs(int(s_a[i]) * int(s_b[0])) >= 1 << 63 for i in range(ma))
+    assert int(s_a[0]) * int(s_b[0]) >= 1 << 63
     dev = "cuda"
     g = torch.empty((ma, mb), dtype=torch.float64, device=dev)
     g32 = torch.empty((mb, ma), dtype=torch.float32, device=dev)
