@@ -48,6 +48,45 @@ __device__ __forceinline__ void kahan_add(float& acc, float& cmp, float v) {
     acc = t;
 }
 
+// Two FP32 lanes in one 64-bit register pair, for the packed f32x2 instructions
+// of sm_100+ (each lane is an ordinary IEEE round-to-nearest FP32 operation).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpk2(f32x2 v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+// kahan_add on both lanes
+__device__ __forceinline__ void kahan_add2(f32x2& acc, f32x2& cmp, f32x2 v) {
+    const f32x2 y = sub2(v, cmp);
+    const f32x2 t = add2(acc, y);
+    cmp = sub2(sub2(t, acc), y);
+    acc = t;
+}
+
 // Taps of one axis from a 32.32 fixed-point coordinate: integer part i and the
 // fraction rounded to 24 bits; taps outside [0, n) get weight 0 and are moved
 // onto in-grid rows, so no read leaves the image.
@@ -104,16 +143,39 @@ struct BandGeom {
     int32_t mode3d;            // 3-D chunked staging (rows wider than 248)
     int32_t stages;            // stage buffers (<= kBandMaxStages)
     uint32_t stage_bytes;      // BH * WS * 4
+    const long long* xcol;     // [n_planes][kBandThreads]: column part of each column thread's x coordinate
+    const long long* xang;     // [n_planes][2]: angular part at bc = 0, and its step per angular column
     unsigned int* status;
     unsigned long long timeout_ns;
 };
+
+// Fixed-point x coordinates of a launch's planes (32.32, each rounded once from
+// FP64): xcol[p][c] = fix(alpha (c - cxa) + cxa) + the 24-bit rounding bias and
+// the staging pad, for every column thread c; xang[p] = {fix(beta sx (0 - cxb)),
+// fix(beta sx)}.
+__global__ void __launch_bounds__(256) refocus_xtables_kernel(const PlaneBlock pl, int n_planes, int wa, int wb,
+                                                              int pad_l, long long* __restrict__ xcol,
+                                                              long long* __restrict__ xang) {
+    const double cxa = 0.5 * (double)(wa - 1), cxb = 0.5 * (double)(wb - 1);
+    const double sx = (double)wa / (double)wb;
+    const long long bias = 128ll + ((long long)pad_l << 32);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_planes * kBandThreads; i += gridDim.x * blockDim.x) {
+        const int p = i / kBandThreads, c = i - p * kBandThreads;
+        xcol[i] = fix32(pl.alpha[p] * ((double)c - cxa) + cxa) + bias;
+        if (c == 0) {
+            const double bs = pl.beta[p] * sx;
+            xang[2 * p] = fix32(bs * (0.0 - cxb));
+            xang[2 * p + 1] = fix32(bs);
+        }
+    }
+}
 
 template <int WS, int KR, int PB>
 __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __grid_constant__ CUtensorMap tm,
                                                                        const BandGeom g, const PlaneBlock pl,
                                                                        float* __restrict__ ubuf) {
     constexpr int NW = kBandThreads / 32;
-    constexpr int PG = PB < 2 ? PB : 2;     // planes whose taps are in registers at a time
+    static_assert(PB % 2 == 0, "planes are processed in pairs");
     extern __shared__ __align__(128) float sm_raw[];
     float* const buf0 =
         sm_raw + (((128u - (static_cast<uint32_t>(__cvta_generic_to_shared(sm_raw)) & 127u)) & 127u) >> 2);
@@ -155,10 +217,7 @@ __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __g
     if (tid == 0)
         for (uint32_t q = 0; q < (uint32_t)stages && q < total_sl; ++q) issue(q);
 
-    const double cxa = 0.5 * (double)(wa - 1), cxb = 0.5 * (double)(wb - 1);
-    const double sx = (double)wa / (double)wb;
     const int lo_b = g.pad_l - 2, hi_b = g.pad_l + wa;    // clamp of a tap's staged column
-    const long long bias = 128ll + ((long long)g.pad_l << 32);
     uint32_t gs = 0;      // slices of this CTA consumed so far
     int cs = 0;           // stage of slice gs
     uint32_t cp = 0;      // phase parity of slice gs in its stage
@@ -170,20 +229,20 @@ __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __g
         const int np = min(PB, g.n_planes - p0);
         // running coordinate of this column at angular column bc (from bc = 0):
         // the column's part (with the 24-bit rounding bias and the staging pad)
-        // plus the angular part, stepped by the increment dB per angular column
+        // plus the angular part, stepped by dB per angular column
         long long X[PB], dB[PB];
 #pragma unroll
         for (int j = 0; j < PB; ++j) {
             const int pj = p0 + min(j, np - 1);
-            const double al = pl.alpha[pj], bs = pl.beta[pj] * sx;
-            X[j] = fix32(al * ((double)c - cxa) + cxa) + bias + fix32(bs * (0.0 - cxb));
-            dB[j] = fix32(bs);
+            X[j] = __ldg(g.xcol + (size_t)pj * kBandThreads + c) + __ldg(g.xang + 2 * pj);
+            dB[j] = __ldg(g.xang + 2 * pj + 1);
         }
-        float U[PB][KR], C[PB][KR];
+        // sums of plane pairs (2q, 2q + 1) in the two lanes of a packed register
+        f32x2 U[PB / 2][KR], C[PB / 2][KR];
 #pragma unroll
-        for (int j = 0; j < PB; ++j)
+        for (int q = 0; q < PB / 2; ++q)
 #pragma unroll
-            for (int kk = 0; kk < KR; ++kk) U[j][kk] = C[j][kk] = 0.0f;
+            for (int kk = 0; kk < KR; ++kk) U[q][kk] = C[q][kk] = 0ull;
         for (int bc0 = 0; bc0 < wb; bc0 += 2) {
             const int nsl = min(2, wb - bc0);
             const int s0 = cs, s1 = cs + 1 == stages ? 0 : cs + 1;
@@ -200,44 +259,43 @@ __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __g
             if (active) {
                 const float* S0 = buf0 + (size_t)s0 * slice_f + rp * KR * WS;
                 const float* S1 = buf0 + (size_t)s1 * slice_f + rp * KR * WS;
-                // planes in groups of PG: the taps of one group live in registers
-                // while its rows are summed
+                const f32x2 one2 = pk2(1.0f, 1.0f);
+                // one plane pair at a time: its taps live in registers while its
+                // rows are summed (lane l of every packed value: plane 2q + l)
 #pragma unroll
-                for (int g0 = 0; g0 < PB; g0 += PG) {
-                    const float* qa[PG];
-                    const float* qb[PG];
-                    float a0[PG], a1[PG], b0[PG], b1[PG];
+                for (int q = 0; q < PB / 2; ++q) {
+                    const float* pa[2];
+                    const float* pb[2];
+                    float fa[2], fb[2];
 #pragma unroll
-                    for (int jj = 0; jj < PG; ++jj) {
-                        const int j = g0 + jj;
+                    for (int l = 0; l < 2; ++l) {
+                        const int j = 2 * q + l;
                         const long long ua = X[j];
                         const long long ub = ua + dB[j];
                         X[j] = ub + dB[j];
-                        qa[jj] = S0 + min(max((int)(ua >> 32), lo_b), hi_b);
-                        a1[jj] = (float)((uint32_t)ua >> 8) * 0x1p-24f;
-                        a0[jj] = 1.0f - a1[jj];
-                        qb[jj] = S1 + min(max((int)(ub >> 32), lo_b), hi_b);
-                        b1[jj] = (float)((uint32_t)ub >> 8) * 0x1p-24f;
-                        b0[jj] = 1.0f - b1[jj];
+                        pa[l] = S0 + min(max((int)(ua >> 32), lo_b), hi_b);
+                        fa[l] = (float)((uint32_t)ua >> 8) * 0x1p-24f;
+                        pb[l] = S1 + min(max((int)(ub >> 32), lo_b), hi_b);
+                        fb[l] = (float)((uint32_t)ub >> 8) * 0x1p-24f;
                     }
+                    const f32x2 a1 = pk2(fa[0], fa[1]), b1 = pk2(fb[0], fb[1]);
+                    const f32x2 a0 = sub2(one2, a1), b0 = sub2(one2, b1);
                     if (nsl == 2) {
 #pragma unroll
                         for (int kk = 0; kk < KR; ++kk) {
-#pragma unroll
-                            for (int jj = 0; jj < PG; ++jj) {
-                                float t = __fmaf_rn(a1[jj], qa[jj][kk * WS + 1], a0[jj] * qa[jj][kk * WS]);
-                                t = __fmaf_rn(b1[jj], qb[jj][kk * WS + 1], __fmaf_rn(b0[jj], qb[jj][kk * WS], t));
-                                kahan_add(U[g0 + jj][kk], C[g0 + jj][kk], t);
-                            }
+                            const int o = kk * WS;
+                            const f32x2 va0 = pk2(pa[0][o], pa[1][o]), va1 = pk2(pa[0][o + 1], pa[1][o + 1]);
+                            const f32x2 vb0 = pk2(pb[0][o], pb[1][o]), vb1 = pk2(pb[0][o + 1], pb[1][o + 1]);
+                            f32x2 t = fma2(a1, va1, mul2(a0, va0));
+                            t = fma2(b1, vb1, fma2(b0, vb0, t));
+                            kahan_add2(U[q][kk], C[q][kk], t);
                         }
                     } else {
 #pragma unroll
                         for (int kk = 0; kk < KR; ++kk) {
-#pragma unroll
-                            for (int jj = 0; jj < PG; ++jj) {
-                                const float t = __fmaf_rn(a1[jj], qa[jj][kk * WS + 1], a0[jj] * qa[jj][kk * WS]);
-                                kahan_add(U[g0 + jj][kk], C[g0 + jj][kk], t);
-                            }
+                            const int o = kk * WS;
+                            const f32x2 va0 = pk2(pa[0][o], pa[1][o]), va1 = pk2(pa[0][o + 1], pa[1][o + 1]);
+                            kahan_add2(U[q][kk], C[q][kk], fma2(a1, va1, mul2(a0, va0)));
                         }
                     }
                 }
@@ -271,14 +329,16 @@ __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __g
         if (active && c < wa) {
             const int64_t Ma = (int64_t)ha * wa;
 #pragma unroll
-            for (int j = 0; j < PB; ++j) {
-                if (j < np) {
-                    float* dst = ubuf + ((int64_t)(p0 + j) * hb + br) * Ma + c;
+            for (int q = 0; q < PB / 2; ++q) {
 #pragma unroll
-                    for (int kk = 0; kk < KR; ++kk) {
-                        const int row = band * g.BH + rp * KR + kk;
-                        if (row < ha) dst[(int64_t)row * wa] = U[j][kk] - C[j][kk];
-                    }
+                for (int kk = 0; kk < KR; ++kk) {
+                    const int row = band * g.BH + rp * KR + kk;
+                    float v[2];
+                    unpk2(sub2(U[q][kk], C[q][kk]), v[0], v[1]);
+#pragma unroll
+                    for (int l = 0; l < 2; ++l)
+                        if (2 * q + l < np && row < ha)
+                            ubuf[((int64_t)(p0 + 2 * q + l) * hb + br) * Ma + (int64_t)row * wa + c] = v[l];
                 }
             }
         }
@@ -456,6 +516,12 @@ int y_rows_per_cta(int hb) {
 
 size_t round256(size_t x) { return (x + 255) / 256 * 256; }
 
+// x-coordinate tables of one launch (at the end of the workspace)
+size_t xtables_bytes() {
+    return round256((size_t)kRefocusMaxPlanesPerLaunch * kBandThreads * sizeof(long long)) +
+           round256((size_t)kRefocusMaxPlanesPerLaunch * 2 * sizeof(long long));
+}
+
 }  // namespace
 
 bool refocus_supported(int ha, int wa, int hb, int wb) {
@@ -471,12 +537,12 @@ size_t refocus_ws_bytes(int ha, int wa, int hb, int wb, int n_planes) {
     const int per_launch = n_planes < kRefocusMaxPlanesPerLaunch ? n_planes : kRefocusMaxPlanesPerLaunch;
     size_t bytes = round256((size_t)per_launch * hb * Ma * sizeof(float));
     if (b.pitch) bytes += round256(Mb * ha * (size_t)b.pitch * sizeof(float));
-    return bytes;
+    return bytes + xtables_bytes();
 }
 
 int refocus_launches(int ha, int wa, int n_planes) {
     const int chunks = (n_planes + kRefocusMaxPlanesPerLaunch - 1) / kRefocusMaxPlanesPerLaunch;
-    return 2 * chunks + (band_plan(ha, wa).pitch ? 1 : 0);
+    return 3 * chunks + (band_plan(ha, wa).pitch ? 1 : 0);
 }
 
 cudaError_t refocus_run(const float* gamma_f32, int ha, int wa, int hb, int wb, const double* alpha,
@@ -516,6 +582,11 @@ cudaError_t refocus_run(const float* gamma_f32, int ha, int wa, int hb, int wb, 
             if (!make_f32_map(&tm, src, 3, dims, strides, box)) return cudaErrorInvalidValue;
         }
         const int RB = y_rows_per_cta(hb);
+        size_t tab_off = round256((size_t)per_launch * hb * Ma * sizeof(float));
+        if (b.pitch) tab_off += round256(Mb * ha * (size_t)b.pitch * sizeof(float));
+        long long* xcol = reinterpret_cast<long long*>(ws + tab_off);
+        long long* xang = reinterpret_cast<long long*>(
+            ws + tab_off + round256((size_t)kRefocusMaxPlanesPerLaunch * kBandThreads * sizeof(long long)));
         for (int p0 = 0; p0 < n_planes; p0 += kRefocusMaxPlanesPerLaunch) {
             const int np = n_planes - p0 < kRefocusMaxPlanesPerLaunch ? n_planes - p0 : kRefocusMaxPlanesPerLaunch;
             std::memset(&pb, 0, sizeof(pb));
@@ -538,11 +609,17 @@ cudaError_t refocus_run(const float* gamma_f32, int ha, int wa, int hb, int wb, 
             g.mode3d = b.mode3d;
             g.stages = b.stages;
             g.stage_bytes = (uint32_t)((size_t)b.BH * b.WS * sizeof(float));
+            g.xcol = xcol;
+            g.xang = xang;
             g.status = status;
             g.timeout_ns = timeout_ns;
+            refocus_xtables_kernel<<<(unsigned)((np * kBandThreads + 255) / 256), 256, 0, st>>>(pb, np, wa, wb, b.pad_l,
+                                                                                               xcol, xang);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
             const int64_t units = (int64_t)hb * g.n_pb * g.n_bands;
             const int grid = units < sm_count ? (int)units : sm_count;
-            cudaError_t e = launch_band(b, &tm, g, pb, ubuf, grid, st);
+            e = launch_band(b, &tm, g, pb, ubuf, grid, st);
             if (e != cudaSuccess) return e;
             YGeom y{ha, wa, hb, RB, p0};
             const size_t ysmem = (size_t)RB * hb * sizeof(YTap);

@@ -70,7 +70,8 @@ def test_refocus_workspace_layout():
     stacks run in chunks of 128 that reuse them), then, when Gamma's rows do not
     meet the staging alignment, a copy of Gamma with padded rows: to a multiple
     of 4 floats for rows up to 248 wide (2-D staging), of 16 floats above
-    (3-D staging in 16-float chunks)."""
+    (3-D staging in 16-float chunks); last the fixed-point x-coordinate tables
+    of one launch (128 planes x 512 column threads, and two values per plane)."""
     up = lambda n: -(-n // 256) * 256
     for ha, wa, hb, wb, P in [(33, 70, 7, 5, 7), (46, 95, 4, 4, 3), (17, 33, 5, 3, 2), (64, 64, 32, 32, 32),
                               (128, 128, 64, 64, 128), (12, 10, 3, 4, 200), (5, 300, 3, 2, 7), (9, 256, 2, 2, 3),
@@ -80,6 +81,7 @@ def test_refocus_workspace_layout():
         pitch = (wa + 3) // 4 * 4 if wa <= 248 else (wa + 15) // 16 * 16
         if pitch != wa:
             want += up(hb * wb * ha * pitch * 4)
+        want += up(128 * 512 * 8) + up(128 * 2 * 8)      # fixed-point x-coordinate tables of one launch
         assert ws == want, (ha, wa, hb, wb, P, ws, want)
     # rows wider than 512 are refused (0)
     assert cpi.cpi_refocus_workspace_size(4, 513, 2, 2, 1) == 0
