@@ -42,6 +42,7 @@ WORKLOADS = {
     "denoise": (None, 0),        # learned denoiser: training, inference and frames saved
     "paper_scale": (None, 0),    # 256x256 vs 256x256 binary, .bin-file blocks, Gamma 65536 x 65536
     "refocus4d": (None, 0),      # 4-D multilinear refocusing at the paper's RoIs and plane counts
+    "streaming": (None, 0),      # streamed acquisitions: sustained frames/s (also a key of the default line)
 }
 L2_FLUSH_BYTES = 512 << 20     # > 129 MB L2
 
@@ -292,7 +293,8 @@ def run_native(args, world, rank, local):
         for name, fn in (("spad_1bit", lambda: measure_single(args, "spad_1bit", world, rank, with_cpu=False,
                                                               with_errors=True, light=True)),
                          ("batched", lambda: run_batched(args, world, rank)),
-                         ("denoise", lambda: denoise_frames_saved(args, world, rank))):
+                         ("denoise", lambda: denoise_frames_saved(args, world, rank)),
+                         ("streaming", lambda: stream_rates(args, world, rank))):
             t0 = time.time()
             r = fn()
             if r is not None:
@@ -1043,6 +1045,80 @@ def run_paper_scale(args, world, rank):
     }
 
 
+# Streamed acquisitions (cpi_acq_*): blocks of frames pushed from pinned host
+# memory while earlier blocks accumulate; sustained frames per second against a
+# SPAD camera's ~10^5 binary frames per second (the paper's Section 1).
+SPAD_FRAME_RATE = 1.0e5
+STREAM_CASES = {
+    "spad_1bit": dict(block=8192, blocks=12),       # 64x64 vs 32x32 binary frames, 768 B each
+    "paper_roi": dict(block=16384, blocks=4),       # 256x256 vs 256x256 binary (.bin layout), 16 KiB each
+}
+
+
+def stream_rates(args, world, rank):
+    """Sustained frames/s of a streamed acquisition for each STREAM_CASES shape:
+    wall time from the first cpi_acq_push to the finalised Gamma (FP32,
+    slice-major) being ready."""
+    import torch
+
+    import paper_2407_20692_gb300 as cpi
+    import synth
+
+    cpi.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    res = {}
+    for name, c in STREAM_CASES.items():
+        n = c["block"] * c["blocks"]
+        if name == "spad_1bit":
+            acq = synth.frames.replace(synth.CONFIGS["spad_1bit"], n_frames=n, seed=555 + rank)
+            A, B = synth.generate(acq, dev)
+            fr, lay = synth.pack_side_by_side(A, B, 1)
+            del A, B
+        else:
+            fr = synth.bin_file_frames(n, 2407 + rank, p=0.1, device=dev)
+            lay = synth.bin_file_layout()
+        host = fr.cpu().pin_memory()
+        mk = lambda l: cpi.frames(fr, 1, l["height"], l["width"], l["x0"], l["y0"], l["row_stride"],
+                                  l["frame_stride_bytes"])
+        a, b = mk(lay["a"]), mk(lay["b"])
+        del fr
+        ma = lay["a"]["height"] * lay["a"]["width"]
+        mb = lay["b"]["height"] * lay["b"]["width"]
+        s_ab = torch.empty((ma, mb), dtype=torch.int64, device=dev)
+        s_a = torch.empty(ma, dtype=torch.int64, device=dev)
+        s_b = torch.empty(mb, dtype=torch.int64, device=dev)
+        g32 = torch.empty((mb, ma), dtype=torch.float32, device=dev)
+        ws = torch.empty(cpi.cpi_acq_workspace_size(a, b, c["block"]), dtype=torch.uint8, device=dev)
+
+        def run(nblocks):
+            h = cpi.cpi_acq_begin(a, b, c["block"], s_ab, s_a, s_b, ws)
+            for k in range(nblocks):
+                cpi.cpi_acq_push(h, host[k * c["block"]:(k + 1) * c["block"]], c["block"])
+            cpi.cpi_acq_finalize(h, None, g32)
+            cpi.cpi_acq_end(h)
+
+        run(1)                                    # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run(c["blocks"])
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if cpi.cpi_device_status() != 0:
+            raise RuntimeError("device status error in the streaming leg")
+        fps = n / _max_over_ranks(world, dt) * world
+        res[name] = {"frames": n, "block_frames": c["block"], "frame_bytes": int(host.shape[1]),
+                     "seconds": dt, "frames_per_s": fps, "vs_spad_rate": fps / SPAD_FRAME_RATE,
+                     "tops": 2.0 * ma * mb * n / dt / 1e12,
+                     "M_a": ma, "M_b": mb}
+        del s_ab, s_a, s_b, g32, ws, host
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return None
+    return {"metric": "sustained frames/s of a streamed acquisition (blocks pushed from pinned host memory "
+                      "while earlier blocks accumulate; Gamma finalised at the end)",
+            "spad_frame_rate": SPAD_FRAME_RATE, "cases": res}
+
+
 def refocus4d_planes(P):
     """Plane coefficients of the 4-D refocusing workload: alpha uniform in
     [0.5, 1.5], beta = 1 - alpha, gamma = (alpha - 1) / 2, delta = 1 - gamma."""
@@ -1307,7 +1383,7 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=3, help="oracle steps (or samples) timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="large_u8: skip the other workloads' keys (spad_1bit, batched, denoise)")
+                    help="large_u8: skip the other workloads' keys (spad_1bit, batched, denoise, streaming)")
     ap.add_argument("--denoise-train-seeds", type=int, default=None)
     ap.add_argument("--denoise-epochs", type=int, default=None)
     ap.add_argument("--save-model", default=None)
@@ -1327,6 +1403,8 @@ def main():
         line = run_paper_scale(args, world, rank)
     elif args.workload == "refocus4d":
         line = run_refocus4d(args, world, rank)
+    elif args.workload == "streaming":
+        line = stream_rates(args, world, rank)
     else:
         line = run_native(args, world, rank, local)
     if rank == 0 and line is not None:

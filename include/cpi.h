@@ -160,6 +160,54 @@ CPI_API cpi_status cpi_correlate_stage(int32_t stage, const cpi_frames *a, const
                                size_t workspace_bytes, cpi_stream stream);
 
 /* --------------------------------------------------------------------------
+ * Streamed acquisitions: Eq. (1) fed block by block from HOST memory while the
+ * frames are being acquired (the paper processes an acquisition in blocks of
+ * files, Section 4.1; a SPAD camera delivers ~10^5 binary frames per second,
+ * Section 1).  The acquisition keeps two staging buffers in the caller's
+ * workspace: the copy of one block to the GPU runs on the acquisition's own
+ * copy stream while the previous block is accumulated (as
+ * cpi_correlate_accumulate) on the caller's stream.  The running sums s_ab,
+ * s_a, s_b and the frame count are the whole state of the correlation:
+ * cpi_acq_sync makes them consistent (a checkpoint), and cpi_acq_begin with
+ * frames_done > 0 resumes from saved sums.
+ *
+ * Layout: a and b describe the two regions inside ONE frame buffer (their
+ * `data` is ignored; both must have the same frame_stride_bytes); a host block
+ * holds n consecutive frames of frame_stride_bytes each (e.g. the paper's .bin
+ * files: 512 frames of 256 x 512 bits, A left, B right).
+ *
+ * cpi_acq_workspace_size : DEVICE workspace bytes for blocks of up to
+ *        block_frames frames (0 on invalid layouts).
+ * cpi_acq_begin : creates the handle (host memory; one CUDA stream and four
+ *        events).  s_ab [M_a][M_b], s_a [M_a], s_b [M_b]: DEVICE int64,
+ *        caller-owned; zeroed on `stream` when frames_done == 0, else they must
+ *        hold the sums of the first frames_done frames.  `stream` is where the
+ *        accumulation and cpi_acq_finalize run.  Make calls on the device that
+ *        was current at cpi_acq_begin.
+ * cpi_acq_push : enqueues one block of 1 <= n_frames <= block_frames frames
+ *        from host memory (pinned memory lets the copy overlap).  Returns once
+ *        the copy of the PREVIOUS block has completed: the caller may overwrite
+ *        a host block as soon as the following cpi_acq_push (or cpi_acq_sync /
+ *        cpi_acq_end) has returned.  CPI_ERR_OVERFLOW once the total would
+ *        reach 2^31 frames.
+ * cpi_acq_frames : frames pushed so far (including frames_done), -1 on NULL.
+ * cpi_acq_finalize : enqueues Gamma of every frame pushed so far (as
+ *        cpi_correlate_finalize) on `stream`; the acquisition continues.
+ * cpi_acq_sync : waits for every copy and accumulation enqueued so far.
+ * cpi_acq_end : cpi_acq_sync, then releases the handle.
+ * -------------------------------------------------------------------------- */
+typedef struct cpi_acq cpi_acq;
+CPI_API size_t cpi_acq_workspace_size(const cpi_frames *a, const cpi_frames *b, int64_t block_frames);
+CPI_API cpi_status cpi_acq_begin(cpi_acq **out, const cpi_frames *a, const cpi_frames *b, int64_t block_frames,
+                                 int64_t *s_ab, int64_t *s_a, int64_t *s_b, int64_t frames_done, void *workspace,
+                                 size_t workspace_bytes, cpi_stream stream);
+CPI_API cpi_status cpi_acq_push(cpi_acq *acq, const void *host_frames, int64_t n_frames);
+CPI_API int64_t cpi_acq_frames(const cpi_acq *acq);
+CPI_API cpi_status cpi_acq_finalize(cpi_acq *acq, double *gamma, float *gamma_f32);
+CPI_API cpi_status cpi_acq_sync(cpi_acq *acq);
+CPI_API cpi_status cpi_acq_end(cpi_acq *acq);
+
+/* --------------------------------------------------------------------------
  * Refocusing (Section "CPI algorithm", item 2; Section 4.1, "Refocusing
  * Optimization": interpolation coordinates are computed on the fly inside the
  * refocusing kernel).  The paper gives no formula; this library implements the
@@ -179,9 +227,10 @@ CPI_API cpi_status cpi_correlate_stage(int32_t stage, const cpi_frames *a, const
  * Sums use compensated FP32 accumulation; coordinates are computed on the fly
  * in 32.32 fixed point from FP64 products, and each interpolation fraction is
  * rounded to 24 bits (the two weights are exact and sum to 1).  Requires
- * ha, wa, hb, wb >= 1, wa <= 512, (ha + 4) * (wa + 4) * 4 bytes <= 200 KiB,
- * hb*wb*ha*wa < 2^31 - 1024, gamma_f32 16-byte aligned; Gamma values must be
- * finite (a non-finite value may reach outputs through zero-weight taps).
+ * ha, wa, hb, wb >= 1, wa <= 512, hb <= 12800, hb*wb*ha < 2^31 - 1024,
+ * gamma_f32 16-byte aligned; Gamma values must be finite (a non-finite value
+ * may reach outputs through zero-weight taps).  Any image height: the spatial
+ * image is processed in bands of rows.
  * -------------------------------------------------------------------------- */
 CPI_API size_t cpi_refocus_workspace_size(int32_t ha, int32_t wa, int32_t hb, int32_t wb,
                                   int32_t n_planes);

@@ -22,7 +22,8 @@ __all__ = [
     "NOALLOC_SCRATCH_BYTES", "cpi_batch_item", "batch_items", "CPI_BATCH_GRAPH", "CPI_BATCH_TUNE", "CPI_BATCH_N128",
     "cpi_batch_workspace_size", "cpi_batch_correlate", "cpi_denoise_workspace_size", "cpi_denoise_grad",
     "cpi_denoise_adam", "DENOISER_PARAMS", "cpi_plane4", "plane4_array",
-    "cpi_refocus4d_workspace_size", "cpi_refocus4d",
+    "cpi_refocus4d_workspace_size", "cpi_refocus4d", "cpi_acq_workspace_size", "cpi_acq_begin", "cpi_acq_push",
+    "cpi_acq_frames", "cpi_acq_finalize", "cpi_acq_sync", "cpi_acq_end",
 ]
 CPI_BATCH_GRAPH, CPI_BATCH_TUNE, CPI_BATCH_N128 = 1, 2, 4
 DENOISER_PARAMS = 21409
@@ -38,7 +39,8 @@ EXPORTED = [
     "cpi_refocus_workspace_size", "cpi_refocus", "cpi_denoise", "cpi_device_status",
     "cpi_set_wait_timeout_ns", "cpi_selftest_wait_timeout", "cpi_correlate_noalloc",
     "cpi_batch_workspace_size", "cpi_batch_correlate", "cpi_denoise_workspace_size", "cpi_denoise_grad",
-    "cpi_denoise_adam", "cpi_refocus4d_workspace_size", "cpi_refocus4d",
+    "cpi_denoise_adam", "cpi_refocus4d_workspace_size", "cpi_refocus4d", "cpi_acq_workspace_size", "cpi_acq_begin",
+    "cpi_acq_push", "cpi_acq_frames", "cpi_acq_finalize", "cpi_acq_sync", "cpi_acq_end",
 ]
 NOALLOC_SCRATCH_BYTES = 32 * 1024 * 1024
 
@@ -130,6 +132,13 @@ def load(path: str | None = None):
         "cpi_correlate_noalloc": ([_F, _F, i64, _P, _P, _P, _P, _P, _P], st),
         "cpi_batch_workspace_size": ([ctypes.POINTER(cpi_batch_item), i32], sz),
         "cpi_batch_correlate": ([ctypes.POINTER(cpi_batch_item), i32, _P, sz, i32, _P], st),
+        "cpi_acq_workspace_size": ([_F, _F, i64], sz),
+        "cpi_acq_begin": ([ctypes.POINTER(_P), _F, _F, i64, _P, _P, _P, i64, _P, sz, _P], st),
+        "cpi_acq_push": ([_P, _P, i64], st),
+        "cpi_acq_frames": ([_P], i64),
+        "cpi_acq_finalize": ([_P, _P, _P], st),
+        "cpi_acq_sync": ([_P], st),
+        "cpi_acq_end": ([_P], st),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -320,3 +329,40 @@ def cpi_batch_correlate(items, workspace, flags=CPI_BATCH_GRAPH | CPI_BATCH_TUNE
 def cpi_selftest_wait_timeout(timeout_ns: int, stream=None):
     _check(load().cpi_selftest_wait_timeout(int(timeout_ns), _stream(stream)),
            "cpi_selftest_wait_timeout")
+
+
+# ----------------------------------------------------------------------------- streamed acquisitions
+
+def cpi_acq_workspace_size(a, b, block_frames) -> int:
+    return load().cpi_acq_workspace_size(ctypes.byref(a), ctypes.byref(b), int(block_frames))
+
+
+def cpi_acq_begin(a, b, block_frames, s_ab, s_a, s_b, workspace, frames_done=0, stream=None):
+    """Opens a streamed acquisition (include/cpi.h); returns its handle."""
+    h = ctypes.c_void_p()
+    _check(load().cpi_acq_begin(ctypes.byref(h), ctypes.byref(a), ctypes.byref(b), int(block_frames), _ptr(s_ab),
+                                _ptr(s_a), _ptr(s_b), int(frames_done), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream)), "cpi_acq_begin")
+    return h
+
+
+def cpi_acq_push(h, host_frames, n_frames):
+    """host_frames: a CPU tensor (pinned for an overlapped copy) or a host address."""
+    addr = host_frames.data_ptr() if hasattr(host_frames, "data_ptr") else int(host_frames)
+    _check(load().cpi_acq_push(h, ctypes.c_void_p(addr), int(n_frames)), "cpi_acq_push")
+
+
+def cpi_acq_frames(h) -> int:
+    return int(load().cpi_acq_frames(h))
+
+
+def cpi_acq_finalize(h, gamma, gamma_f32):
+    _check(load().cpi_acq_finalize(h, _ptr(gamma), _ptr(gamma_f32)), "cpi_acq_finalize")
+
+
+def cpi_acq_sync(h):
+    _check(load().cpi_acq_sync(h), "cpi_acq_sync")
+
+
+def cpi_acq_end(h):
+    _check(load().cpi_acq_end(h), "cpi_acq_end")

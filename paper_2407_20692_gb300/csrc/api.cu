@@ -652,6 +652,42 @@ cpi_status tuned_shape(const cpi_batch_item* items, int n, uint8_t* ws, DeviceIn
     return CPI_OK;
 }
 
+// ------------------------------------------------------------------ streamed acquisitions
+// A correlation fed block by block from host memory while it is acquired (the
+// paper processes its acquisitions in blocks of files; a SPAD camera delivers
+// ~10^5 frames per second).  Two staging buffers in the caller's workspace: the
+// copy of block k runs on the acquisition's own copy stream while block k - 1 is
+// accumulated on the caller's stream; the running sums are the whole state.
+struct Acquisition {
+    int dev = 0;
+    cpi_frames a{}, b{};              // layout of the two regions inside one frame
+    int64_t block_frames = 0, frame_bytes = 0;
+    int64_t *s_ab = nullptr, *s_a = nullptr, *s_b = nullptr;
+    uint8_t* staging[2] = {nullptr, nullptr};
+    uint8_t* ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t compute = nullptr;   // the caller's stream
+    cudaStream_t copy = nullptr;      // created by cpi_acq_begin
+    cudaEvent_t arrived[2] = {nullptr, nullptr}, consumed[2] = {nullptr, nullptr};
+    bool copied_once[2] = {false, false};
+    int next = 0;
+    int64_t n_done = 0;
+};
+
+size_t acq_staging_bytes(const cpi_frames* a, int64_t block_frames) {
+    return round_up((size_t)block_frames * (size_t)a->frame_stride_bytes, 256);
+}
+
+cpi_status acq_check_layout(const cpi_frames* a, const cpi_frames* b, int64_t block_frames) {
+    if (!a || !b || block_frames < 1) return CPI_ERR_INVALID_ARG;
+    if (a->frame_stride_bytes != b->frame_stride_bytes) return CPI_ERR_INVALID_ARG;
+    // validate with a placeholder data pointer (the regions' data come from the staging buffers)
+    cpi_frames ta = *a, tb = *b;
+    ta.data = tb.data = reinterpret_cast<const void*>(uintptr_t(256));
+    if (check_frames(&ta) != CPI_OK || check_frames(&tb) != CPI_OK) return CPI_ERR_INVALID_ARG;
+    return CPI_OK;
+}
+
 }  // namespace
 }  // namespace cpi
 
@@ -957,4 +993,134 @@ cpi_status cpi_selftest_wait_timeout(int64_t timeout_ns, cpi_stream stream) {
                                             reinterpret_cast<cudaStream_t>(stream)));
 }
 
+
+size_t cpi_acq_workspace_size(const cpi_frames* a, const cpi_frames* b, int64_t block_frames) {
+    if (acq_check_layout(a, b, block_frames) != CPI_OK) return 0;
+    cpi_frames ta = *a, tb = *b;
+    ta.data = tb.data = reinterpret_cast<const void*>(uintptr_t(256));
+    const size_t ws = cpi_correlate_workspace_size(&ta, &tb, block_frames);
+    if (ws == 0) return 0;
+    return 2 * acq_staging_bytes(a, block_frames) + ws;
+}
+
+cpi_status cpi_acq_begin(cpi_acq** out, const cpi_frames* a, const cpi_frames* b, int64_t block_frames,
+                         int64_t* s_ab, int64_t* s_a, int64_t* s_b, int64_t frames_done, void* workspace,
+                         size_t workspace_bytes, cpi_stream stream) {
+    if (!out) return CPI_ERR_INVALID_ARG;
+    *out = nullptr;
+    cpi_status st = acq_check_layout(a, b, block_frames);
+    if (st != CPI_OK) return st;
+    if (!s_ab || !s_a || !s_b || !aligned(s_ab, 16) || !aligned(s_a, 16) || !aligned(s_b, 16))
+        return CPI_ERR_INVALID_ARG;
+    if (frames_done < 0 || frames_done > ((int64_t)1 << 31) - 1) return CPI_ERR_INVALID_ARG;
+    const size_t need = cpi_acq_workspace_size(a, b, block_frames);
+    if (need == 0) return CPI_ERR_INVALID_ARG;
+    if (!workspace || workspace_bytes < need || !aligned(workspace, 256)) return CPI_ERR_WORKSPACE;
+    std::unique_ptr<Acquisition> q(new Acquisition);
+    if (cudaGetDevice(&q->dev) != cudaSuccess) return CPI_ERR_CUDA;
+    q->a = *a;
+    q->b = *b;
+    q->block_frames = block_frames;
+    q->frame_bytes = a->frame_stride_bytes;
+    q->s_ab = s_ab;
+    q->s_a = s_a;
+    q->s_b = s_b;
+    uint8_t* w = static_cast<uint8_t*>(workspace);
+    const size_t sb = acq_staging_bytes(a, block_frames);
+    q->staging[0] = w;
+    q->staging[1] = w + sb;
+    q->ws = w + 2 * sb;
+    q->ws_bytes = workspace_bytes - 2 * sb;
+    q->compute = reinterpret_cast<cudaStream_t>(stream);
+    q->n_done = frames_done;
+    if (cudaStreamCreateWithFlags(&q->copy, cudaStreamNonBlocking) != cudaSuccess) return CPI_ERR_CUDA;
+    for (int k = 0; k < 2; ++k)
+        if (cudaEventCreateWithFlags(&q->arrived[k], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&q->consumed[k], cudaEventDisableTiming) != cudaSuccess) {
+            cpi_acq_end(reinterpret_cast<cpi_acq*>(q.release()));
+            return CPI_ERR_CUDA;
+        }
+    if (frames_done == 0) {       // a new acquisition: the running sums start at zero
+        cudaStream_t cs = q->compute;
+        const int64_t ma = (int64_t)a->height * a->width, mb = (int64_t)b->height * b->width;
+        if (cudaMemsetAsync(s_ab, 0, (size_t)ma * mb * 8, cs) != cudaSuccess ||
+            cudaMemsetAsync(s_a, 0, (size_t)ma * 8, cs) != cudaSuccess ||
+            cudaMemsetAsync(s_b, 0, (size_t)mb * 8, cs) != cudaSuccess) {
+            cpi_acq_end(reinterpret_cast<cpi_acq*>(q.release()));
+            return CPI_ERR_CUDA;
+        }
+    }
+    *out = reinterpret_cast<cpi_acq*>(q.release());
+    return CPI_OK;
+}
+
+cpi_status cpi_acq_push(cpi_acq* handle, const void* host_frames, int64_t n_frames) {
+    Acquisition* q = reinterpret_cast<Acquisition*>(handle);
+    if (!q || !host_frames || n_frames < 1 || n_frames > q->block_frames) return CPI_ERR_INVALID_ARG;
+    if (q->n_done + n_frames > ((int64_t)1 << 31) - 1) return CPI_ERR_OVERFLOW;
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess || cur != q->dev) return CPI_ERR_INVALID_ARG;
+    const int k = q->next;
+    uint8_t* dst = q->staging[k];
+    // staging k is free once the block it held two pushes ago has been accumulated
+    if (q->copied_once[k] && cudaStreamWaitEvent(q->copy, q->consumed[k], 0) != cudaSuccess) return CPI_ERR_CUDA;
+    if (cudaMemcpyAsync(dst, host_frames, (size_t)n_frames * (size_t)q->frame_bytes, cudaMemcpyHostToDevice,
+                        q->copy) != cudaSuccess ||
+        cudaEventRecord(q->arrived[k], q->copy) != cudaSuccess ||
+        cudaStreamWaitEvent(q->compute, q->arrived[k], 0) != cudaSuccess)
+        return CPI_ERR_CUDA;
+    cpi_frames a = q->a, b = q->b;
+    a.data = dst;
+    b.data = dst;
+    static const int32_t stages[3] = {CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD};
+    const cpi_status st = correlate_common(stages, 3, &a, &b, n_frames, 1, q->s_ab, q->s_a, q->s_b, nullptr, nullptr,
+                                           q->ws, q->ws_bytes, reinterpret_cast<cpi_stream>(q->compute));
+    if (st != CPI_OK) return st;
+    if (cudaEventRecord(q->consumed[k], q->compute) != cudaSuccess) return CPI_ERR_CUDA;
+    q->copied_once[k] = true;
+    // the previous block's host buffer is free once its copy has arrived
+    const int prev = k ^ 1;
+    if (q->copied_once[prev] && cudaEventSynchronize(q->arrived[prev]) != cudaSuccess) return CPI_ERR_CUDA;
+    q->n_done += n_frames;
+    q->next = prev;
+    return CPI_OK;
+}
+
+int64_t cpi_acq_frames(const cpi_acq* handle) {
+    const Acquisition* q = reinterpret_cast<const Acquisition*>(handle);
+    return q ? q->n_done : -1;
+}
+
+cpi_status cpi_acq_finalize(cpi_acq* handle, double* gamma, float* gamma_f32) {
+    Acquisition* q = reinterpret_cast<Acquisition*>(handle);
+    if (!q || q->n_done < 1) return CPI_ERR_INVALID_ARG;
+    const int64_t ma = (int64_t)q->a.height * q->a.width, mb = (int64_t)q->b.height * q->b.width;
+    return cpi_correlate_finalize(q->s_ab, q->s_a, q->s_b, ma, mb, q->n_done, gamma, gamma_f32,
+                                  reinterpret_cast<cpi_stream>(q->compute));
+}
+
+cpi_status cpi_acq_sync(cpi_acq* handle) {
+    Acquisition* q = reinterpret_cast<Acquisition*>(handle);
+    if (!q) return CPI_ERR_INVALID_ARG;
+    if (cudaStreamSynchronize(q->copy) != cudaSuccess || cudaStreamSynchronize(q->compute) != cudaSuccess)
+        return CPI_ERR_CUDA;
+    return CPI_OK;
+}
+
+cpi_status cpi_acq_end(cpi_acq* handle) {
+    Acquisition* q = reinterpret_cast<Acquisition*>(handle);
+    if (!q) return CPI_ERR_INVALID_ARG;
+    cpi_status st = CPI_OK;
+    if (q->copy && cudaStreamSynchronize(q->copy) != cudaSuccess) st = CPI_ERR_CUDA;
+    if (q->compute && cudaStreamSynchronize(q->compute) != cudaSuccess) st = CPI_ERR_CUDA;
+    for (int k = 0; k < 2; ++k) {
+        if (q->arrived[k]) cudaEventDestroy(q->arrived[k]);
+        if (q->consumed[k]) cudaEventDestroy(q->consumed[k]);
+    }
+    if (q->copy) cudaStreamDestroy(q->copy);
+    delete q;
+    return st;
+}
+
 }  // extern "C"
+

@@ -328,14 +328,20 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
+                    // two 16-column loads in flight per wait (the segment drain
+                    // is on the MMA's critical path when segments are short)
 #pragma unroll
-                    for (int c = 0; c < kHalf / 16; ++c) {
-                        uint32_t r[16];
-                        tmem_ld_32x32b_x16(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN) + col0 + c * 16, r);
+                    for (int c = 0; c < kHalf / 16; c += 2) {
+                        uint32_t r0[16], r1[16];
+                        const uint32_t ta = tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN) + col0 + c * 16;
+                        tmem_ld_32x32b_x16(ta, r0);
+                        tmem_ld_32x32b_x16(ta + 16, r1);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            run[c][j] += __float_as_uint(__fadd_rn(__uint_as_float(r[j]), 8388608.0f)) - 0x4B000000u;
+                        for (int j = 0; j < 16; ++j) {
+                            run[c][j] += __float_as_uint(__fadd_rn(__uint_as_float(r0[j]), 8388608.0f)) - 0x4B000000u;
+                            run[c + 1][j] += __float_as_uint(__fadd_rn(__uint_as_float(r1[j]), 8388608.0f)) - 0x4B000000u;
+                        }
                     }
                     tc_fence_before();
                     mbar_arrive(&tempty[acc]);
