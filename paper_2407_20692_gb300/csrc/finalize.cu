@@ -1,5 +1,5 @@
-// Step a4: fold the exact int32 partial sums of the raw-moment step into the
-// int64 S_ab and apply Eq. (1):
+// Step a4: fold the exact partial sums of the raw-moment step (uint32, one per
+// frame chunk) into the int64 S_ab and apply Eq. (1):
 //     Gamma = (1/N) S_ab - (S_a/N)(S_b/N) = (N S_ab - S_a S_b) / N^2.
 // The numerator is computed exactly in int64 (the host refuses inputs for which
 // N^2 max(A) max(B) could reach 2^63), converted to double with one rounding
@@ -50,7 +50,8 @@ __global__ void __launch_bounds__(256) fold_kernel(const int32_t* __restrict__ p
             if (a < M && b < N) {
                 const int64_t idx = a * N + b;
                 int64_t s = accumulate ? s_ab[idx] : 0;
-                for (int c = 0; c < n_chunks; ++c) s += (int64_t)__ldg(partial + (int64_t)c * plane + idx);
+                for (int c = 0; c < n_chunks; ++c)
+                    s += (int64_t)(uint32_t)__ldg(partial + (int64_t)c * plane + idx);
                 if (write_sab) s_ab[idx] = s;
                 if (want_g) {
                     const int64_t sa = __ldg(s_a + a), sb = __ldg(s_b + b);

@@ -38,7 +38,7 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
 // One raw-moment problem: S_ab of one (A, B) pair, split into work units of
 // (frame chunk, 128 x BLOCK_N output tile).
 struct MomentsProblem {
-    int32_t* partial;        // [n_chunks][M][N] exact int32 partial sums
+    int32_t* partial;        // [n_chunks][M][N] exact partial sums (uint32 bit patterns)
     int32_t M, N;            // A pixels (rows), B pixels (columns)
     int32_t k_blocks;        // K blocks of 128 bytes per operand row
     int32_t kb_per_chunk;    // K blocks per frame chunk (one partial slot each)
@@ -46,6 +46,16 @@ struct MomentsProblem {
     int32_t unit_begin;      // first unit of this problem in the launch
     const uint32_t* vmax;    // BF16 path: largest A and B value of the call's frames (written by
                              // ingest), which set the exact FP32 segment length
+    // fused != 0 (a single frame chunk, not accumulating): the epilogue finishes
+    // Eq. (1) itself and writes s_ab (if non-null), gamma and gamma_f32 (if
+    // non-null) instead of the partial slot
+    int32_t fused;
+    int64_t* s_ab;
+    const int64_t* s_a;
+    const int64_t* s_b;
+    double* gamma;
+    float* gamma_f32;
+    GammaDiv gd;
 };
 
 // A persistent launch over the units of up to K problems (K = 1 for a single

@@ -78,8 +78,9 @@ def test_correlate_large_u8_sampled_rows():
 
 
 def test_exactness_adversarial_all_ones_and_max_counts():
-    """Partial sums at the exactness bounds: all-ones binary frames over more than
-    one 32768-frame chunk, and all-255 counts (products 65025) over 33000 frames."""
+    """Partial sums at the exactness bounds on a small output (whose frames are
+    split into many chunks to fill the GPU, then added by the fold): all-ones
+    binary frames, and all-255 counts (products 65025) over 33000 frames."""
     n = 32768 + 300
     ha, wa, hb, wb = 4, 8, 2, 8
     W = wa + wb
@@ -101,6 +102,44 @@ def test_exactness_adversarial_all_ones_and_max_counts():
     assert_exact(got, want)
 
 
+@pytest.mark.parametrize("n", [65536, 65600])
+def test_full_chunk_of_max_counts_closed_form(n):
+    """A frame chunk holds up to 65536 frames: with counts of 255 every partial
+    sum passes 2^31 (65536 x 255^2 = 4.26e9 < 2^32, kept as uint32).  2560 x 2048
+    outputs (160 tiles, so no extra frame split): n = 65536 is one chunk, finished
+    in the raw-moment epilogue; n = 65600 is two chunks, added by the fold.
+    A_i[a] = 255 - [a == 0][i % 3 == 0], B_i[b] = 255 - [b == 0][i % 5 == 0];
+    the sums follow by counting frames, Gamma from Python big integers."""
+    ha, wa, hb, wb = 40, 64, 32, 64
+    W = wa + wb
+    fr = torch.full((n, ha, W), 255, dtype=torch.uint8, device="cuda")
+    i = torch.arange(n, device="cuda")
+    fr[i % 3 == 0, 0, 0] = 254
+    fr[i % 5 == 0, 0, wa] = 254
+    la = dict(bits=8, height=ha, width=wa, x0=0, y0=0, row_stride=W, frame_stride_bytes=ha * W)
+    lb = dict(la, height=hb, width=wb, x0=wa)
+    got = gpu_correlate(fr, la, lb, n, want_f32=False)
+    ma, mb = ha * wa, hb * wb
+    c3, c5, c15 = (n + 2) // 3, (n + 4) // 5, (n + 14) // 15
+    sa = np.full(ma, 255 * n, dtype=np.int64)
+    sa[0] -= c3
+    sb = np.full(mb, 255 * n, dtype=np.int64)
+    sb[0] -= c5
+    sab = np.full((ma, mb), 255 * 255 * n, dtype=np.int64)
+    sab[0, :] -= 255 * c3
+    sab[:, 0] -= 255 * c5
+    sab[0, 0] += c15
+    assert np.array_equal(got["s_a"].numpy(), sa) and np.array_equal(got["s_b"].numpy(), sb)
+    assert np.array_equal(got["s_ab"].numpy(), sab)
+    assert int(sab.max()) > 2 ** 31
+    g = got["gamma"].numpy()
+    d = float(n) * float(n)
+    for (a, b) in [(0, 0), (0, 1), (1, 0), (1, 1), (ma - 1, mb - 1)]:
+        want = float(n * int(sab[a, b]) - int(sa[a]) * int(sb[b])) / d
+        assert g[a, b] == want, (a, b, g[a, b], want)
+    assert (g[1:, 1:] == 0.0).all()
+
+
 @pytest.mark.parametrize("top", [23, 91, 255])
 def test_segment_length_follows_the_recorded_value_range(top):
     """8-bit frames: the FP32 tensor-memory accumulator is folded into int32
@@ -108,8 +147,8 @@ def test_segment_length_follows_the_recorded_value_range(top):
     (from the maxima the ingest records).  Constant A = top and B = top except
     in every 16th frame (top - 1) make every tensor-core K step add an odd
     increment, so a segment that overran 2^23 would lose low bits in the
-    conversion and the sums would be wrong.  2048 x 1280 outputs keep the frame
-    chunk at the full 32768 frames (several segments per unit for every top)."""
+    conversion and the sums would be wrong.  2048 x 1280 outputs keep the 32768
+    frames in one chunk (several segments per unit for every top)."""
     n = 32768
     ha, wa, hb, wb = 32, 64, 20, 64
     W = wa + wb
