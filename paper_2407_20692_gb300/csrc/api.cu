@@ -242,10 +242,6 @@ cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm
 cpi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? CPI_OK : CPI_ERR_CUDA; }
 
 
-// A single frame chunk that does not accumulate: the raw-moment epilogue
-// finishes Eq. (1) and the fold stage has nothing left to do.
-bool fused_fold(const CorrPlan& pl, int accumulate) { return pl.n_chunks == 1 && !accumulate; }
-
 // vmax: the ingest's value maxima (BF16 path), which set the exact FP32
 // segment length on the device.
 void fill_problem(const CorrPlan& pl, int32_t* part, int unit_begin, MomentsProblem* P, const uint32_t* vmax) {
@@ -259,18 +255,6 @@ void fill_problem(const CorrPlan& pl, int32_t* part, int unit_begin, MomentsProb
     P->tiles_n = pl.tiles_n;
     P->unit_begin = unit_begin;
     P->vmax = pl.bf16 ? vmax : nullptr;
-    P->fused = 0;
-}
-
-void fill_fused(const CorrPlan& pl, int64_t* s_ab, const int64_t* s_a, const int64_t* s_b, double* gamma,
-                float* gamma_f32, MomentsProblem* P) {
-    P->fused = 1;
-    P->s_ab = s_ab;
-    P->s_a = s_a;
-    P->s_b = s_b;
-    P->gamma = gamma;
-    P->gamma_f32 = gamma_f32;
-    P->gd = make_gamma_div(pl.n);
 }
 
 cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const cpi_frames* b,
@@ -303,7 +287,6 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
         L.map_a[0] = tm_a;
         L.map_b[0] = tm_b;
         fill_problem(pl, part, 0, &L.prob[0], vmax);
-        if (fused_fold(pl, accumulate)) fill_fused(pl, s_ab, s_a, s_b, gamma, gamma_f32, &L.prob[0]);
         L.n_problems = 1;
         L.n_units = pl.n_units;
         L.status = dev->status;
@@ -311,7 +294,6 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
         return cuda_status(launch_moments(pl.bf16, pl.block_n, L, dev->sm_count, st));
     }
     if (stage == CPI_STAGE_FOLD) {
-        if (fused_fold(pl, accumulate)) return CPI_OK;      // finished by the raw-moment epilogue
         return cuda_status(launch_fold(part, pl.n_chunks, pl.Ma, pl.Mb, s_ab, accumulate, s_ab != nullptr ? 1 : 0,
                                        s_a, s_b, pl.n, gamma, gamma_f32, st));
     }
@@ -470,10 +452,6 @@ cpi_status launch_batch_moments(const cpi_batch_item* items, const BatchPlan& bp
                     return CPI_ERR_CUDA;
                 fill_problem(ip.pl, reinterpret_cast<int32_t*>(w + ip.pl.off_part), (int)units, &L->prob[np],
                              reinterpret_cast<const uint32_t*>(w + ip.pl.off_vmax));
-                if (fused_fold(ip.pl, 0)) {
-                    const cpi_batch_item& it = items[idx[g]];
-                    fill_fused(ip.pl, it.s_ab, it.s_a, it.s_b, it.gamma, it.gamma_f32, &L->prob[np]);
-                }
                 units += ip.pl.n_units;
                 if (units > 0x7fffffff) return CPI_ERR_UNSUPPORTED;
             }
@@ -484,6 +462,7 @@ cpi_status launch_batch_moments(const cpi_batch_item* items, const BatchPlan& bp
             if (launch_moments_group(bf16, bp.block_n, *L, dev->sm_count, st) != cudaSuccess) return CPI_ERR_CUDA;
         }
     }
+    (void)items;
     return CPI_OK;
 }
 

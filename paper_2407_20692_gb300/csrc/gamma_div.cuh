@@ -1,5 +1,4 @@
-// Correctly rounded Gamma of Eq. (1) from exact integer sums, shared by the fold
-// kernel and the fused epilogue of the raw-moment kernel.
+// Correctly rounded Gamma of Eq. (1) from exact integer sums (the fold kernel).
 //
 // Gamma = RN(RN(num) / RN(N * N)) with num = N S_ab - S_a S_b exact in int64:
 // the same two IEEE round-to-nearest-even operations a plain C evaluation of

@@ -46,16 +46,6 @@ struct MomentsProblem {
     int32_t unit_begin;      // first unit of this problem in the launch
     const uint32_t* vmax;    // BF16 path: largest A and B value of the call's frames (written by
                              // ingest), which set the exact FP32 segment length
-    // fused != 0 (a single frame chunk, not accumulating): the epilogue finishes
-    // Eq. (1) itself and writes s_ab (if non-null), gamma and gamma_f32 (if
-    // non-null) instead of the partial slot
-    int32_t fused;
-    int64_t* s_ab;
-    const int64_t* s_a;
-    const int64_t* s_b;
-    double* gamma;
-    float* gamma_f32;
-    GammaDiv gd;
 };
 
 // A persistent launch over the units of up to K problems (K = 1 for a single

@@ -19,9 +19,10 @@
 //     sums are uint32: every product is non-negative).
 // Each (frame chunk, 128 x 256 output tile) of a problem is one work unit; its
 // exact partial sum goes to its own slot of the workspace, and the fold step
-// adds the slots into int64 -- or, for a problem with a single frame chunk, the
-// epilogue finishes Eq. (1) itself (S_ab, Gamma, the FP32 copy) and the fold
-// step has nothing to do.  Integer addition is associative, so the
+// adds the slots into int64.  (Finishing Eq. (1) in this epilogue was measured
+// slower on GB300: the correctly rounded quotients keep the epilogue warps from
+// draining the next tile's segments, and the MMAs wait; the fold kernel spreads
+// that work over every SM instead.)  Integer addition is associative, so the
 // split over chunks, segments and CTAs never changes the result.  One launch
 // serves one problem (a correlation) or up to kMaxGroup problems of uneven
 // shapes (a batch): the persistent CTAs walk one list of units, each unit naming
@@ -77,54 +78,6 @@ __device__ __forceinline__ void store_row_chunk(const MomentsProblem& P, int chu
 #pragma unroll
         for (int j = 0; j < 32; ++j)
             if (nb + j < P.N) out[nb + j] = v[j];
-    }
-}
-
-// Eq. (1) finished in the epilogue (a problem with one frame chunk): for the 32
-// exact sums v of output row m, columns nb .. nb+31 (those < N), writes S_ab
-// (int64, when asked for), Gamma (FP64) and the slice-major FP32 copy.  Each
-// lane owns one row, so a warp's slice-major writes (32 consecutive rows of one
-// column) are coalesced; the row-major ones go out as 16-byte pairs.  The
-// numerator N S_ab - S_a S_b is exact in int64 (the host checks
-// N^2 max A max B < 2^63) and rounded once as in the fold kernel.
-__device__ __forceinline__ void store_row_fused(const MomentsProblem& P, int m, int nb, const uint32_t (&v)[32]) {
-    if (m >= P.M) return;
-    const int64_t sa = __ldg(P.s_a + m);
-    const bool want_g = P.gamma != nullptr || P.gamma_f32 != nullptr;
-    const bool pairs = (P.N & 1) == 0;
-    const size_t row = (size_t)m * (size_t)P.N;
-    // not unrolled: one pair of quotients at a time keeps the running sums of
-    // the other columns in registers (v is a small local array)
-#pragma unroll 1
-    for (int j = 0; j < 32; j += 2) {
-        const int n = nb + j;
-        if (n >= P.N) break;
-        const bool two = n + 1 < P.N;
-        const int64_t s0 = (int64_t)v[j], s1 = (int64_t)v[j + 1];
-        if (P.s_ab != nullptr) {
-            if (pairs && two) {
-                *reinterpret_cast<longlong2*>(P.s_ab + row + n) = make_longlong2(s0, s1);
-            } else {
-                P.s_ab[row + n] = s0;
-                if (two) P.s_ab[row + n + 1] = s1;
-            }
-        }
-        if (want_g) {
-            const double g0 = gamma_from_num(P.gd.n * s0 - sa * __ldg(P.s_b + n), P.gd);
-            const double g1 = two ? gamma_from_num(P.gd.n * s1 - sa * __ldg(P.s_b + n + 1), P.gd) : 0.0;
-            if (P.gamma != nullptr) {
-                if (pairs && two) {
-                    *reinterpret_cast<double2*>(P.gamma + row + n) = make_double2(g0, g1);
-                } else {
-                    P.gamma[row + n] = g0;
-                    if (two) P.gamma[row + n + 1] = g1;
-                }
-            }
-            if (P.gamma_f32 != nullptr) {
-                P.gamma_f32[(size_t)n * P.M + m] = double_to_float_rn(g0);
-                if (two) P.gamma_f32[(size_t)(n + 1) * P.M + m] = double_to_float_rn(g1);
-            }
-        }
     }
 }
 
@@ -349,17 +302,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     uint32_t r[32];
                     tmem_ld_32x32b_x32(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN) + col0 + c * 32, r);
                     tmem_ld_wait();
-                    if (P.fused) {
-                        uint32_t v[32];
+                    int32_t v[32];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = (uint32_t)__float2int_rn(__uint_as_float(r[j]));
-                        store_row_fused(P, m, n0 + c * 32, v);
-                    } else {
-                        int32_t v[32];
-#pragma unroll
-                        for (int j = 0; j < 32; ++j) v[j] = __float2int_rn(__uint_as_float(r[j]));
-                        store_row_chunk(P, chunk, m, n0 + c * 32, v);
-                    }
+                    for (int j = 0; j < 32; ++j) v[j] = __float2int_rn(__uint_as_float(r[j]));
+                    store_row_chunk(P, chunk, m, n0 + c * 32, v);
                 }
                 tc_fence_before();
                 mbar_arrive(&tempty[acc]);
@@ -403,23 +349,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (!ok) break;
 #pragma unroll
                 for (int c = 0; c < kHalf / 32; ++c) {
-                    if (P.fused) {
-                        uint32_t v[32];
+                    int32_t v[32];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            v[j] = run[2 * c][j];
-                            v[16 + j] = run[2 * c + 1][j];
-                        }
-                        store_row_fused(P, m, n0 + c * 32, v);
-                    } else {
-                        int32_t v[32];
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            v[j] = (int32_t)run[2 * c][j];
-                            v[16 + j] = (int32_t)run[2 * c + 1][j];
-                        }
-                        store_row_chunk(P, chunk, m, n0 + c * 32, v);
+                    for (int j = 0; j < 16; ++j) {
+                        v[j] = (int32_t)run[2 * c][j];
+                        v[16 + j] = (int32_t)run[2 * c + 1][j];
                     }
+                    store_row_chunk(P, chunk, m, n0 + c * 32, v);
                 }
             }
         }
