@@ -501,7 +501,7 @@ def _traffic(kernel_key, workload):
         return None
     with open(path) as f:
         table = json.load(f)
-    ent = table.get(kernel_key)
+    ent = table.get(f"{kernel_key}@{workload}")
     if not ent or ent.get("workload") != workload:
         return None
     h = hashlib.sha256()
