@@ -8,16 +8,13 @@
 // 2^24, and the schedule guarantees that:
 //   - binary frames: a frame chunk has at most 65536 frames, so every sum is
 //     <= 65536;
-//   - 8-bit values: the FP32 accumulator starts every segment at 2^23 and is
-//     folded into exact uint32 running sums (in the epilogue threads'
-//     registers) every S frames, S the largest multiple of 64 with
-//     S x max A x max B < 2^23 (at least 128 frames, since 128 x 255^2 < 2^23),
-//     so it stays in [2^23, 2^24), where FP32 holds every integer.  The maxima
-//     are the ones the ingest records for the call's frames, read on the
-//     device, so photon counts far below 255 fold rarely or never.  The fold is
-//     one integer add per value: the accumulator's bit pattern is 0x4B000000
-//     plus the segment's sum; the epilogue re-arms it with 2^23 (a tensor-memory
-//     store) before handing it back.  A chunk of
+//   - 8-bit values: the FP32 accumulator is folded into exact int32 running
+//     sums (kept in tensor memory beside it) every S frames, S the largest
+//     multiple of 64 with S x max A x max B < 2^23 (at least 128 frames, since
+//     128 x 255^2 < 2^23).  The maxima are the ones the ingest records for the
+//     call's frames, read on the device, so photon counts far below 255 fold
+//     rarely or never.  Below 2^23 the fold needs no float-to-integer
+//     conversion: f + 2^23 is exact with bit pattern 0x4B000000 + f.  A chunk of
 //     <= 65536 frames keeps each total below 65536 x 255^2 < 2^32 (the running
 //     sums are uint32: every product is non-negative).
 // Each (frame chunk, 128 x 256 output tile) of a problem is one work unit; its
@@ -234,10 +231,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const bool seg_end =
                         kBf16 ? ((local + 1) % kb_per_fold == 0 || kb + 1 == kb1) : (kb + 1 == kb1);
                     if (seg_start) {
-                        // BF16: the epilogue arms both accumulators once before the first
-                        // segment (one extra phase of tempty), so the wait is one phase later
-                        if (!mbar_wait_bounded(&tempty[acc], kBf16 ? acc_phase : acc_phase ^ 1, abort_flag, status,
-                                               tmo)) {
+                        if (!mbar_wait_bounded(&tempty[acc], acc_phase ^ 1, abort_flag, status, tmo)) {
                             ok = false;
                             break;
                         }
@@ -255,7 +249,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int k = 0; k < kRowBytes / 32; ++k) {
                         // advance the start address by 32 bytes (2 x 16-byte units) per MMA
                         umma_f32<kBf16>(d, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc,
-                                        (!kBf16 && seg_start && k == 0) ? 0u : 1u);
+                                        (seg_start && k == 0) ? 0u : 1u);
                     }
                     issued_any = true;
                     umma_commit(&empty[stage]);
@@ -289,7 +283,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         int acc = 0;
         uint32_t acc_phase = 0;
         bool ok = true;
-        bool armed = false;     // BF16: accumulators armed with 2^23
         for (int u = blockIdx.x; ok && u < L.n_units; u += gridDim.x) {
             const Unit w = decode_unit<K>(L, u);
             const MomentsProblem& P = L.prob[w.prob];
@@ -326,19 +319,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // after the last segment they go to the partial slot.
                 const int seg = seg_kb[w.prob];
                 const int nseg = (kb1 - kb0 + seg - 1) / seg;
-                if (!armed) {   // both accumulators start at 2^23 before the first segment
-#pragma unroll 1
-                    for (int a = 0; a < C::kAcc; ++a)
-#pragma unroll 1
-                        for (int c = 0; c < kHalf / 16; ++c)
-                            tmem_st_32x32b_x16_fill(tmem_base + lane_addr + (uint32_t)(a * C::kBlockN) + col0 + c * 16,
-                                                    0x4B000000u);
-                    tmem_st_wait();
-                    tc_fence_before();
-#pragma unroll
-                    for (int a = 0; a < C::kAcc; ++a) mbar_arrive(&tempty[a]);
-                    armed = true;
-                }
                 uint32_t run[kHalf / 16][16];
 #pragma unroll
                 for (int c = 0; c < kHalf / 16; ++c)
@@ -350,19 +330,15 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t tacc = tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN) + col0;
 #pragma unroll
                     for (int c = 0; c < kHalf / 16; ++c) {
                         uint32_t r[16];
-                        tmem_ld_32x32b_x16(tacc + c * 16, r);
+                        tmem_ld_32x32b_x16(tmem_base + lane_addr + (uint32_t)(acc * C::kBlockN) + col0 + c * 16, r);
                         tmem_ld_wait();
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) run[c][j] += r[j] - 0x4B000000u;
+                        for (int j = 0; j < 16; ++j)
+                            run[c][j] += __float_as_uint(__fadd_rn(__uint_as_float(r[j]), 8388608.0f)) - 0x4B000000u;
                     }
-                    // re-arm the accumulator with 2^23 for the segment after next
-#pragma unroll 1
-                    for (int c = 0; c < kHalf / 16; ++c) tmem_st_32x32b_x16_fill(tacc + c * 16, 0x4B000000u);
-                    tmem_st_wait();
                     tc_fence_before();
                     mbar_arrive(&tempty[acc]);
                     if (++acc == C::kAcc) {
