@@ -8,7 +8,8 @@
 //     FP8 E4M3 bytes (0x00 / 0x38 = 1.0), ingest_bits_kernel: a block of frames
 //     staged word-wise in shared memory, transposed 32 x 32 bits per warp;
 //   - any frames -> BF16 (integers 0..255 are exact; 1-bit frames that do not
-//     meet the above as E4M3), one CTA per tile of 32 pixels x 256 output bytes.
+//     meet the above as E4M3), one CTA per tile of 32 pixels x 256 frames (32
+//     frames per warp, one byte load per lane and frame, all in flight).
 // Frames at or beyond n_frames are written as 0, so every operand row is padded
 // to a whole number of CTA tiles.  The same pass adds the marginal sums
 // S_a = sum_i A_i (Eq. (1), second term) with exact int64 atomics.
@@ -30,7 +31,9 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
                                                      int64_t kstride_bytes, uint8_t* op_a,
                                                      uint8_t* op_b, int64_t* s_a, int64_t* s_b,
                                                      int tiles_a, uint32_t* vmax) {
-    constexpr int kFramesPerWarp = kBf16 ? 16 : 32;   // 32 operand bytes per pixel per warp
+    constexpr int kFramesPerWarp = 32;                // 32 frames per warp: 32 independent loads in flight per lane
+    constexpr int kRowBytes = ingest_row_bytes(kBf16);   // operand bytes per pixel per CTA (256 frames)
+    constexpr int kWords = kFramesPerWarp * (kBf16 ? 2 : 1) / 4;   // 32-bit words per lane
     const bool is_a = (int)blockIdx.x < tiles_a;
     const FramesDev d = is_a ? A : B;
     const int tile = is_a ? (int)blockIdx.x : (int)blockIdx.x - tiles_a;
@@ -39,7 +42,7 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
     const int64_t M = (int64_t)d.height * d.width;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    __shared__ __align__(16) uint8_t tile_s[kIngestPixels][kIngestRowBytes + 16];
+    __shared__ __align__(16) uint8_t tile_s[kIngestPixels][kRowBytes + 16];
     __shared__ long long part[8][32];
     __shared__ uint32_t wmax[8];
 
@@ -56,11 +59,11 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
 
     const int64_t f0 = (int64_t)blockIdx.y * (kFramesPerWarp * 8) + warp * kFramesPerWarp;
     long long sum = 0;
-    uint32_t w[8];
+    uint32_t w[kWords];
     uint32_t mx = 0;
     if constexpr (kBf16) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < kWords; ++j) {
             uint32_t lo = 0, hi = 0;
             const int64_t f = f0 + 2 * j;
             if (valid && f < n_frames) lo = load_pixel(d, base, sh, f);
@@ -86,9 +89,9 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
             w[j] = word;
         }
     }
-    uint4* dst = reinterpret_cast<uint4*>(&tile_s[lane][warp * 32]);
-    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    uint4* dst = reinterpret_cast<uint4*>(&tile_s[lane][warp * kWords * 4]);
+#pragma unroll
+    for (int q = 0; q < kWords / 4; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
     part[warp][lane] = sum;
     if constexpr (kBf16) {
         mx = __reduce_max_sync(0xffffffffu, mx);
@@ -104,17 +107,17 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
         if (m > *reinterpret_cast<volatile uint32_t*>(slot)) atomicMax(slot, m);
     }
 
-    // 32 rows x 256 bytes = 512 chunks of 16 bytes; consecutive threads write
+    // 32 rows x kRowBytes bytes in chunks of 16 bytes; consecutive threads write
     // consecutive chunks of one operand row.
+    constexpr int kChunks = kRowBytes / 16;
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < kIngestPixels * kChunks / 256; ++it) {
         const int idx = it * 256 + threadIdx.x;
-        const int row = idx >> 4, chunk = idx & 15;
+        const int row = idx / kChunks, chunk = idx % kChunks;
         const int64_t pp = (int64_t)tile * kIngestPixels + row;
         if (pp < M) {
             const uint4 v = *reinterpret_cast<const uint4*>(&tile_s[row][chunk * 16]);
-            *reinterpret_cast<uint4*>(op + pp * kstride_bytes + (int64_t)blockIdx.y * kIngestRowBytes +
-                                      chunk * 16) = v;
+            *reinterpret_cast<uint4*>(op + pp * kstride_bytes + (int64_t)blockIdx.y * kRowBytes + chunk * 16) = v;
         }
     }
     if (warp == 0 && valid) {
@@ -290,7 +293,8 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
         }
         return cudaSuccess;
     }
-    const int64_t frame_tiles = kstride_bytes / kIngestRowBytes;
+    const int64_t row_bytes = ingest_row_bytes(bf16);
+    const int64_t frame_tiles = kstride_bytes / row_bytes;
     if (frame_tiles > 65535) {
         // grid.y limit: split the frame range over several launches
         for (int64_t t0 = 0; t0 < frame_tiles; t0 += 65535) {
@@ -303,13 +307,13 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
             dim3 grid(tiles_a + tiles_b, (unsigned)nt);
             if (bf16)
                 ingest_kernel<true><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes,
-                                                          op_a + t0 * kIngestRowBytes,
-                                                          op_b + t0 * kIngestRowBytes, s_a, s_b,
+                                                          op_a + t0 * row_bytes,
+                                                          op_b + t0 * row_bytes, s_a, s_b,
                                                           tiles_a, vmax);
             else
                 ingest_kernel<false><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes,
-                                                           op_a + t0 * kIngestRowBytes,
-                                                           op_b + t0 * kIngestRowBytes, s_a, s_b,
+                                                           op_a + t0 * row_bytes,
+                                                           op_b + t0 * row_bytes, s_a, s_b,
                                                            tiles_a, nullptr);
         }
         return cudaGetLastError();

@@ -349,7 +349,8 @@ __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __g
 // out[p][r][c] = sum over br of wy0 U[p][br][yo][c] + wy1 U[p][br][yo + 1][c],
 // Kahan-added over br in order.  CTA = (RB output rows, plane); the y taps of its
 // rows for every angular row are formed first (FP64 -> 32.32 fixed point) into
-// shared memory.
+// shared memory.  Rows whose width is a multiple of 4 are read as 16-byte
+// vectors (four adjacent outputs per thread).
 constexpr int kYThreads = 256;
 struct YGeom {
     int32_t ha, wa, hb, RB;
@@ -373,6 +374,32 @@ __global__ void __launch_bounds__(kYThreads) refocus_ystage_kernel(const float* 
     __syncthreads();
     const int64_t Ma = (int64_t)ha * wa;
     const float* src = ubuf + (int64_t)p * hb * Ma;
+    if ((wa & 3) == 0) {   // four adjacent columns per thread, 16-byte loads
+        const int wq = wa >> 2;
+        for (int idx = threadIdx.x; idx < RB * wq; idx += kYThreads) {
+            const int rr = idx / wq, c = (idx - rr * wq) * 4;
+            const int r = r0 + rr;
+            if (r >= ha) continue;
+            const YTap* t = ytab + rr * hb;
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f}, cmp[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+            const float* s = src + c;
+#pragma unroll 4
+            for (int br = 0; br < hb; ++br) {
+                const YTap y = t[br];
+                const float4 v0 = __ldg(reinterpret_cast<const float4*>(s + y.o0));
+                const float4 v1 = __ldg(reinterpret_cast<const float4*>(s + y.o1));
+                kahan_add(acc[0], cmp[0], __fmaf_rn(y.w1, v1.x, y.w0 * v0.x));
+                kahan_add(acc[1], cmp[1], __fmaf_rn(y.w1, v1.y, y.w0 * v0.y));
+                kahan_add(acc[2], cmp[2], __fmaf_rn(y.w1, v1.z, y.w0 * v0.z));
+                kahan_add(acc[3], cmp[3], __fmaf_rn(y.w1, v1.w, y.w0 * v0.w));
+                s += Ma;
+            }
+            float* o = out + ((int64_t)(g.plane_offset + p) * ha + r) * wa + c;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[k] = acc[k] - cmp[k];
+        }
+        return;
+    }
     for (int idx = threadIdx.x; idx < RB * wa; idx += kYThreads) {
         const int rr = idx / wa, c = idx - rr * wa;
         const int r = r0 + rr;
