@@ -294,7 +294,8 @@ def run_native(args, world, rank, local):
                                                               with_errors=True, light=True)),
                          ("batched", lambda: run_batched(args, world, rank)),
                          ("denoise", lambda: denoise_frames_saved(args, world, rank)),
-                         ("streaming", lambda: stream_rates(args, world, rank))):
+                         ("streaming", lambda: stream_rates(args, world, rank)),
+                         ("refocus2d", lambda: refocus2d_paper_rois(args, world, rank))):
             t0 = time.time()
             r = fn()
             if r is not None:
@@ -1119,6 +1120,55 @@ def stream_rates(args, world, rank):
             "spad_frame_rate": SPAD_FRAME_RATE, "cases": res}
 
 
+def refocus2d_paper_rois(args, world, rank):
+    """2-D refocusing (cpi_refocus) at the RoIs and plane counts of the paper's
+    refocusing benchmark (Section 4.2): 128x128 vs 128x128 (Gamma 16384 x 16384)
+    with 100 and 261 planes, and 256x256 vs 256x256 (Gamma 65536 x 65536, 17 GB
+    FP32) with 100 planes.  Gamma is a seeded random FP32 array (the kernels'
+    cost does not depend on its values); uniformly spaced planes."""
+    import torch
+
+    import paper_2407_20692_gb300 as cpi
+    import synth
+
+    cpi.load()
+    dev = torch.device("cuda", torch.cuda.current_device())
+    res = {}
+    peaks, _ = _peaks()
+    for side, P in ((128, 100), (128, 261), (256, 100)):
+        M = side * side
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(2692 + side)
+        g32 = torch.randn((M, M), generator=gen, device=dev, dtype=torch.float32)
+        alpha, beta = synth.uniform_planes(P)
+        planes = cpi.plane_array(alpha, beta)
+        out = torch.empty((P, side, side), dtype=torch.float32, device=dev)
+        ws = torch.empty(cpi.cpi_refocus_workspace_size(side, side, side, side, P), dtype=torch.uint8, device=dev)
+        cpi.cpi_refocus(g32, side, side, side, side, planes, out, ws)
+        torch.cuda.synchronize()
+        reps = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            cpi.cpi_refocus(g32, side, side, side, side, planes, out, ws)
+        e1.record()
+        torch.cuda.synchronize()
+        if cpi.cpi_device_status() != 0:
+            raise RuntimeError("device status error")
+        ms = e0.elapsed_time(e1) / reps
+        samples = P * M * M
+        res[f"{side}x{side}_P{P}"] = {
+            "ms": ms, "planes_per_s": P / (ms / 1e3),
+            "per_plane_gamma_gbs": samples * 4 / (ms / 1e3) / 1e9,
+            "lsu_frac": samples * 8 / (ms / 1e3) / (SM_COUNT * SMEM_BYTES_PER_CLK *
+                                                    peaks.get("sm_max_mhz", 2070.0) * 1e6)}
+        del g32, ws, out
+        torch.cuda.empty_cache()
+    if rank != 0:
+        return None
+    return {"metric": "2-D refocusing planes/s at the paper's refocusing RoIs (seeded random Gamma)", "cases": res}
+
+
 def refocus4d_planes(P):
     """Plane coefficients of the 4-D refocusing workload: alpha uniform in
     [0.5, 1.5], beta = 1 - alpha, gamma = (alpha - 1) / 2, delta = 1 - gamma."""
@@ -1383,7 +1433,8 @@ def main():
     ap.add_argument("--cpu-reps", type=int, default=3, help="oracle steps (or samples) timed for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="large_u8: skip the other workloads' keys (spad_1bit, batched, denoise, streaming)")
+                    help="large_u8: skip the other workloads' keys (spad_1bit, batched, denoise, streaming, "
+                         "refocus2d)")
     ap.add_argument("--denoise-train-seeds", type=int, default=None)
     ap.add_argument("--denoise-epochs", type=int, default=None)
     ap.add_argument("--save-model", default=None)

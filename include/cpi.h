@@ -291,7 +291,10 @@ CPI_API cpi_status cpi_refocus4d(const float *gamma_f32, int32_t ha, int32_t wa,
  *   batch's operands: the frame-chunk split (1, 2 or 4 times the minimum)
  *   times the output tile width (128 x 256 or 128 x 128); this first call
  *   synchronises the stream.  Without it: split 1 and 128 x 256 tiles, or
- *   128 x 128 tiles with CPI_BATCH_N128.
+ *   128 x 128 tiles with CPI_BATCH_N128.  When the environment variable
+ *   CPI_TUNE_CACHE names a file, tuned decompositions are read from it and
+ *   appended to it (one text line per batch shape and GPU model), so a later
+ *   process skips the timing.
  * -------------------------------------------------------------------------- */
 typedef struct cpi_batch_item {
     cpi_frames a, b;

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <mutex>
@@ -596,9 +597,56 @@ struct BatchCache {
 BatchCache g_batch;
 constexpr size_t kMaxGraphs = 16;
 
+// Persistent tuner cache: when the environment variable CPI_TUNE_CACHE names a
+// file, tuned decompositions are looked up there and appended to it, one line
+// per (batch shape, GPU model): "<key in hex> <split> <tile width>".  The key
+// hashes the items' shapes with the GPU's name, SM count and compute
+// capability, so a cache file can be shared by processes and boxes.
+uint64_t tune_file_key(const cpi_batch_item* items, int n, int dev) {
+    uint64_t h = batch_shape_key(items, n, 0);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+        h = fnv(h, prop.name, strnlen(prop.name, sizeof(prop.name)));
+        h = fnv(h, &prop.multiProcessorCount, sizeof(prop.multiProcessorCount));
+        h = fnv(h, &prop.major, sizeof(prop.major));
+        h = fnv(h, &prop.minor, sizeof(prop.minor));
+    }
+    return h;
+}
+
+bool tune_file_lookup(uint64_t key, BatchShape* out) {
+    const char* path = std::getenv("CPI_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return false;
+    unsigned long long k = 0;
+    int split = 0, bn = 0;
+    bool found = false;
+    while (std::fscanf(f, "%llx %d %d", &k, &split, &bn) == 3) {
+        if (k == key) {
+            for (const BatchShape& c : kBatchCandidates)
+                if (c.split == split && c.block_n == bn) {
+                    *out = c;
+                    found = true;
+                }
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+void tune_file_store(uint64_t key, BatchShape s) {
+    const char* path = std::getenv("CPI_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "a");
+    if (!f) return;
+    std::fprintf(f, "%016llx %d %d\n", (unsigned long long)key, s.split, s.block_n);
+    std::fclose(f);
+}
+
 // Decomposition of the grouped raw-moment launches (frame-chunk split x output
 // tile width), tuned on first use of a batch shape by timing every candidate on
-// the batch's own operands.
+// the batch's own operands (or read from the CPI_TUNE_CACHE file).
 cpi_status tuned_shape(const cpi_batch_item* items, int n, uint8_t* ws, DeviceInfo* dev, int dev_id,
                        cudaStream_t st, BatchShape* shape_out) {
     const uint64_t key = batch_shape_key(items, n, dev_id);
@@ -607,6 +655,12 @@ cpi_status tuned_shape(const cpi_batch_item* items, int n, uint8_t* ws, DeviceIn
         auto it = g_batch.tuned.find(key);
         if (it != g_batch.tuned.end()) {
             *shape_out = it->second;
+            return CPI_OK;
+        }
+        BatchShape cached;
+        if (tune_file_lookup(tune_file_key(items, n, dev_id), &cached)) {
+            g_batch.tuned[key] = cached;
+            *shape_out = cached;
             return CPI_OK;
         }
     }
@@ -651,6 +705,7 @@ cpi_status tuned_shape(const cpi_batch_item* items, int n, uint8_t* ws, DeviceIn
     if (s != CPI_OK) return s;
     std::lock_guard<std::mutex> lk(g_batch.mu);
     g_batch.tuned[key] = best_shape;
+    tune_file_store(tune_file_key(items, n, dev_id), best_shape);
     *shape_out = best_shape;
     return CPI_OK;
 }

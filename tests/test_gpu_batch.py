@@ -190,3 +190,67 @@ def test_batch_rejects_bad_items():
     with pytest.raises(cpi.CpiError) as e:
         cpi.cpi_batch_correlate(arr, torch.empty(1024, dtype=torch.uint8, device="cuda"))
     assert e.value.code == 1
+
+
+_TUNE_CHILD = r"""
+import os, sys, json
+sys.path.insert(0, {root!r}); sys.path.insert(0, {tests!r})
+import torch
+import paper_2407_20692_gb300 as cpi
+from test_gpu_batch import _tune_batch
+items, keep = _tune_batch()
+arr = cpi.batch_items(items)
+ws = torch.empty(cpi.cpi_batch_workspace_size(arr), dtype=torch.uint8, device="cuda")
+cpi.cpi_batch_correlate(arr, ws, flags=cpi.CPI_BATCH_TUNE)
+torch.cuda.synchronize()
+print(json.dumps([int(e["s_ab"].sum()) for e in items]))
+"""
+
+
+def _tune_batch():
+    """Three acquisitions of shapes no other test uses (a fresh tuner key)."""
+    items, keep = [], []
+    for k, (sa, sb, n) in enumerate([(27, 13, 1300), (19, 11, 900), (35, 21, 2100)]):
+        acq = synth.Acquisition(sa, sb, n, 1.5, "poisson8", seed=4400 + k)
+        A, B = synth.generate(acq, "cuda")
+        fr, lay = synth.pack_side_by_side(A, B, 8)
+        ma, mb = sa * sa, sb * sb
+        items.append(dict(a=desc(fr, lay["a"]), b=desc(fr, lay["b"]), n_frames=n,
+                          s_ab=torch.empty((ma, mb), dtype=torch.int64, device="cuda"),
+                          s_a=torch.empty(ma, dtype=torch.int64, device="cuda"),
+                          s_b=torch.empty(mb, dtype=torch.int64, device="cuda"),
+                          gamma=None, gamma_f32=None, planes=None, refocus_out=None))
+        keep.append(fr)
+    return items, keep
+
+
+def test_tuner_cache_file(tmp_path, monkeypatch):
+    """CPI_TUNE_CACHE: the first tuned call of a batch shape appends one line
+    (key, frame-chunk split, tile width); a second process with the same shapes
+    reads it instead of timing again (the file keeps one line) and gets the same
+    sums."""
+    import json
+    import os
+    import subprocess
+    import sys
+
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("CPI_TUNE_CACHE", str(path))
+    items, keep = _tune_batch()
+    arr = cpi.batch_items(items)
+    ws = torch.empty(cpi.cpi_batch_workspace_size(arr), dtype=torch.uint8, device="cuda")
+    cpi.cpi_batch_correlate(arr, ws, flags=cpi.CPI_BATCH_TUNE)
+    torch.cuda.synchronize()
+    lines = path.read_text().split("\n")
+    lines = [ln for ln in lines if ln.strip()]
+    assert len(lines) == 1
+    key, split, width = lines[0].split()
+    assert int(key, 16) > 0 and int(split) in (1, 2, 4) and int(width) in (128, 256)
+    want = [int(e["s_ab"].sum()) for e in items]
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = _TUNE_CHILD.format(root=root, tests=os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600,
+                       env=dict(os.environ, CPI_TUNE_CACHE=str(path)))
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert json.loads(r.stdout.strip().splitlines()[-1]) == want
+    assert len([ln for ln in path.read_text().split("\n") if ln.strip()]) == 1
