@@ -170,12 +170,16 @@ __global__ void __launch_bounds__(256) refocus_xtables_kernel(const PlaneBlock p
     }
 }
 
-template <int WS, int KR, int PB>
-__global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __grid_constant__ CUtensorMap tm,
-                                                                       const BandGeom g, const PlaneBlock pl,
-                                                                       float* __restrict__ ubuf) {
-    constexpr int NW = kBandThreads / 32;
-    static_assert(PB % 2 == 0, "planes are processed in pairs");
+// PT planes per thread, G groups of kBandThreads threads per CTA: a unit holds
+// PB = PT * G planes, group g taking planes g * PT .. g * PT + PT - 1 of it, so
+// every staged value serves PB planes while each thread keeps the sums of PT.
+template <int WS, int KR, int PT, int G>
+__global__ void __launch_bounds__(kBandThreads * G, 1) refocus_band_kernel(const __grid_constant__ CUtensorMap tm,
+                                                                           const BandGeom g, const PlaneBlock pl,
+                                                                           float* __restrict__ ubuf) {
+    constexpr int NW = kBandThreads * G / 32;
+    constexpr int PB = PT * G;
+    static_assert(PT % 2 == 0, "planes are processed in pairs");
     extern __shared__ __align__(128) float sm_raw[];
     float* const buf0 =
         sm_raw + (((128u - (static_cast<uint32_t>(__cvta_generic_to_shared(sm_raw)) & 127u)) & 127u) >> 2);
@@ -186,7 +190,9 @@ __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __g
     const int stages = g.stages;
     const int slice_f = (g.BH * WS + 31) & ~31;    // floats per stage buffer (128-byte multiple)
     const int tid = threadIdx.x, lane = tid & 31;
-    const int c = tid % g.cwt, rp = tid / g.cwt;
+    const int grp = G > 1 ? tid / kBandThreads : 0;
+    const int tg = G > 1 ? tid - grp * kBandThreads : tid;
+    const int c = tg % g.cwt, rp = tg / g.cwt;
     const bool active = rp < g.R;
     const int per_br = g.n_pb * g.n_bands;
     const int n_units = hb * per_br;
@@ -230,17 +236,17 @@ __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __g
         // running coordinate of this column at angular column bc (from bc = 0):
         // the column's part (with the 24-bit rounding bias and the staging pad)
         // plus the angular part, stepped by dB per angular column
-        long long X[PB], dB[PB];
+        long long X[PT], dB[PT];
 #pragma unroll
-        for (int j = 0; j < PB; ++j) {
-            const int pj = p0 + min(j, np - 1);
+        for (int j = 0; j < PT; ++j) {
+            const int pj = p0 + min(grp * PT + j, np - 1);
             X[j] = __ldg(g.xcol + (size_t)pj * kBandThreads + c) + __ldg(g.xang + 2 * pj);
             dB[j] = __ldg(g.xang + 2 * pj + 1);
         }
         // sums of plane pairs (2q, 2q + 1) in the two lanes of a packed register
-        f32x2 U[PB / 2][KR], C[PB / 2][KR];
+        f32x2 U[PT / 2][KR], C[PT / 2][KR];
 #pragma unroll
-        for (int q = 0; q < PB / 2; ++q)
+        for (int q = 0; q < PT / 2; ++q)
 #pragma unroll
             for (int kk = 0; kk < KR; ++kk) U[q][kk] = C[q][kk] = 0ull;
         for (int bc0 = 0; bc0 < wb; bc0 += 2) {
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __g
                 // one plane pair at a time: its taps live in registers while its
                 // rows are summed (lane l of every packed value: plane 2q + l)
 #pragma unroll
-                for (int q = 0; q < PB / 2; ++q) {
+                for (int q = 0; q < PT / 2; ++q) {
                     const float* pa[2];
                     const float* pb[2];
                     float fa[2], fb[2];
@@ -329,16 +335,18 @@ __global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __g
         if (active && c < wa) {
             const int64_t Ma = (int64_t)ha * wa;
 #pragma unroll
-            for (int q = 0; q < PB / 2; ++q) {
+            for (int q = 0; q < PT / 2; ++q) {
 #pragma unroll
                 for (int kk = 0; kk < KR; ++kk) {
                     const int row = band * g.BH + rp * KR + kk;
                     float v[2];
                     unpk2(sub2(U[q][kk], C[q][kk]), v[0], v[1]);
 #pragma unroll
-                    for (int l = 0; l < 2; ++l)
-                        if (2 * q + l < np && row < ha)
-                            ubuf[((int64_t)(p0 + 2 * q + l) * hb + br) * Ma + (int64_t)row * wa + c] = v[l];
+                    for (int l = 0; l < 2; ++l) {
+                        const int j = grp * PT + 2 * q + l;
+                        if (j < np && row < ha)
+                            ubuf[((int64_t)(p0 + j) * hb + br) * Ma + (int64_t)row * wa + c] = v[l];
+                    }
                 }
             }
         }
@@ -507,13 +515,13 @@ cudaError_t set_smem_attr(K kernel, int slot, size_t bytes) {
     return cudaSuccess;
 }
 
-template <int WS, int KR, int PB>
+template <int WS, int KR, int PT, int G = 1>
 cudaError_t launch_band_t(const CUtensorMap* tm, const BandGeom& g, const PlaneBlock& pl, float* ubuf, size_t smem,
                           int grid, cudaStream_t st, int slot) {
-    auto kern = refocus_band_kernel<WS, KR, PB>;
+    auto kern = refocus_band_kernel<WS, KR, PT, G>;
     cudaError_t e = set_smem_attr(kern, slot, kSmemCap);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kBandThreads, smem, st>>>(*tm, g, pl, ubuf);
+    kern<<<grid, kBandThreads * G, smem, st>>>(*tm, g, pl, ubuf);
     return cudaGetLastError();
 }
 
