@@ -28,8 +28,12 @@ namespace cpi {
 namespace {
 
 constexpr int kTile = 32;
+constexpr int kRowsPerThread = kTile / 8;
 
-__global__ void __launch_bounds__(256) fold_kernel(const int32_t* __restrict__ partial,
+// CTA = 32 x 32 entries (32 x 8 threads, 4 rows each).  Every load of a
+// thread's 4 entries is issued before any of them is used, so their latencies
+// overlap; then the 4 quotients are formed and stored.
+__global__ void __launch_bounds__(256, 4) fold_kernel(const int32_t* __restrict__ partial,
                                                    int n_chunks, int64_t M, int64_t N,
                                                    int64_t* s_ab, int accumulate, int write_sab,
                                                    const int64_t* __restrict__ s_a,
@@ -42,21 +46,32 @@ __global__ void __launch_bounds__(256) fold_kernel(const int32_t* __restrict__ p
     const bool want_g = gamma != nullptr || gamma_f32 != nullptr;
     const int64_t plane = M * N;
     const int64_t row_tiles = (M + kTile - 1) / kTile;
+    const int64_t sb = (want_g && b < N) ? __ldg(s_b + b) : 0;
     for (int64_t rt = blockIdx.y; rt < row_tiles; rt += gridDim.y) {
         const int64_t a0 = rt * kTile;
+        int64_t sum[kRowsPerThread], sa[kRowsPerThread];
 #pragma unroll
-        for (int k = 0; k < kTile / 8; ++k) {
+        for (int k = 0; k < kRowsPerThread; ++k) {
+            const int64_t a = a0 + ty + 8 * k;
+            sum[k] = (accumulate && a < M && b < N) ? s_ab[a * N + b] : 0;
+            sa[k] = (want_g && a < M) ? __ldg(s_a + a) : 0;
+        }
+        for (int c = 0; c < n_chunks; ++c) {
+#pragma unroll
+            for (int k = 0; k < kRowsPerThread; ++k) {
+                const int64_t a = a0 + ty + 8 * k;
+                if (a < M && b < N) sum[k] += (int64_t)(uint32_t)__ldg(partial + (int64_t)c * plane + a * N + b);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kRowsPerThread; ++k) {
             const int64_t a = a0 + ty + 8 * k;
             if (a < M && b < N) {
                 const int64_t idx = a * N + b;
-                int64_t s = accumulate ? s_ab[idx] : 0;
-                for (int c = 0; c < n_chunks; ++c)
-                    s += (int64_t)(uint32_t)__ldg(partial + (int64_t)c * plane + idx);
-                if (write_sab) s_ab[idx] = s;
+                if (write_sab) s_ab[idx] = sum[k];
                 if (want_g) {
-                    const int64_t sa = __ldg(s_a + a), sb = __ldg(s_b + b);
-                    const double g =
-                        wide ? gamma_from_sums_wide(s, sa, sb, gd) : gamma_from_num(gd.n * s - sa * sb, gd);
+                    const double g = wide ? gamma_from_sums_wide(sum[k], sa[k], sb, gd)
+                                          : gamma_from_num(gd.n * sum[k] - sa[k] * sb, gd);
                     if (gamma) gamma[idx] = g;
                     tile[ty + 8 * k][tx] = double_to_float_rn(g);
                 }

@@ -7,9 +7,10 @@
 //   - 1-bit frames whose region rows are whole 32-pixel words apart ->
 //     FP8 E4M3 bytes (0x00 / 0x38 = 1.0), ingest_bits_kernel: a block of frames
 //     staged word-wise in shared memory, transposed 32 x 32 bits per warp;
-//   - any frames -> BF16 (integers 0..255 are exact; 1-bit frames that do not
-//     meet the above as E4M3), one CTA per tile of 32 pixels x 256 frames (32
-//     frames per warp, one byte load per lane and frame, all in flight).
+//   - 8-bit frames with 4-pixel aligned regions -> BF16 (integers 0..255 are
+//     exact), ingest_u8x4_kernel: one CTA per tile of 128 pixels x 128 frames;
+//   - any other frames -> BF16 (1-bit frames that do not meet the first case as
+//     E4M3), one CTA per tile of 32 pixels x 256 output bytes.
 // Frames at or beyond n_frames are written as 0, so every operand row is padded
 // to a whole number of CTA tiles.  The same pass adds the marginal sums
 // S_a = sum_i A_i (Eq. (1), second term) with exact int64 atomics.
@@ -31,9 +32,7 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
                                                      int64_t kstride_bytes, uint8_t* op_a,
                                                      uint8_t* op_b, int64_t* s_a, int64_t* s_b,
                                                      int tiles_a, uint32_t* vmax) {
-    constexpr int kFramesPerWarp = 32;                // 32 frames per warp: 32 independent loads in flight per lane
-    constexpr int kRowBytes = ingest_row_bytes(kBf16);   // operand bytes per pixel per CTA (256 frames)
-    constexpr int kWords = kFramesPerWarp * (kBf16 ? 2 : 1) / 4;   // 32-bit words per lane
+    constexpr int kFramesPerWarp = kBf16 ? 16 : 32;   // 32 operand bytes per pixel per warp
     const bool is_a = (int)blockIdx.x < tiles_a;
     const FramesDev d = is_a ? A : B;
     const int tile = is_a ? (int)blockIdx.x : (int)blockIdx.x - tiles_a;
@@ -42,7 +41,7 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
     const int64_t M = (int64_t)d.height * d.width;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    __shared__ __align__(16) uint8_t tile_s[kIngestPixels][kRowBytes + 16];
+    __shared__ __align__(16) uint8_t tile_s[kIngestPixels][kIngestRowBytes + 16];
     __shared__ long long part[8][32];
     __shared__ uint32_t wmax[8];
 
@@ -59,11 +58,11 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
 
     const int64_t f0 = (int64_t)blockIdx.y * (kFramesPerWarp * 8) + warp * kFramesPerWarp;
     long long sum = 0;
-    uint32_t w[kWords];
+    uint32_t w[8];
     uint32_t mx = 0;
     if constexpr (kBf16) {
 #pragma unroll
-        for (int j = 0; j < kWords; ++j) {
+        for (int j = 0; j < 8; ++j) {
             uint32_t lo = 0, hi = 0;
             const int64_t f = f0 + 2 * j;
             if (valid && f < n_frames) lo = load_pixel(d, base, sh, f);
@@ -89,9 +88,9 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
             w[j] = word;
         }
     }
-    uint4* dst = reinterpret_cast<uint4*>(&tile_s[lane][warp * kWords * 4]);
-#pragma unroll
-    for (int q = 0; q < kWords / 4; ++q) dst[q] = make_uint4(w[4 * q], w[4 * q + 1], w[4 * q + 2], w[4 * q + 3]);
+    uint4* dst = reinterpret_cast<uint4*>(&tile_s[lane][warp * 32]);
+    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
     part[warp][lane] = sum;
     if constexpr (kBf16) {
         mx = __reduce_max_sync(0xffffffffu, mx);
@@ -107,17 +106,17 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
         if (m > *reinterpret_cast<volatile uint32_t*>(slot)) atomicMax(slot, m);
     }
 
-    // 32 rows x kRowBytes bytes in chunks of 16 bytes; consecutive threads write
+    // 32 rows x 256 bytes = 512 chunks of 16 bytes; consecutive threads write
     // consecutive chunks of one operand row.
-    constexpr int kChunks = kRowBytes / 16;
 #pragma unroll
-    for (int it = 0; it < kIngestPixels * kChunks / 256; ++it) {
+    for (int it = 0; it < 2; ++it) {
         const int idx = it * 256 + threadIdx.x;
-        const int row = idx / kChunks, chunk = idx % kChunks;
+        const int row = idx >> 4, chunk = idx & 15;
         const int64_t pp = (int64_t)tile * kIngestPixels + row;
         if (pp < M) {
             const uint4 v = *reinterpret_cast<const uint4*>(&tile_s[row][chunk * 16]);
-            *reinterpret_cast<uint4*>(op + pp * kstride_bytes + (int64_t)blockIdx.y * kRowBytes + chunk * 16) = v;
+            *reinterpret_cast<uint4*>(op + pp * kstride_bytes + (int64_t)blockIdx.y * kIngestRowBytes +
+                                      chunk * 16) = v;
         }
     }
     if (warp == 0 && valid) {
@@ -125,6 +124,111 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
 #pragma unroll
         for (int k = 0; k < 8; ++k) t += part[k][lane];
         if (t) atomicAdd(reinterpret_cast<unsigned long long*>(s + p), (unsigned long long)t);
+    }
+}
+
+// 8-bit frames whose regions are 4-pixel aligned (width, x0, row and frame
+// strides multiples of 4 bytes): CTA = 128 pixels x 128 frames.  Lane l of warp
+// w loads pixels 4l .. 4l + 3 of the tile (one 4-byte word, so a warp reads 128
+// contiguous bytes of a frame row) for frames 16w .. 16w + 15, all 16 loads in
+// flight.  BF16 of a byte v without the conversion pipe: the float with bits
+// 0x4B000000 | v is 2^23 + v, minus 2^23 is v exactly, and v < 2^8 leaves the low
+// 16 bits of its float zero, so its upper half is BF16(v) exactly.  Each lane
+// writes its pixels' 32-byte row segments to a shared tile whose 16-byte chunks
+// are XOR-swizzled by pixel / 4 (the 8 lanes of one store phase hit 8 distinct
+// chunks), and the tile leaves as whole 256-byte operand rows.
+constexpr int kX4Pixels = 128;
+constexpr int kX4Frames = 128;                           // 256 bytes of BF16 per operand row
+static_assert(kX4Frames * 2 == kIngestRowBytes, "same operand row blocks as ingest_kernel");
+
+__device__ __forceinline__ uint32_t x4_prmt(uint32_t a, uint32_t b, uint32_t sel) {
+    return __byte_perm(a, b, sel);
+}
+
+__global__ void __launch_bounds__(256) ingest_u8x4_kernel(FramesDev A, FramesDev B, int64_t n_frames,
+                                                          int64_t kstride_bytes, uint8_t* op_a, uint8_t* op_b,
+                                                          int64_t* s_a, int64_t* s_b, int tiles_a, uint32_t* vmax) {
+    __shared__ __align__(16) uint8_t tile_s[kX4Pixels * kX4Frames * 2];   // [pixel][16 chunks of 16 B], swizzled
+    __shared__ uint32_t part[8][kX4Pixels];
+    __shared__ uint32_t wmax[8];
+    const bool is_a = (int)blockIdx.x < tiles_a;
+    const FramesDev d = is_a ? A : B;
+    const int tile = is_a ? (int)blockIdx.x : (int)blockIdx.x - tiles_a;
+    uint8_t* op = is_a ? op_a : op_b;
+    int64_t* s = is_a ? s_a : s_b;
+    const int64_t M = (int64_t)d.height * d.width;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    const int64_t p = (int64_t)tile * kX4Pixels + 4 * lane;   // first of the lane's 4 pixels (same image row)
+    const bool valid = p < M;
+    const uint8_t* base = d.data;
+    if (valid) {
+        const int64_t y = p / d.width, x = p - y * d.width;
+        base += (d.y0 + y) * d.row_stride + d.x0 + x;
+    }
+    const int64_t f0 = (int64_t)blockIdx.y * kX4Frames + warp * 16;
+    uint32_t v[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j)
+        v[j] = (valid && f0 + j < n_frames) ? __ldg(reinterpret_cast<const uint32_t*>(base + (f0 + j) * d.frame_stride))
+                                            : 0u;
+    // marginal sums: bytes 0, 2 and 1, 3 in 16-bit lanes (16 x 255 < 2^16)
+    uint32_t s02 = 0, s13 = 0, mx4 = 0;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        s02 += v[j] & 0x00FF00FFu;
+        s13 += (v[j] >> 8) & 0x00FF00FFu;
+        mx4 = __vmaxu4(mx4, v[j]);
+    }
+    const uint32_t pix_sum[4] = {s02 & 0xFFFFu, s13 & 0xFFFFu, s02 >> 16, s13 >> 16};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        // 16 frames of pixel 4 lane + q: 8 words of two BF16 values, as two 16-byte chunks
+        uint32_t w[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            // 0x4B0000vv for frames 2j and 2j + 1 (byte q of each word)
+            const uint32_t lo = x4_prmt(v[2 * j], 0x4B000000u, 0x7440u + (uint32_t)q);
+            const uint32_t hi = x4_prmt(v[2 * j + 1], 0x4B000000u, 0x7440u + (uint32_t)q);
+            const float flo = __uint_as_float(lo) - 8388608.0f, fhi = __uint_as_float(hi) - 8388608.0f;
+            w[j] = x4_prmt(__float_as_uint(flo), __float_as_uint(fhi), 0x7632u);
+        }
+        const int row = 4 * lane + q, swz = lane & 7;
+        uint4* dst = reinterpret_cast<uint4*>(tile_s + row * (kX4Frames * 2));
+        dst[(2 * warp) ^ swz] = make_uint4(w[0], w[1], w[2], w[3]);
+        dst[(2 * warp + 1) ^ swz] = make_uint4(w[4], w[5], w[6], w[7]);
+        part[warp][row] = pix_sum[q];
+    }
+    uint32_t m = max(max(mx4 & 0xFFu, (mx4 >> 8) & 0xFFu), max((mx4 >> 16) & 0xFFu, mx4 >> 24));
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane == 0) wmax[warp] = m;
+    __syncthreads();
+    if (vmax != nullptr && threadIdx.x == 0) {
+        uint32_t mm = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) mm = max(mm, wmax[k]);
+        uint32_t* slot = vmax + (is_a ? 0 : 1);
+        if (mm > *reinterpret_cast<volatile uint32_t*>(slot)) atomicMax(slot, mm);
+    }
+    // 128 rows x 16 chunks; 16 consecutive threads write one 256-byte operand row
+#pragma unroll
+    for (int it = 0; it < kX4Pixels * 16 / 256; ++it) {
+        const int idx = it * 256 + threadIdx.x;
+        const int row = idx >> 4, c = idx & 15;
+        const int64_t pp = (int64_t)tile * kX4Pixels + row;
+        if (pp < M) {
+            const uint4 val = reinterpret_cast<const uint4*>(tile_s + row * (kX4Frames * 2))[c ^ ((row >> 2) & 7)];
+            *reinterpret_cast<uint4*>(op + pp * kstride_bytes + (int64_t)blockIdx.y * (kX4Frames * 2) + c * 16) = val;
+        }
+    }
+    if (threadIdx.x < kX4Pixels) {
+        const int64_t pp = (int64_t)tile * kX4Pixels + threadIdx.x;
+        if (pp < M) {
+            uint32_t t = 0;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) t += part[k][threadIdx.x];
+            if (t) atomicAdd(reinterpret_cast<unsigned long long*>(s + pp), (unsigned long long)t);
+        }
     }
 }
 
@@ -265,6 +369,11 @@ static bool bits_fast_ok(const FramesDev& d) {
     return d.bits == 1 && d.width % 32 == 0 && d.frame_stride % 4 == 0 &&
            reinterpret_cast<uintptr_t>(d.data) % 4 == 0;
 }
+// Conditions of the 4-pixel path for 8-bit frames.
+static bool u8x4_ok(const FramesDev& d) {
+    return d.bits == 8 && d.width % 4 == 0 && d.x0 % 4 == 0 && d.row_stride % 4 == 0 && d.frame_stride % 4 == 0 &&
+           reinterpret_cast<uintptr_t>(d.data) % 4 == 0;
+}
 cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int64_t n_frames,
                           int64_t kstride_bytes, uint8_t* op_a, uint8_t* op_b, int64_t* s_a,
                           int64_t* s_b, uint32_t* vmax, cudaStream_t st) {
@@ -293,8 +402,22 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
         }
         return cudaSuccess;
     }
-    const int64_t row_bytes = ingest_row_bytes(bf16);
-    const int64_t frame_tiles = kstride_bytes / row_bytes;
+    const int64_t frame_tiles = kstride_bytes / kIngestRowBytes;
+    if (bf16 && u8x4_ok(a) && u8x4_ok(b)) {
+        const int xa = (int)((Ma + kX4Pixels - 1) / kX4Pixels), xb = (int)((Mb + kX4Pixels - 1) / kX4Pixels);
+        for (int64_t t0 = 0; t0 < frame_tiles; t0 += 65535) {   // grid.y limit
+            const int64_t nt = frame_tiles - t0 < 65535 ? frame_tiles - t0 : 65535;
+            FramesDev a2 = a, b2 = b;
+            a2.data = a.data + t0 * kX4Frames * a.frame_stride;
+            b2.data = b.data + t0 * kX4Frames * b.frame_stride;
+            ingest_u8x4_kernel<<<dim3((unsigned)(xa + xb), (unsigned)nt), 256, 0, st>>>(
+                a2, b2, n_frames - t0 * kX4Frames, kstride_bytes, op_a + t0 * kIngestRowBytes,
+                op_b + t0 * kIngestRowBytes, s_a, s_b, xa, vmax);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
     if (frame_tiles > 65535) {
         // grid.y limit: split the frame range over several launches
         for (int64_t t0 = 0; t0 < frame_tiles; t0 += 65535) {
@@ -307,13 +430,13 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
             dim3 grid(tiles_a + tiles_b, (unsigned)nt);
             if (bf16)
                 ingest_kernel<true><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes,
-                                                          op_a + t0 * row_bytes,
-                                                          op_b + t0 * row_bytes, s_a, s_b,
+                                                          op_a + t0 * kIngestRowBytes,
+                                                          op_b + t0 * kIngestRowBytes, s_a, s_b,
                                                           tiles_a, vmax);
             else
                 ingest_kernel<false><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes,
-                                                           op_a + t0 * row_bytes,
-                                                           op_b + t0 * row_bytes, s_a, s_b,
+                                                           op_a + t0 * kIngestRowBytes,
+                                                           op_b + t0 * kIngestRowBytes, s_a, s_b,
                                                            tiles_a, nullptr);
         }
         return cudaGetLastError();

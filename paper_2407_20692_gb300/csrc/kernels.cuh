@@ -25,9 +25,8 @@ struct FramesDev {
 // Frames -> K-major tensor-core operands [M][kstride] and marginal sums.
 // kBf16: values as BF16 (any bit depth); else 1-bit values as FP8 E4M3.
 constexpr int kIngestPixels = 32;                 // pixels per CTA
-// operand bytes per pixel per CTA: 256 frames as E4M3 bytes or BF16 values
-__host__ __device__ constexpr int ingest_row_bytes(bool bf16) { return bf16 ? 512 : 256; }
-inline int ingest_frames_per_cta(bool) { return 256; }
+constexpr int kIngestRowBytes = 256;              // operand bytes per pixel per CTA
+inline int ingest_frames_per_cta(bool bf16) { return bf16 ? 128 : 256; }
 
 // vmax (BF16 path, may be null): the largest A and B value seen is raised into
 // vmax[0] and vmax[1] (the caller zeroes them first).

@@ -42,7 +42,8 @@ def test_hand_worked_cases(case):
 @pytest.mark.parametrize("side_a,side_b,n,counts", [
     (16, 16, 2000, "poisson8"),          # the small 16x16 vs 16x16 uint8 workload, full size
     (24, 12, 3001, "bernoulli"),         # ragged tiles and a ragged frame count
-    (20, 9, 777, "poisson8"),
+    (20, 9, 777, "poisson8"),            # rows not 4-byte aligned: the per-byte ingest
+    (36, 20, 1234, "poisson8"),          # 4-pixel ingest: ragged 128-pixel tiles and frame tail
     (40, 36, 4500, "bernoulli"),         # several M and N tiles, N tile ragged
     (8, 40, 300, "binomial255"),         # M_a < one tile, large counts
 ])
