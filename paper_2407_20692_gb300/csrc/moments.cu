@@ -8,15 +8,18 @@
 // 2^24, and the schedule guarantees that:
 //   - binary frames: a frame chunk has at most 65536 frames, so every sum is
 //     <= 65536;
-//   - 8-bit values: the FP32 accumulator is folded into exact int32 running
-//     sums (kept in tensor memory beside it) every S frames, S the largest
-//     multiple of 64 with S x max A x max B < 2^23 (at least 128 frames, since
-//     128 x 255^2 < 2^23).  The maxima are the ones the ingest records for the
+//   - 8-bit values: the FP32 accumulator is folded into exact uint32 running
+//     sums (in the epilogue threads' registers) every S frames, S the largest
+//     multiple of 64 with S x max A x max B < 2^24 (at least 256 frames, since
+//     256 x 255^2 < 2^24).  The maxima are the ones the ingest records for the
 //     call's frames, read on the device, so photon counts far below 255 fold
-//     rarely or never.  Below 2^23 the fold needs no float-to-integer
-//     conversion: f + 2^23 is exact with bit pattern 0x4B000000 + f.  A chunk of
-//     <= 65536 frames keeps each total below 65536 x 255^2 < 2^32 (the running
-//     sums are uint32: every product is non-negative).
+//     rarely or never.  Each segment sum, an integer below 2^24, converts
+//     exactly (cvt.rni.u32.f32).  (Bounding the segments by 2^23 instead, where
+//     f + 2^23 gives the integer in its bit pattern without a conversion,
+//     halves S; measured slower, 4.65 -> 5.25 ms on 128x128 vs 64x64 with
+//     N = 50000.)  A chunk of <= 65536 frames keeps each total below
+//     65536 x 255^2 < 2^32 (the running sums are uint32: every product is
+//     non-negative).
 // Each (frame chunk, 128 x 256 output tile) of a problem is one work unit; its
 // exact partial sum goes to its own slot of the workspace, and the fold step
 // adds the slots into int64.  (Finishing Eq. (1) in this epilogue was measured
@@ -113,13 +116,13 @@ __device__ __forceinline__ Unit decode_unit(const MomentsLaunch<K>& L, int u) {
 }
 
 // K blocks (64 frames) per exact FP32 segment of a BF16 problem: the largest S
-// with S x 64 x max A x max B < 2^23, from the ingest's maxima (worst case
+// with S x 64 x max A x max B < 2^24, from the ingest's maxima (worst case
 // 255 x 255 when they are missing).
 __device__ __forceinline__ int segment_kblocks(const MomentsProblem& P) {
     uint64_t prod = 255u * 255u;
     if (P.vmax != nullptr) prod = (uint64_t)__ldcg(P.vmax) * (uint64_t)__ldcg(P.vmax + 1);
     if (prod < 1) prod = 1;
-    const uint64_t frames = ((1ull << 23) - 1) / prod;
+    const uint64_t frames = ((1ull << 24) - 1) / prod;
     const uint64_t kb = frames / 64;
     return kb < 1 ? 1 : (kb > 0x40000000ull ? 0x40000000 : (int)kb);
 }
@@ -314,9 +317,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     acc_phase ^= 1;
                 }
             } else {
-                // Every segment: running sums (registers, int32) += the FP32
-                // segment sums (< 2^23, converted through their bit patterns);
-                // after the last segment they go to the partial slot.
+                // Every segment: running sums (registers, uint32) += the FP32
+                // segment sums (integers < 2^24, converted exactly); after the
+                // last segment they go to the partial slot.
                 const int seg = seg_kb[w.prob];
                 const int nseg = (kb1 - kb0 + seg - 1) / seg;
                 uint32_t run[kHalf / 16][16];
@@ -337,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         tmem_ld_wait();
 #pragma unroll
                         for (int j = 0; j < 16; ++j)
-                            run[c][j] += __float_as_uint(__fadd_rn(__uint_as_float(r[j]), 8388608.0f)) - 0x4B000000u;
+                            run[c][j] += __float2uint_rn(__uint_as_float(r[j]));
                     }
                     tc_fence_before();
                     mbar_arrive(&tempty[acc]);

@@ -143,13 +143,14 @@ def test_full_chunk_of_max_counts_closed_form(n):
 
 @pytest.mark.parametrize("top", [23, 91, 255])
 def test_segment_length_follows_the_recorded_value_range(top):
-    """8-bit frames: the FP32 tensor-memory accumulator is folded into int32
-    every S frames, S the largest multiple of 64 with S x max A x max B < 2^23
-    (from the maxima the ingest records).  Constant A = top and B = top except
-    in every 16th frame (top - 1) make every tensor-core K step add an odd
-    increment, so a segment that overran 2^23 would lose low bits in the
-    conversion and the sums would be wrong.  2048 x 1280 outputs keep the 32768
-    frames in one chunk (several segments per unit for every top)."""
+    """8-bit frames: the FP32 tensor-memory accumulator is folded into uint32
+    every S frames, S the largest multiple of 64 with S x max A x max B < 2^24
+    (from the maxima the ingest records; at top = 255 the segment sums reach
+    16,646,400, within 2 frames' worth of 2^24).  Constant A = top and B = top
+    except in every 16th frame (top - 1) make every tensor-core K step add an
+    odd increment, so a segment that overran 2^24 (where FP32 integers are 2
+    apart) would lose low bits and the sums would be wrong.  2048 x 1280 outputs
+    keep the 32768 frames in one chunk (several segments per unit for every top)."""
     n = 32768
     ha, wa, hb, wb = 32, 64, 20, 64
     W = wa + wb
