@@ -102,6 +102,28 @@ bool make_operand_map(CUtensorMap* m, void* base, bool bf16, int64_t rows, int64
 
 }  // namespace
 
+static bool make_bf16_map_swz(CUtensorMap* m, const void* base, int rank, const uint64_t* dims,
+                              const uint64_t* strides, const uint32_t* box, CUtensorMapSwizzle swz) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || rank < 3 || rank > 4) return false;
+    cuuint64_t d[4], st[3];
+    cuuint32_t bx[4], es[4] = {1, 1, 1, 1};
+    for (int i = 0; i < rank; ++i) {
+        d[i] = dims[i];
+        bx[i] = box[i];
+    }
+    for (int i = 0; i < rank - 1; ++i) st[i] = strides[i];
+    const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, (cuuint32_t)rank, const_cast<void*>(base), d, st, bx,
+                           es, CU_TENSOR_MAP_INTERLEAVE_NONE, swz, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+bool make_bf16_map_sw128(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                         const uint32_t* box) {
+    return make_bf16_map_swz(m, base, rank, dims, strides, box, CU_TENSOR_MAP_SWIZZLE_128B);
+}
+
 bool make_bf16_map_sw64(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
                         const uint32_t* box) {
     EncodeTiledFn enc = encode_fn();
@@ -976,7 +998,9 @@ cpi_status cpi_denoise_grad(const float* model, const float* gamma_in, const flo
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     uint8_t* ws = static_cast<uint8_t*>(workspace);
     cudaError_t e = denoise_forward(model, gamma_in, ha, wa, hb, wb, ws, L, true, dev->status, g_timeout_ns, st);
-    if (e == cudaSuccess) e = denoise_backward(model, gamma_target, ha, wa, hb, wb, ws, L, grad, loss, st);
+    if (e == cudaSuccess)
+        e = denoise_backward(model, gamma_target, ha, wa, hb, wb, ws, L, grad, loss, dev->sm_count, dev->status,
+                             g_timeout_ns, st);
     return cuda_status(e);
 }
 

@@ -227,9 +227,16 @@ inline size_t tc_smem(int W) { return 1024 + 6 * tc_copy_stride(W) + kTcWBytes +
 // warps 2..5 drain an accumulator (TMEM lane quarter = warp % 4) while the next
 // unit is loaded and multiplied.  Every wait is bounded; on a time-out the CTA
 // records it, drains its own copies and MMAs, frees its tensor memory and stops.
+//
+// BWD: the input gradient of a hidden layer, g = conv(delta; flipped, transposed
+// weights), no bias: delta arrives as two channels-last bf16 terms (hi, lo),
+// loaded one after the other into the two stages of a unit and multiplied by
+// the same weights into the same accumulator; the epilogue writes the FP32 sums
+// channels-first to y_out [slice][32][H * W].
 constexpr int kTcThreadsP = 192;          // warp 0 TMA, warp 1 MMA, warps 2..5 epilogue
-template <int NOUT>
+template <int NOUT, bool BWD = false>
 __global__ void __launch_bounds__(kTcThreadsP, 1) dn_conv_tc_kernel(const __grid_constant__ CUtensorMap in_map,
+                                                                   const __grid_constant__ CUtensorMap in_map_lo,
                                                                    const __grid_constant__ CUtensorMap w_map,
                                                                    const float* __restrict__ bias,
                                                                    __nv_bfloat16* __restrict__ out_cf,
@@ -286,18 +293,25 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) dn_conv_tc_kernel(const __grid
             tma_load_3d(sw, &w_map, wbar, 0, 0, 0);
             int stage = 0;
             uint32_t phase = 0, issued = 0, issued_phase = 0;
-            for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+            bool go = true;
+            for (int u = blockIdx.x; go && u < n_units; u += gridDim.x) {
                 const int b = u / nrb, y0 = (u - b * nrb) * R;
-                if (!mbar_wait_bounded(&empty[stage], phase ^ 1, abort_flag, status, timeout_ns)) break;
-                mbar_arrive_expect_tx(&full[stage], 3 * copy_bytes);
+                for (int part = 0; part < (BWD ? 2 : 1); ++part) {   // BWD: the hi, then the lo term
+                    if (!mbar_wait_bounded(&empty[stage], phase ^ 1, abort_flag, status, timeout_ns)) {
+                        go = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], 3 * copy_bytes);
+                    const CUtensorMap* m = part == 0 ? &in_map : &in_map_lo;
 #pragma unroll
-                for (int kx = 0; kx < 3; ++kx)
-                    tma_load_4d(sm + (size_t)(stage * 3 + kx) * cstride, &in_map, &full[stage], 0, kx - 1, y0 - 1, b);
-                issued |= 1u << stage;
-                issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
-                if (++stage == 2) {
-                    stage = 0;
-                    phase ^= 1;
+                    for (int kx = 0; kx < 3; ++kx)
+                        tma_load_4d(sm + (size_t)(stage * 3 + kx) * cstride, m, &full[stage], 0, kx - 1, y0 - 1, b);
+                    issued |= 1u << stage;
+                    issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
+                    if (++stage == 2) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
                 }
             }
             if (*abort_flag) {   // copies of this thread still in flight must land before the CTA ends
@@ -314,33 +328,39 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) dn_conv_tc_kernel(const __grid
             int stage = 0, acc = 0;
             uint32_t phase = 0, acc_phase = 0;
             for (int u = blockIdx.x; ok && u < n_units; u += gridDim.x) {
-                if (!mbar_wait_bounded(&tempty[acc], acc_phase ^ 1, abort_flag, status, timeout_ns) ||
-                    !mbar_wait_bounded(&full[stage], phase, abort_flag, status, timeout_ns)) {
+                if (!mbar_wait_bounded(&tempty[acc], acc_phase ^ 1, abort_flag, status, timeout_ns)) {
                     ok = false;
                     break;
                 }
-                tc_fence_after();
                 const uint32_t d0 = tmem_base + (uint32_t)(acc * 2 * NOUT);
-#pragma unroll
-                for (int t = 0; t < 2; ++t)
-#pragma unroll
-                    for (int tap = 0; tap < 9; ++tap) {
-                        const int ky = tap / 3, kx = tap % 3;
-                        const uint64_t a = sdesc_kmajor_sw64(
-                            smem_u32(sm + (size_t)(stage * 3 + kx) * cstride + (size_t)(ky * W + t * 128) * 64));
-                        const uint64_t bd = sdesc_kmajor_sw64(smem_u32(sw + tap * NOUT * 64));
-#pragma unroll
-                        for (int h = 0; h < 2; ++h)   // second half of the 64-byte rows: +32 bytes
-                            umma_f32<true>(d0 + (uint32_t)(t * NOUT), a + (uint64_t)(2 * h), bd + (uint64_t)(2 * h),
-                                           idesc, (tap | h) ? 1u : 0u);
+                for (int part = 0; part < (BWD ? 2 : 1); ++part) {
+                    if (!mbar_wait_bounded(&full[stage], phase, abort_flag, status, timeout_ns)) {
+                        ok = false;
+                        break;
                     }
-                any = true;
-                umma_commit(&empty[stage]);
-                umma_commit(&tfull[acc]);
-                if (++stage == 2) {
-                    stage = 0;
-                    phase ^= 1;
+                    tc_fence_after();
+#pragma unroll
+                    for (int t = 0; t < 2; ++t)
+#pragma unroll
+                        for (int tap = 0; tap < 9; ++tap) {
+                            const int ky = tap / 3, kx = tap % 3;
+                            const uint64_t a = sdesc_kmajor_sw64(
+                                smem_u32(sm + (size_t)(stage * 3 + kx) * cstride + (size_t)(ky * W + t * 128) * 64));
+                            const uint64_t bd = sdesc_kmajor_sw64(smem_u32(sw + tap * NOUT * 64));
+#pragma unroll
+                            for (int h = 0; h < 2; ++h)   // second half of the 64-byte rows: +32 bytes
+                                umma_f32<true>(d0 + (uint32_t)(t * NOUT), a + (uint64_t)(2 * h),
+                                               bd + (uint64_t)(2 * h), idesc, (part | tap | h) ? 1u : 0u);
+                        }
+                    any = true;
+                    umma_commit(&empty[stage]);
+                    if (++stage == 2) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
                 }
+                if (!ok) break;
+                umma_commit(&tfull[acc]);
                 if (++acc == 2) {
                     acc = 0;
                     acc_phase ^= 1;
@@ -382,6 +402,10 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) dn_conv_tc_kernel(const __grid
                 tmem_ld_wait();
                 if (y >= H) continue;
                 const int64_t pix = (int64_t)y * W + x;
+                if constexpr (BWD) {   // raw sums, channels-first float
+#pragma unroll
+                    for (int co = 0; co < 32; ++co) y_out[((int64_t)b * 32 + co) * HW + pix] = __uint_as_float(r[co]);
+                } else {
                 uint32_t pk[16];
 #pragma unroll
                 for (int co = 0; co < 32; co += 2) {
@@ -398,6 +422,7 @@ __global__ void __launch_bounds__(kTcThreadsP, 1) dn_conv_tc_kernel(const __grid
                     uint4* dst = reinterpret_cast<uint4*>(out_cl + ((int64_t)b * HW + pix) * 32);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) dst[k] = make_uint4(pk[4 * k], pk[4 * k + 1], pk[4 * k + 2], pk[4 * k + 3]);
+                }
                 }
             }
             tc_fence_before();
@@ -462,6 +487,19 @@ __global__ void dn_wprep_kernel(const float* __restrict__ model, int64_t w0, int
     const int cin = l == 0 ? 9 : 32;
     const int64_t base = l == 0 ? w0 : (l == 1 ? w1 : w2);
     wt[i] = __float2bfloat16_rn(ci < cin ? model[base + ((int64_t)co * cin + ci) * 9 + tap] : 0.0f);
+}
+
+// Weights of the input-gradient convolutions of layers 1 and 2 as bf16
+// [layer - 1][tap][Cin][Cout]: tap t of the flipped kernel, W[co][ci][8 - t],
+// output channel ci, input channel co.
+__global__ void dn_wprep_bwd_kernel(const float* __restrict__ model, int64_t w1, int64_t w2,
+                                    __nv_bfloat16* __restrict__ wt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * 9 * 32 * 32) return;
+    const int l = i / (9 * 32 * 32), rem = i - l * 9 * 32 * 32;
+    const int tap = rem / (32 * 32), ci = (rem / 32) % 32, co = rem % 32;
+    const int64_t base = l == 0 ? w1 : w2;
+    wt[i] = __float2bfloat16_rn(model[base + ((int64_t)co * 32 + ci) * 9 + (8 - tap)]);
 }
 
 // ------------------------------------------------------------------ weight gradients
@@ -545,6 +583,320 @@ __global__ void __launch_bounds__(((CIN * 9 + 31) / 32) * 32)
 #pragma unroll
         for (int co = 0; co < COUT; ++co) out[(co * CIN + ci) * 9 + tap] = acc[co];
     if (tid < COUT) out[COUT * CIN * 9 + tid] = bacc;
+}
+
+// ------------------------------------------------------------------ tensor-core weight gradients
+// For images 64 pixels wide the weight gradient of a layer,
+//     dW[co][ci][ky][kx] = sum over pixels of delta[co](y, x) in[ci](y + ky - 1, x + kx - 1),
+// is a GEMM whose K dimension is the pixels.  delta (float32) is split into two
+// bf16 terms, hi = bf16(delta) and lo = bf16(delta - hi) (the difference is exact
+// in float32), so hi + lo is delta within 2^-17 and every product of a bf16 term
+// with a bf16 input is exact in the FP32 accumulator.
+
+// delta = d masked by mask > 0, as [slice][2 COUT][H * W] bf16 (hi channels
+// 0 .. COUT-1, lo channels COUT .. 2 COUT-1) and, when cl_hi is given, also
+// channels-last [slice][H * W][COUT] (the input of the tensor-core input-gradient
+// convolution, staged in shared memory and stored as contiguous 16-byte words);
+// per (slice, block of 256 pixels, channel) the sum of delta over the block's
+// pixels (the bias gradient's terms: each warp in a fixed butterfly, then the
+// warps in order).  CTA = (block of 256 pixels, slice), one pixel per thread.
+constexpr int kSplitPix = 256;
+template <int COUT>
+__global__ void __launch_bounds__(256) dn_dsplit_kernel(const float* __restrict__ d,
+                                                        const __nv_bfloat16* __restrict__ mask, int64_t HW,
+                                                        __nv_bfloat16* __restrict__ out, __nv_bfloat16* __restrict__ cl_hi,
+                                                        __nv_bfloat16* __restrict__ cl_lo, float* __restrict__ bpart) {
+    constexpr int NW = COUT > 1 ? COUT / 2 : 1;                 // 32-bit words per pixel and term
+    __shared__ float red[8][COUT];
+    __shared__ __align__(16) uint32_t stage[2][COUT > 1 ? kSplitPix : 1][NW + (COUT > 1 ? 4 : 0)];
+    const int b = blockIdx.y;
+    const int64_t p0 = (int64_t)blockIdx.x * kSplitPix, p = p0 + threadIdx.x;
+    const bool in = p < HW;
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) {
+        float v = 0.0f;
+        if (in) {
+            const int64_t idx = ((int64_t)b * COUT + co) * HW + p;
+            v = d[idx];
+            if (mask != nullptr && !(__bfloat162float(mask[idx]) > 0.0f)) v = 0.0f;
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            out[((int64_t)b * 2 * COUT + co) * HW + p] = hi;
+            out[((int64_t)b * 2 * COUT + COUT + co) * HW + p] = lo;
+            if constexpr (COUT > 1) {
+                reinterpret_cast<__nv_bfloat16*>(stage[0][threadIdx.x])[co] = hi;
+                reinterpret_cast<__nv_bfloat16*>(stage[1][threadIdx.x])[co] = lo;
+            }
+        }
+        // the warp's 32 pixels in a fixed butterfly, then the 8 warps in order
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][co] = v;
+    }
+    __syncthreads();
+    if constexpr (COUT > 1) {
+        if (cl_hi != nullptr) {
+            // the block's pixels are contiguous in the channels-last arrays: 16-byte words in order
+            const int64_t npx = HW - p0 < kSplitPix ? HW - p0 : kSplitPix;
+            constexpr int Q = NW / 4;                                  // 16-byte words per pixel
+            for (int t = threadIdx.x; t < 2 * npx * Q; t += 256) {
+                const int term = t / (int)(npx * Q), r = t - term * (int)(npx * Q);
+                const int px = r / Q, q = r - px * Q;
+                const uint4 w = *reinterpret_cast<const uint4*>(&stage[term][px][4 * q]);
+                __nv_bfloat16* dst = term == 0 ? cl_hi : cl_lo;
+                *reinterpret_cast<uint4*>(dst + ((int64_t)b * HW + p0 + px) * COUT + 8 * q) = w;
+            }
+        }
+    }
+    if (threadIdx.x < COUT) {
+        float s = 0.0f;
+        for (int w = 0; w < 8; ++w) s += red[w][threadIdx.x];
+        bpart[((int64_t)b * gridDim.x + blockIdx.x) * COUT + threadIdx.x] = s;
+    }
+}
+
+// x-shifted copies of a layer input (bf16 [slice][CIN][H][W]) for the GEMM's B
+// operand: out[slice][kx * CINP + c][y][x] = in[slice][c][y][x + kx - 1], zero
+// outside the image and for c >= CIN.  One thread per (slice, c < CINP, y, group
+// of 8 columns; W a multiple of 8): one 16-byte load, its two neighbours, three
+// 16-byte stores.
+template <int CIN, int CINP>
+__global__ void __launch_bounds__(256) dn_shift3_kernel(const __nv_bfloat16* __restrict__ in, int B, int H, int W,
+                                                        __nv_bfloat16* __restrict__ out) {
+    const int64_t HW = (int64_t)H * W;
+    const int G = W / 8;
+    const int64_t n = (int64_t)B * CINP * H * G;
+    const uint16_t* src = reinterpret_cast<const uint16_t*>(in);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int gx = (int)(i % G);
+        const int64_t r = i / G;                 // (b, c, y)
+        const int y = (int)(r % H);
+        const int64_t bc = r / H;
+        const int c = (int)(bc % CINP), b = (int)(bc / CINP);
+        const int x0 = gx * 8;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        uint32_t left = 0u, right = 0u;
+        if (c < CIN) {
+            const int64_t row = ((int64_t)b * CIN + c) * HW + (int64_t)y * W;
+            const uint4 v = *reinterpret_cast<const uint4*>(src + row + x0);
+            w[0] = v.x; w[1] = v.y; w[2] = v.z; w[3] = v.w;
+            if (x0 > 0) left = (uint32_t)src[row + x0 - 1] << 16;   // in the high half, as element 2q - 1 of a word
+            if (x0 + 8 < W) right = src[row + x0 + 8];
+        }
+        // kx = 0: element j is in[x0 + j - 1]; kx = 2: in[x0 + j + 1]
+        uint32_t s0[4], s2[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const uint32_t prev = q == 0 ? left : w[q - 1];
+            const uint32_t next = q == 3 ? right : w[q + 1];
+            s0[q] = __byte_perm(prev, w[q], 0x5432);   // (high half of prev, low half of w[q])
+            s2[q] = __byte_perm(w[q], next, 0x5432);   // (high half of w[q], low half of next)
+        }
+        const int64_t o = (int64_t)b * 3 * CINP * HW + (int64_t)y * W + x0;
+        *reinterpret_cast<uint4*>(out + o + (int64_t)c * HW) = make_uint4(s0[0], s0[1], s0[2], s0[3]);
+        *reinterpret_cast<uint4*>(out + o + (int64_t)(CINP + c) * HW) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint4*>(out + o + (int64_t)(2 * CINP + c) * HW) = make_uint4(s2[0], s2[1], s2[2], s2[3]);
+    }
+}
+
+// The GEMM on tcgen05, persistent over units (slice, block of up to 32 rows).
+// Per image row y of a unit, one stage holds A(y) = the 2 COUT delta rows of
+// that image row (64 pixels, 128-byte rows, 128-byte swizzle; the tile's other
+// rows up to M = 128 stay zero) and B(y) = the 3 CINP shifted input rows of
+// image row y; rows y0 - 1 and y0 + R are loaded too (TMA zero fill outside
+// the image).  For A(y) and each ky, one MMA with B(y + ky - 1) (N = 3 CINP)
+// per 16 pixels adds into TMEM columns [ky * 3 CINP, (ky + 1) * 3 CINP): column
+// ky * 3 CINP + kx * CINP + ci of row co is dW[co][ci][ky][kx] (rows >= COUT: the
+// lo terms).  The accumulator spans all of the CTA's units; at the end the
+// CTA writes its 2 COUT rows to part[cta].  Warp 0 (one thread) loads, warp 1
+// (one thread) issues the MMAs and frees each stage once the MMAs that read it
+// are done; all four warps drain the accumulator.  Every wait is bounded.
+constexpr int kWgThreads = 128;
+constexpr int kWgStages = 6;
+constexpr int kWgRows = 32;
+template <int CINP, int COUT>
+struct WgCfg {
+    static constexpr int kNB = 3 * CINP;                         // B rows per image row: 48 or 96
+    static constexpr int kABytes = 128 * 128;                    // A tile, M = 128 rows of 128 bytes
+    static constexpr uint32_t kALoad = 2 * COUT * 128;           // bytes of A the copies write
+    static constexpr uint32_t kBBytes = kNB * 128;
+    static constexpr int kStage = kABytes + (int)kBBytes;        // a multiple of 1024
+    static constexpr uint32_t kCols = 9 * CINP;                  // accumulator columns: 144 or 288
+    static constexpr uint32_t kTmemCols = kCols > 256 ? 512 : 256;
+    static constexpr size_t kSmem = 1024 + (size_t)kWgStages * kStage + 256;
+};
+
+template <int CINP, int COUT>
+__global__ void __launch_bounds__(kWgThreads, 1) dn_wgrad_tc_kernel(const __grid_constant__ CUtensorMap a_map,
+                                                                    const __grid_constant__ CUtensorMap b_map, int H,
+                                                                    int n_slices, float* __restrict__ part,
+                                                                    unsigned int* status,
+                                                                    unsigned long long timeout_ns) {
+    using C = WgCfg<CINP, COUT>;
+    constexpr int S = kWgStages;
+    extern __shared__ uint8_t smem_wg[];
+    uint8_t* sm = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_wg) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(sm + (size_t)S * C::kStage);
+    uint64_t* empty = full + S;
+    uint64_t* done = empty + S;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* any_flag = abort_flag + 1;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int R = H < kWgRows ? H : kWgRows;
+    const int nrb = (H + R - 1) / R, n_units = nrb * n_slices;
+
+    // rows 2 COUT .. 127 of every A tile stay zero (the copies write rows below)
+    for (int s = 0; s < S; ++s) {
+        uint4* a = reinterpret_cast<uint4*>(sm + (size_t)s * C::kStage + C::kALoad);
+        for (int i = tid; i < (int)((C::kABytes - C::kALoad) / 16); i += kWgThreads) a[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    fence_proxy_async_smem();
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(done, 1);
+        *abort_flag = 0;
+        *any_flag = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, C::kTmemCols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------- producer
+        uint32_t g = 0;   // stage items issued
+        bool ok = true;
+        for (int u = blockIdx.x; ok && u < n_units; u += gridDim.x) {
+            const int b = u / nrb, y0 = (u - b * nrb) * R;
+            const int rows = min(R, H - y0);
+            for (int k = 0; k <= rows + 1; ++k, ++g) {
+                const int s = (int)(g % S);
+                if (!mbar_wait_bounded(&empty[s], ((g / S) & 1u) ^ 1u, abort_flag, status, timeout_ns)) {
+                    ok = false;
+                    break;
+                }
+                const bool with_a = k >= 1 && k <= rows;
+                mbar_arrive_expect_tx(&full[s], C::kBBytes + (with_a ? C::kALoad : 0u));
+                uint8_t* st = sm + (size_t)s * C::kStage;
+                tma_load_4d(st + C::kABytes, &b_map, &full[s], 0, 0, y0 - 1 + k, b);
+                if (with_a) tma_load_4d(st, &a_map, &full[s], 0, 0, y0 - 1 + k, b);
+            }
+        }
+        if (!ok)   // copies still in flight land before the CTA ends
+            for (uint32_t j = g > (uint32_t)S ? g - S : 0u; j < g; ++j)
+                mbar_wait_bounded(&full[j % S], (j / S) & 1u, nullptr, nullptr, timeout_ns);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------------- MMA issuer
+        constexpr uint32_t idesc = idesc_f32acc<true>(128, C::kNB);
+        uint32_t g = 0, waited = 0;
+        bool ok = true, any = false;
+        for (int u = blockIdx.x; ok && u < n_units; u += gridDim.x) {
+            const int b = u / nrb, y0 = (u - b * nrb) * R;
+            const int rows = min(R, H - y0);
+            const uint32_t g0 = g;
+            for (int k = 1; ok && k <= rows; ++k) {
+                while (waited <= g0 + (uint32_t)k + 1u) {
+                    if (!mbar_wait_bounded(&full[waited % S], (waited / S) & 1u, abort_flag, status, timeout_ns)) {
+                        ok = false;
+                        break;
+                    }
+                    ++waited;
+                }
+                if (!ok) break;
+                tc_fence_after();
+                const uint64_t ad = sdesc_kmajor_sw128(smem_u32(sm + (size_t)((g0 + k) % S) * C::kStage));
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks)   // 16 pixels (32 bytes of each 128-byte row) per MMA
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky) {
+                        const uint32_t item = g0 + (uint32_t)(k - 1 + ky);
+                        const uint64_t bd =
+                            sdesc_kmajor_sw128(smem_u32(sm + (size_t)(item % S) * C::kStage + C::kABytes));
+                        umma_f32<true>(tmem_base + (uint32_t)(ky * C::kNB), ad + (uint64_t)(2 * ks),
+                                       bd + (uint64_t)(2 * ks), idesc, (any || ks > 0) ? 1u : 0u);
+                    }
+                any = true;
+                umma_commit(&empty[(g0 + k - 1) % S]);
+            }
+            if (!ok) break;
+            umma_commit(&empty[(g0 + rows) % S]);
+            umma_commit(&empty[(g0 + rows + 1) % S]);
+            g = g0 + rows + 2;
+        }
+        *any_flag = any ? 1 : 0;
+        if (any) umma_commit(done);
+        else mbar_arrive(done);
+    }
+    // ------------------------------------------------------------ all warps: drain
+    __syncwarp();
+    const bool fin = mbar_wait_bounded(done, 0, nullptr, status, timeout_ns);
+    tc_fence_after();
+    if (fin && !*abort_flag && 32 * warp < 2 * COUT) {
+        const int row = 32 * warp + lane;
+        float* out = part + ((size_t)blockIdx.x * 2 * COUT + row) * C::kCols;
+        const bool any = *any_flag != 0;
+#pragma unroll 1
+        for (uint32_t c0 = 0; c0 < C::kCols; c0 += 16) {
+            uint32_t r[16];
+            if (any) {
+                tmem_ld_32x32b_x16(tmem_base + ((uint32_t)(32 * warp) << 16) + c0, r);
+                tmem_ld_wait();
+            }
+            if (row < 2 * COUT)
+#pragma unroll
+                for (int j = 0; j < 16; ++j) out[c0 + j] = any ? __uint_as_float(r[j]) : 0.0f;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        tmem_dealloc(tmem_base, C::kTmemCols);
+    }
+}
+
+// Bias gradient: CTA co sums bpart[i][co] over i, thread t the terms
+// i = t, t + 256, ... in order, then the threads in a fixed tree.
+template <int COUT>
+__global__ void __launch_bounds__(256) dn_bias_reduce_kernel(const float* __restrict__ bpart, int nb,
+                                                             float* __restrict__ grad_bias) {
+    __shared__ float red[256];
+    const int co = blockIdx.x;
+    float s = 0.0f;
+    for (int i = threadIdx.x; i < nb; i += 256) s += bpart[(size_t)i * COUT + co];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) grad_bias[co] = red[0];
+}
+
+// dW[co][ci][tap] = sum over CTAs in order of the hi and lo rows of column
+// tap * CINP + ci (the bias gradient: dn_bias_reduce_kernel).
+template <int CIN, int CINP, int COUT>
+__global__ void dn_wgrad_tc_reduce_kernel(const float* __restrict__ part, int nparts, float* __restrict__ grad) {
+    constexpr int kCols = 9 * CINP;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= COUT * CIN * 9) return;
+    const int co = k / (CIN * 9), ci = (k / 9) % CIN, tap = k % 9;
+    const int col = tap * CINP + ci;
+    float s = 0.0f;
+    for (int i = 0; i < nparts; ++i) {
+        const float* p = part + (size_t)i * 2 * COUT * kCols;
+        s += p[(size_t)co * kCols + col] + p[(size_t)(COUT + co) * kCols + col];
+    }
+    grad[k] = s;
 }
 
 // grad[k] = sum over CTAs of part[cta][k], CTAs in order
@@ -655,6 +1007,100 @@ cudaError_t wgrad(const __nv_bfloat16* in, const float* d, const __nv_bfloat16* 
     return cudaGetLastError();
 }
 
+// Input gradient of a hidden layer on the tensor cores: g = conv(delta_hi +
+// delta_lo; flipped weights wt [tap][32][32]), FP32 channels-first.
+cudaError_t conv_tc_bwd(const __nv_bfloat16* d_hi, const __nv_bfloat16* d_lo, const __nv_bfloat16* wt, float* g,
+                        int B, int H, int W, int sm_count, unsigned int* status, unsigned long long timeout_ns,
+                        cudaStream_t st) {
+    const int64_t HW = (int64_t)H * W;
+    const int R = tc_rows(W);
+    const uint64_t dims[4] = {32, (uint64_t)W, (uint64_t)H, (uint64_t)B};
+    const uint64_t str[3] = {64, (uint64_t)W * 64, (uint64_t)HW * 64};
+    const uint32_t box[4] = {32, (uint32_t)W, (uint32_t)(R + 2), 1};
+    const uint64_t wdims[3] = {32, 32, 9}, wstr[2] = {64, 64 * 32};
+    const uint32_t wbox[3] = {32, 32, 9};
+    CUtensorMap hi_map, lo_map, w_map;
+    if (!make_bf16_map_sw64(&hi_map, d_hi, 4, dims, str, box) || !make_bf16_map_sw64(&lo_map, d_lo, 4, dims, str, box) ||
+        !make_bf16_map_sw64(&w_map, wt, 3, wdims, wstr, wbox))
+        return cudaErrorInvalidValue;
+    static bool attr[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    const size_t smem = tc_smem(W);
+    if (!attr[dev]) {
+        const int smax = (int)(tc_smem(32) > tc_smem(128) ? tc_smem(32) : tc_smem(128));
+        e = cudaFuncSetAttribute(dn_conv_tc_kernel<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    const int64_t units = (int64_t)((H + R - 1) / R) * B;
+    const unsigned grid = (unsigned)(units < sm_count ? units : sm_count);
+    dn_conv_tc_kernel<32, true><<<grid, kTcThreadsP, smem, st>>>(hi_map, lo_map, w_map, nullptr, nullptr, nullptr,
+                                                                 nullptr, g, H, W, B, status, timeout_ns);
+    return cudaGetLastError();
+}
+
+// Weight gradient of one layer on the tensor cores (images 64 pixels wide):
+// delta split, shifted input copies, the GEMM, the fixed-order reduction.
+struct WgBuffers {
+    __nv_bfloat16* dsplit;
+    __nv_bfloat16* cl_hi;   // channels-last split of delta (null: not wanted)
+    __nv_bfloat16* cl_lo;
+    __nv_bfloat16* shifted;
+    float* part;
+    float* bpart;
+};
+template <int CIN, int CINP, int COUT>
+cudaError_t wgrad_tc(const __nv_bfloat16* in, const float* d, const __nv_bfloat16* mask, int B, int H, int W,
+                     const WgBuffers& wb, float* grad, int sm_count, unsigned int* status,
+                     unsigned long long timeout_ns, cudaStream_t st) {
+    using C = WgCfg<CINP, COUT>;
+    if (W != 64) return cudaErrorInvalidValue;
+    const int64_t HW = (int64_t)H * W;
+    const int nblk = (int)((HW + kSplitPix - 1) / kSplitPix);
+    dn_dsplit_kernel<COUT><<<dim3((unsigned)nblk, (unsigned)B), 256, 0, st>>>(d, mask, HW, wb.dsplit, wb.cl_hi,
+                                                                               wb.cl_lo, wb.bpart);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int64_t nshift = (int64_t)B * CINP * HW / 8;
+    const int64_t sblocks = (nshift + 255) / 256 < 8 * (int64_t)sm_count ? (nshift + 255) / 256 : 8 * (int64_t)sm_count;
+    dn_shift3_kernel<CIN, CINP><<<(unsigned)sblocks, 256, 0, st>>>(in, B, H, W, wb.shifted);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    CUtensorMap amap, bmap;
+    const uint64_t adims[4] = {(uint64_t)W, (uint64_t)(2 * COUT), (uint64_t)H, (uint64_t)B};
+    const uint64_t astr[3] = {(uint64_t)HW * 2, (uint64_t)W * 2, (uint64_t)(2 * COUT) * HW * 2};
+    const uint32_t abox[4] = {64, (uint32_t)(2 * COUT), 1, 1};
+    const uint64_t bdims[4] = {(uint64_t)W, (uint64_t)C::kNB, (uint64_t)H, (uint64_t)B};
+    const uint64_t bstr[3] = {(uint64_t)HW * 2, (uint64_t)W * 2, (uint64_t)C::kNB * HW * 2};
+    const uint32_t bbox[4] = {64, (uint32_t)C::kNB, 1, 1};
+    if (!make_bf16_map_sw128(&amap, wb.dsplit, 4, adims, astr, abox) ||
+        !make_bf16_map_sw128(&bmap, wb.shifted, 4, bdims, bstr, bbox))
+        return cudaErrorInvalidValue;
+    static bool attr[64] = {};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!attr[dev]) {
+        e = cudaFuncSetAttribute(dn_wgrad_tc_kernel<CINP, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)C::kSmem);
+        if (e != cudaSuccess) return e;
+        attr[dev] = true;
+    }
+    const int R = H < kWgRows ? H : kWgRows;
+    const int64_t units = (int64_t)B * ((H + R - 1) / R);
+    int grid = sm_count < kWgMaxCtas ? sm_count : kWgMaxCtas;
+    if (units < grid) grid = (int)units;
+    dn_wgrad_tc_kernel<CINP, COUT><<<grid, kWgThreads, C::kSmem, st>>>(amap, bmap, H, B, wb.part, status, timeout_ns);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    constexpr int n = COUT * CIN * 9;
+    dn_wgrad_tc_reduce_kernel<CIN, CINP, COUT><<<(n + 255) / 256, 256, 0, st>>>(wb.part, grid, grad);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    dn_bias_reduce_kernel<COUT><<<COUT, 256, 0, st>>>(wb.bpart, B * nblk, grad + n);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
 // Parameter offsets in the model blob.
@@ -690,6 +1136,16 @@ DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training) {
         L.d_hi = take(4 * (size_t)(B * 32 * HW));
         L.d_lo = take(4 * (size_t)(B * 32 * HW));
         L.part = take(sizeof(float) * (size_t)kDenoiseParts * (32 * 32 * 9 + 32));
+        L.wg = wa == 64 && B <= 65535 ? 1 : 0;
+        if (L.wg) {
+            L.dsplit = take(2 * (size_t)(B * 64 * HW));
+            L.shifted = take(2 * (size_t)(B * 96 * HW));
+            L.wgpart = take(sizeof(float) * (size_t)kWgMaxCtas * 64 * 288);
+            L.bpart = take(sizeof(float) * (size_t)B * ((HW + 255) / 256) * 32);
+            L.dcl_hi = take(2 * (size_t)(B * 32 * HW));
+            L.dcl_lo = take(2 * (size_t)(B * 32 * HW));
+            L.wtb = take(2 * (size_t)(2 * 9 * 32 * 32));
+        }
     }
     L.bytes = o;
     return L;
@@ -754,10 +1210,10 @@ cudaError_t forward_tc(const float* model, const float* gamma_in, const float* s
             !make_bf16_map_sw64(&w_map, wt + (size_t)l * 9 * 32 * 32, 3, wdims, wstr, wbox))
             return cudaErrorInvalidValue;
         if (l < 3)
-            dn_conv_tc_kernel<32><<<grid, kTcThreadsP, smem, st>>>(in_map, w_map, biases[l], acf[l], outs_cl[l],
+            dn_conv_tc_kernel<32><<<grid, kTcThreadsP, smem, st>>>(in_map, in_map, w_map, biases[l], acf[l], outs_cl[l],
                                                                    nullptr, nullptr, ha, wa, B, status, timeout_ns);
         else
-            dn_conv_tc_kernel<16><<<grid, kTcThreadsP, smem, st>>>(in_map, w_map, biases[l], nullptr, nullptr, x0, y,
+            dn_conv_tc_kernel<16><<<grid, kTcThreadsP, smem, st>>>(in_map, in_map, w_map, biases[l], nullptr, nullptr, x0, y,
                                                                    ha, wa, B, status, timeout_ns);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
@@ -798,7 +1254,8 @@ cudaError_t denoise_output(const uint8_t* ws, const DenoiseLayout& L, int64_t n,
 }
 
 cudaError_t denoise_backward(const float* model, const float* gamma_target, int ha, int wa, int hb, int wb,
-                             uint8_t* ws, const DenoiseLayout& L, float* grad, float* loss, cudaStream_t st) {
+                             uint8_t* ws, const DenoiseLayout& L, float* grad, float* loss, int sm_count,
+                             unsigned int* status, unsigned long long timeout_ns, cudaStream_t st) {
     const int B = hb * wb;
     const int64_t HW = (int64_t)ha * wa, n = (int64_t)B * HW;
     const float* scale = reinterpret_cast<const float*>(ws + L.scale);
@@ -816,16 +1273,46 @@ cudaError_t denoise_backward(const float* model, const float* gamma_target, int 
     dn_loss_kernel<<<1, 32, 0, st>>>(sums, kSumBlocks, n, loss);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    WgBuffers wgb{L.wg ? reinterpret_cast<__nv_bfloat16*>(ws + L.dsplit) : nullptr, nullptr, nullptr,
+                  L.wg ? reinterpret_cast<__nv_bfloat16*>(ws + L.shifted) : nullptr,
+                  L.wg ? reinterpret_cast<float*>(ws + L.wgpart) : nullptr,
+                  L.wg ? reinterpret_cast<float*>(ws + L.bpart) : nullptr};
+    __nv_bfloat16* dcl_hi = L.wg ? reinterpret_cast<__nv_bfloat16*>(ws + L.dcl_hi) : nullptr;
+    __nv_bfloat16* dcl_lo = L.wg ? reinterpret_cast<__nv_bfloat16*>(ws + L.dcl_lo) : nullptr;
+    __nv_bfloat16* wtb = L.wg ? reinterpret_cast<__nv_bfloat16*>(ws + L.wtb) : nullptr;
+    if (L.wg) {
+        dn_wprep_bwd_kernel<<<(2 * 9 * 32 * 32 + 255) / 256, 256, 0, st>>>(model, kW1, kW2, wtb);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     // layer 3 (32 -> 1): d at its output = dy
-    if ((e = wgrad<32, 1>(a3, dy, nullptr, B, ha, wa, kDenoiseParts, part, grad + kW3, st)) != cudaSuccess) return e;
+    if (L.wg) e = wgrad_tc<32, 32, 1>(a3, dy, nullptr, B, ha, wa, wgb, grad + kW3, sm_count, status, timeout_ns, st);
+    else e = wgrad<32, 1>(a3, dy, nullptr, B, ha, wa, kDenoiseParts, part, grad + kW3, st);
+    if (e != cudaSuccess) return e;
     if ((e = conv<1, 32, kBwdData>(dy, nullptr, model + kW3, nullptr, nullptr, dhi, B, ha, wa, st)) != cudaSuccess) return e;
     // layer 2: d at its output = dhi masked by a3
-    if ((e = wgrad<32, 32>(a2, dhi, a3, B, ha, wa, kDenoiseParts, part, grad + kW2, st)) != cudaSuccess) return e;
-    if ((e = conv<32, 32, kBwdData>(dhi, a3, model + kW2, nullptr, nullptr, dlo, B, ha, wa, st)) != cudaSuccess) return e;
+    if (L.wg) {   // the split of delta also feeds the tensor-core input gradient
+        wgb.cl_hi = dcl_hi;
+        wgb.cl_lo = dcl_lo;
+        e = wgrad_tc<32, 32, 32>(a2, dhi, a3, B, ha, wa, wgb, grad + kW2, sm_count, status, timeout_ns, st);
+        if (e == cudaSuccess)
+            e = conv_tc_bwd(dcl_hi, dcl_lo, wtb + 9 * 32 * 32, dlo, B, ha, wa, sm_count, status, timeout_ns, st);
+    } else {
+        e = wgrad<32, 32>(a2, dhi, a3, B, ha, wa, kDenoiseParts, part, grad + kW2, st);
+        if (e == cudaSuccess) e = conv<32, 32, kBwdData>(dhi, a3, model + kW2, nullptr, nullptr, dlo, B, ha, wa, st);
+    }
+    if (e != cudaSuccess) return e;
     // layer 1: d at its output = dlo masked by a2
-    if ((e = wgrad<32, 32>(a1, dlo, a2, B, ha, wa, kDenoiseParts, part, grad + kW1, st)) != cudaSuccess) return e;
-    if ((e = conv<32, 32, kBwdData>(dlo, a2, model + kW1, nullptr, nullptr, dhi, B, ha, wa, st)) != cudaSuccess) return e;
+    if (L.wg) {
+        e = wgrad_tc<32, 32, 32>(a1, dlo, a2, B, ha, wa, wgb, grad + kW1, sm_count, status, timeout_ns, st);
+        if (e == cudaSuccess) e = conv_tc_bwd(dcl_hi, dcl_lo, wtb, dhi, B, ha, wa, sm_count, status, timeout_ns, st);
+        wgb.cl_hi = wgb.cl_lo = nullptr;
+    } else {
+        e = wgrad<32, 32>(a1, dlo, a2, B, ha, wa, kDenoiseParts, part, grad + kW1, st);
+        if (e == cudaSuccess) e = conv<32, 32, kBwdData>(dlo, a2, model + kW1, nullptr, nullptr, dhi, B, ha, wa, st);
+    }
+    if (e != cudaSuccess) return e;
     // layer 0: d at its output = dhi masked by a1
+    if (L.wg) return wgrad_tc<9, 16, 32>(x0, dhi, a1, B, ha, wa, wgb, grad + kW0, sm_count, status, timeout_ns, st);
     return wgrad<9, 32>(x0, dhi, a1, B, ha, wa, kDenoiseParts, part, grad + kW0, st);
 }
 

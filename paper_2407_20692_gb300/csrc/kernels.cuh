@@ -137,13 +137,26 @@ struct DenoiseLayout {                    // byte offsets in the workspace
     // to 32 channels), a1 and a2, and the bf16 weights of layers 0..2; tc = 0 if
     // the width does not allow it
     int tc;
-    size_t xc, c1, c2, wt, bytes;
+    size_t xc, c1, c2, wt;
+    // tensor-core weight gradients (training, width 64): the layer's output
+    // gradient as two bf16 terms [slice][2 Cout][H][W], x-shifted copies of the
+    // layer input [slice][3 Cin'][H][W] (Cin' = 16 or 32), per-CTA partial sums
+    // and per-block bias sums; wg = 0 if the width does not allow it
+    int wg;
+    size_t dsplit, shifted, wgpart, bpart;
+    // and the input gradients of layers 2 and 1 on the tensor cores: the split
+    // delta channels-last (hi, lo) and the flipped bf16 weights of layers 1, 2
+    size_t dcl_hi, dcl_lo, wtb, bytes;
 };
+constexpr int kWgMaxCtas = 152 * 2;       // CTAs of a tensor-core weight-gradient pass (partial slots)
 // Tiled tensor map over a bfloat16 array of rank 3 or 4 with 64-byte swizzle
 // (box innermost extent 64 bytes); dims innermost first, strides in bytes for
 // dims 1..rank-1.  False if the driver rejects it.
 bool make_bf16_map_sw64(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
                         const uint32_t* box);
+// As make_bf16_map_sw64 with 128-byte swizzle (box innermost extent 128 bytes).
+bool make_bf16_map_sw128(CUtensorMap* m, const void* base, int rank, const uint64_t* dims, const uint64_t* strides,
+                         const uint32_t* box);
 DenoiseLayout denoise_layout(int ha, int wa, int hb, int wb, bool training);
 // scale, stacked input, activations and y of the network on gamma_in (keep_cf:
 // also the channels-first activations the backward pass reads; status,
@@ -155,7 +168,8 @@ cudaError_t denoise_output(const uint8_t* ws, const DenoiseLayout& L, int64_t n,
                            cudaStream_t st);
 // after denoise_forward: loss and gradient of the model blob
 cudaError_t denoise_backward(const float* model, const float* gamma_target, int ha, int wa, int hb, int wb,
-                             uint8_t* ws, const DenoiseLayout& L, float* grad, float* loss, cudaStream_t st);
+                             uint8_t* ws, const DenoiseLayout& L, float* grad, float* loss, int sm_count,
+                             unsigned int* status, unsigned long long timeout_ns, cudaStream_t st);
 cudaError_t denoise_adam(float* model, float* m, float* v, const float* grad, int64_t step, float lr,
                          cudaStream_t st);
 

@@ -99,6 +99,17 @@ def test_denoise_workspace_has_channels_last_buffers_for_tensor_core_widths():
         if wa in (32, 64, 128):
             want += 3 * up(64 * B * HW) + up(2 * (3 * 9 * 32 * 32 + 9 * 16 * 32))
         assert cpi.cpi_denoise_workspace_size(ha, wa, hb, wb) == want, (ha, wa, hb, wb)
+        # training adds dy, two float32 gradient buffers of 32 channels and the
+        # per-CTA partials; width 64 (tensor-core weight gradients) also the
+        # split gradient (64 bf16 channels), the shifted input copies (96 bf16
+        # channels), the GEMM partials (304 x 64 x 288 floats), the bias sums, the
+        # channels-last split gradient and the flipped weights of the input gradients
+        want += up(4 * B * HW) + 2 * up(4 * B * 32 * HW) + up(4 * 456 * (32 * 32 * 9 + 32))
+        if wa == 64:
+            want += up(2 * B * 64 * HW) + up(2 * B * 96 * HW) + up(4 * 304 * 64 * 288)
+            want += up(4 * B * (-(-HW // 256)) * 32)                       # bias sums per (slice, 256 pixels)
+            want += 2 * up(2 * B * 32 * HW) + up(2 * 2 * 9 * 32 * 32)      # channels-last split, flipped weights
+        assert cpi.cpi_denoise_workspace_size(ha, wa, hb, wb, training=True) == want, (ha, wa, hb, wb)
 
 
 def test_refocus4d_workspace_chunks_planes():

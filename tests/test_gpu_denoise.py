@@ -116,6 +116,28 @@ def test_denoise_gradient_through_tensor_core_forward_matches_oracle():
         o += n
 
 
+def test_denoise_gradient_tensor_core_weight_gradients_match_oracle():
+    """Images 64 pixels wide take the tensor-core weight gradients (delta split
+    into two bf16 terms, x-shifted input copies, one GEMM over the pixels per
+    layer); 40 rows make a ragged second block of rows.  Same tolerance as the
+    float32 path, and bit-identical on a second run."""
+    hb, wb, ha, wa = 2, 3, 40, 64
+    blob = _model(21)
+    g = _gamma(22, hb, wb, ha, wa)
+    t = _gamma(23, hb, wb, ha, wa) * 0.5 + g * 0.5
+    got, loss = _grad(blob, g, t, hb, wb, ha, wa)
+    want_loss, want = dn.loss_and_grad(blob, g.reshape(-1, ha, wa), t.reshape(-1, ha, wa), hb, wb)
+    assert abs(loss - want_loss) <= 1e-4 * want_loss
+    o = 0
+    for ci, co in dn.LAYERS:
+        n = co * ci * 9 + co
+        gl, wl = got[o:o + n], want[o:o + n]
+        assert np.abs(gl - wl).max() <= 2e-3 * np.abs(wl).max(), (ci, co, np.abs(gl - wl).max() / np.abs(wl).max())
+        o += n
+    again, loss2 = _grad(blob, g, t, hb, wb, ha, wa)
+    assert np.array_equal(got.view(np.uint32), again.view(np.uint32)) and loss2 == loss
+
+
 def _grad(blob, g, t, hb, wb, ha, wa):
     ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb, training=True), dtype=torch.uint8,
                      device="cuda")
