@@ -899,7 +899,6 @@ def run_denoise(args, world, rank):
         + (32 + 32 * 32 + 32 * 32)                 # input gradients of layers 3, 2, 1
         + (9 * 32 + 32 * 32 + 32 * 32 + 32))       # weight gradients
     step_s = train_ms / 1e3 / n_steps
-    peak = SM_COUNT * 128 * 2 * _peaks()[0].get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     ach = flops / step_s / 1e12
     # inference: the forward network on tcgen05 (widths 32/64/128), one Gamma
     fwd_flops = 2.0 * hb * wb * ha * wa * 9 * (9 * 32 + 32 * 32 + 32 * 32 + 32)
@@ -932,11 +931,13 @@ def run_denoise(args, world, rank):
                      "bound": "tensor", "achieved": fwd_ach, "peak": tc_peak, "unit": "TFLOP/s",
                      "frac": fwd_ach / tc_peak, "traffic": None, "peak_source": "measured bf16 burst",
                      "work": "forward network of one Gamma (1024 slices of 64 x 64; MMA padding not counted)"},
-        "roofline_training": {"kernel": "denoiser training step (forward on tcgen05; backward: direct bf16/fp32 "
-                                        "3x3 convolutions on the FP32 pipe)",
-                              "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
-                              "peak_source": "derived: 152 SMs x 128 FP32 FMA/clk x 2 x max SM clock",
-                              "work": "forward + input gradients + weight gradients of one Gamma (1024 slices)"},
+        "roofline_training": {"kernel": "denoiser training step (forward, hidden-layer input gradients and weight "
+                                        "gradients on tcgen05, gradients as two bf16 terms; last layer's input "
+                                        "gradient on the FP32 pipe)",
+                              "bound": "tensor", "achieved": ach, "peak": tc_peak, "unit": "TFLOP/s",
+                              "frac": ach / tc_peak, "peak_source": "measured bf16 burst",
+                              "work": "forward + input gradients + weight gradients of one Gamma (1024 slices), "
+                                      "counted once (the two bf16 terms and MMA padding not counted)"},
         "gpu_launches": None,
     }
 
