@@ -1053,7 +1053,8 @@ def run_paper_scale(args, world, rank):
 SPAD_FRAME_RATE = 1.0e5
 STREAM_CASES = {
     "spad_1bit": dict(block=8192, blocks=12),       # 64x64 vs 32x32 binary frames, 768 B each
-    "paper_roi": dict(block=16384, blocks=4),       # 256x256 vs 256x256 binary (.bin layout), 16 KiB each
+    "paper_roi": dict(block=32768, blocks=2),       # 256x256 vs 256x256 binary (.bin layout), 16 KiB each;
+                                                    # blocks of 64 files of 512 frames (Section 4.1)
 }
 
 

@@ -89,7 +89,13 @@ struct Unit {
 };
 
 // Unit u of the launch: its problem (binary search over first units), frame
-// chunk, output tile and K-block range.
+// chunk, output tile and K-block range.  Within a chunk the tiles run in groups
+// of kGroupM tile rows, column by column (row fastest), so the persistent CTAs
+// working at one time cover a block of about kGroupM rows x (CTAs / kGroupM)
+// columns of tiles: the A and B rows they stream stay within L2 (a row-by-row
+// order has every CTA of a wave read its own B rows, which for wide problems
+// do not fit and come from DRAM once per tile row).
+constexpr int kGroupM = 16;
 template <int K>
 __device__ __forceinline__ Unit decode_unit(const MomentsLaunch<K>& L, int u) {
     int lo = 0;
@@ -108,8 +114,12 @@ __device__ __forceinline__ Unit decode_unit(const MomentsLaunch<K>& L, int u) {
     w.prob = lo;
     w.chunk = local / per_chunk;
     const int t = local - w.chunk * per_chunk;
-    w.tm = t / P.tiles_n;
-    w.tn = t - w.tm * P.tiles_n;
+    const int g = t / (kGroupM * P.tiles_n);                       // group of tile rows
+    const int m0 = g * kGroupM;
+    const int gm = min(kGroupM, P.tiles_m - m0);                   // rows in this group
+    const int r = t - g * kGroupM * P.tiles_n;
+    w.tn = r / gm;
+    w.tm = m0 + (r - w.tn * gm);
     w.kb0 = w.chunk * P.kb_per_chunk;
     w.kb1 = min(w.kb0 + P.kb_per_chunk, P.k_blocks);
     return w;
