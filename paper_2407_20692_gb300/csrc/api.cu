@@ -278,11 +278,12 @@ void fill_problem(const CorrPlan& pl, int32_t* part, int unit_begin, MomentsProb
     P->tiles_n = pl.tiles_n;
     P->unit_begin = unit_begin;
     P->vmax = pl.bf16 ? vmax : nullptr;
+    P->add_partial = 0;
 }
 
 cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const cpi_frames* b,
                      int accumulate, int64_t* s_ab, int64_t* s_a, int64_t* s_b, double* gamma,
-                     float* gamma_f32, void* ws, DeviceInfo* dev, cudaStream_t st) {
+                     float* gamma_f32, void* ws, DeviceInfo* dev, cudaStream_t st, int add_partial = 0) {
     uint8_t* w = static_cast<uint8_t*>(ws);
     uint8_t* op_a = w + pl.off_a;
     uint8_t* op_b = w + pl.off_b;
@@ -310,6 +311,7 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
         L.map_a[0] = tm_a;
         L.map_b[0] = tm_b;
         fill_problem(pl, part, 0, &L.prob[0], vmax);
+        L.prob[0].add_partial = add_partial;
         L.n_problems = 1;
         L.n_units = pl.n_units;
         L.status = dev->status;
@@ -326,7 +328,7 @@ cpi_status run_stage(int stage, const CorrPlan& pl, const cpi_frames* a, const c
 cpi_status correlate_common(const int32_t* stages, int n_stages, const cpi_frames* a,
                             const cpi_frames* b, int64_t n_frames, int accumulate, int64_t* s_ab,
                             int64_t* s_a, int64_t* s_b, double* gamma, float* gamma_f32, void* ws,
-                            size_t ws_bytes, cpi_stream stream) {
+                            size_t ws_bytes, cpi_stream stream, int add_partial = 0) {
     DeviceInfo* dev = nullptr;
     if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
     CorrPlan pl;
@@ -347,7 +349,7 @@ cpi_status correlate_common(const int32_t* stages, int n_stages, const cpi_frame
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     for (int i = 0; i < n_stages; ++i) {
         s = run_stage(stages[i], pl, a, b, accumulate, s_ab, s_a, s_b, gamma, gamma_f32, ws, dev,
-                      st);
+                      st, add_partial);
         if (s != CPI_OK) return s;
     }
     return CPI_OK;
@@ -752,7 +754,27 @@ struct Acquisition {
     bool copied_once[2] = {false, false};
     int next = 0;
     int64_t n_done = 0;
+    // Binary frames: full blocks add their raw moments into the workspace's
+    // uint32 partial slots (every entry counts at most the 2^31 frames of an
+    // acquisition) and the fold into the int64 S_ab waits for a checkpoint
+    // (sync, finalize, end) or a block of another size.
+    bool defer = false;
+    int64_t deferred = 0;             // full blocks whose moments are still in the partial slots
+    size_t off_part = 0;              // partial slots of a full block's workspace layout
+    int n_chunks = 0;
 };
+
+// Fold the deferred partial sums into S_ab on the compute stream.
+cpi_status acq_flush(Acquisition* q) {
+    if (q->deferred == 0) return CPI_OK;
+    const int64_t ma = (int64_t)q->a.height * q->a.width, mb = (int64_t)q->b.height * q->b.width;
+    const int32_t* part = reinterpret_cast<const int32_t*>(q->ws + q->off_part);
+    const cudaError_t e = launch_fold(part, q->n_chunks, ma, mb, q->s_ab, 1, 1, q->s_a, q->s_b, q->n_done, nullptr,
+                                      nullptr, q->compute, 0);
+    if (e != cudaSuccess) return CPI_ERR_CUDA;
+    q->deferred = 0;
+    return CPI_OK;
+}
 
 size_t acq_staging_bytes(const cpi_frames* a, int64_t block_frames) {
     return round_up((size_t)block_frames * (size_t)a->frame_stride_bytes, 256);
@@ -1115,6 +1137,18 @@ cpi_status cpi_acq_begin(cpi_acq** out, const cpi_frames* a, const cpi_frames* b
     q->ws_bytes = workspace_bytes - 2 * sb;
     q->compute = reinterpret_cast<cudaStream_t>(stream);
     q->n_done = frames_done;
+    if (a->bits == 1 && b->bits == 1) {
+        DeviceInfo* dev = nullptr;
+        if (device_info(&dev) != cudaSuccess) return CPI_ERR_CUDA;
+        cpi_frames ta = *a, tb = *b;
+        ta.data = tb.data = w;
+        CorrPlan pl;
+        if (make_plan(&ta, &tb, block_frames, dev->sm_count, &pl) == CPI_OK) {
+            q->defer = true;
+            q->off_part = pl.off_part;
+            q->n_chunks = pl.n_chunks;
+        }
+    }
     if (cudaStreamCreateWithFlags(&q->copy, cudaStreamNonBlocking) != cudaSuccess) return CPI_ERR_CUDA;
     for (int k = 0; k < 2; ++k)
         if (cudaEventCreateWithFlags(&q->arrived[k], cudaEventDisableTiming) != cudaSuccess ||
@@ -1155,9 +1189,16 @@ cpi_status cpi_acq_push(cpi_acq* handle, const void* host_frames, int64_t n_fram
     a.data = dst;
     b.data = dst;
     static const int32_t stages[3] = {CPI_STAGE_INGEST, CPI_STAGE_MOMENTS, CPI_STAGE_FOLD};
-    const cpi_status st = correlate_common(stages, 3, &a, &b, n_frames, 1, q->s_ab, q->s_a, q->s_b, nullptr, nullptr,
-                                           q->ws, q->ws_bytes, reinterpret_cast<cpi_stream>(q->compute));
+    const bool defer = q->defer && n_frames == q->block_frames;
+    if (!defer) {
+        const cpi_status f = acq_flush(q);   // a block of another size uses another layout
+        if (f != CPI_OK) return f;
+    }
+    const cpi_status st = correlate_common(stages, defer ? 2 : 3, &a, &b, n_frames, 1, q->s_ab, q->s_a, q->s_b,
+                                           nullptr, nullptr, q->ws, q->ws_bytes,
+                                           reinterpret_cast<cpi_stream>(q->compute), defer && q->deferred > 0 ? 1 : 0);
     if (st != CPI_OK) return st;
+    if (defer) ++q->deferred;
     if (cudaEventRecord(q->consumed[k], q->compute) != cudaSuccess) return CPI_ERR_CUDA;
     q->copied_once[k] = true;
     // the previous block's host buffer is free once its copy has arrived
@@ -1177,6 +1218,8 @@ cpi_status cpi_acq_finalize(cpi_acq* handle, double* gamma, float* gamma_f32) {
     Acquisition* q = reinterpret_cast<Acquisition*>(handle);
     if (!q || q->n_done < 1) return CPI_ERR_INVALID_ARG;
     const int64_t ma = (int64_t)q->a.height * q->a.width, mb = (int64_t)q->b.height * q->b.width;
+    const cpi_status f = acq_flush(q);
+    if (f != CPI_OK) return f;
     return cpi_correlate_finalize(q->s_ab, q->s_a, q->s_b, ma, mb, q->n_done, gamma, gamma_f32,
                                   reinterpret_cast<cpi_stream>(q->compute));
 }
@@ -1184,6 +1227,8 @@ cpi_status cpi_acq_finalize(cpi_acq* handle, double* gamma, float* gamma_f32) {
 cpi_status cpi_acq_sync(cpi_acq* handle) {
     Acquisition* q = reinterpret_cast<Acquisition*>(handle);
     if (!q) return CPI_ERR_INVALID_ARG;
+    const cpi_status f = acq_flush(q);
+    if (f != CPI_OK) return f;
     if (cudaStreamSynchronize(q->copy) != cudaSuccess || cudaStreamSynchronize(q->compute) != cudaSuccess)
         return CPI_ERR_CUDA;
     return CPI_OK;
@@ -1192,7 +1237,7 @@ cpi_status cpi_acq_sync(cpi_acq* handle) {
 cpi_status cpi_acq_end(cpi_acq* handle) {
     Acquisition* q = reinterpret_cast<Acquisition*>(handle);
     if (!q) return CPI_ERR_INVALID_ARG;
-    cpi_status st = CPI_OK;
+    cpi_status st = acq_flush(q);
     if (q->copy && cudaStreamSynchronize(q->copy) != cudaSuccess) st = CPI_ERR_CUDA;
     if (q->compute && cudaStreamSynchronize(q->compute) != cudaSuccess) st = CPI_ERR_CUDA;
     for (int k = 0; k < 2; ++k) {

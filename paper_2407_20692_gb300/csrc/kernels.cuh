@@ -46,6 +46,8 @@ struct MomentsProblem {
     int32_t unit_begin;      // first unit of this problem in the launch
     const uint32_t* vmax;    // BF16 path: largest A and B value of the call's frames (written by
                              // ingest), which set the exact FP32 segment length
+    int32_t add_partial;     // 1: add the sums into the partial slots (uint32, wrapping never
+                             // reached: binary frames, fewer than 2^32 per slot) instead of storing
 };
 
 // A persistent launch over the units of up to K problems (K = 1 for a single

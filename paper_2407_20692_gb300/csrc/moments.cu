@@ -67,20 +67,29 @@ struct MomentsCfg {
     static constexpr size_t kSmem = 1024 + (size_t)kStages * (kABytes + kBBytes) + 256;
 };
 
-// Write 32 exact sums of output row m, columns nb .. nb+31 (those < N), to the
-// chunk's partial slot (uint32 bit patterns).
+// Write (with add_partial: add) 32 exact sums of output row m, columns
+// nb .. nb+31 (those < N), to the chunk's partial slot (uint32 bit patterns).
 __device__ __forceinline__ void store_row_chunk(const MomentsProblem& P, int chunk, int m, int nb,
                                                 const int32_t (&v)[32]) {
     if (m >= P.M) return;
     int32_t* out = P.partial + ((size_t)chunk * P.M + (size_t)m) * P.N;
+    const bool add = P.add_partial != 0;
     if ((P.N & 3) == 0 && nb + 32 <= P.N) {
         int4* o4 = reinterpret_cast<int4*>(out + nb);
 #pragma unroll
-        for (int j = 0; j < 8; ++j) o4[j] = make_int4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        for (int j = 0; j < 8; ++j) {
+            int4 w = make_int4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            if (add) {
+                const int4 o = o4[j];
+                w = make_int4((int)((uint32_t)w.x + (uint32_t)o.x), (int)((uint32_t)w.y + (uint32_t)o.y),
+                              (int)((uint32_t)w.z + (uint32_t)o.z), (int)((uint32_t)w.w + (uint32_t)o.w));
+            }
+            o4[j] = w;
+        }
     } else {
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-            if (nb + j < P.N) out[nb + j] = v[j];
+            if (nb + j < P.N) out[nb + j] = add ? (int32_t)((uint32_t)out[nb + j] + (uint32_t)v[j]) : v[j];
     }
 }
 

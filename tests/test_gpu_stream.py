@@ -92,6 +92,35 @@ def test_checkpoint_and_resume():
     assert_exact({"s_ab": r_ab.cpu(), "s_a": r_a.cpu(), "s_b": r_b.cpu(), "gamma": g.cpu()}, want)
 
 
+def test_binary_blocks_of_mixed_sizes():
+    """Binary acquisitions keep the raw moments of full blocks in the workspace's
+    uint32 partial slots and fold them into S_ab at a checkpoint or before a
+    block of another size: full, full, short, full, full, then Gamma, against the
+    oracle bit for bit."""
+    sizes = [1024, 1024, 300, 1024, 1024]
+    n = sum(sizes)
+    acq = synth.Acquisition(48, 24, n, 0.3, "bernoulli", seed=123)
+    A, B = synth.generate(acq, "cuda")
+    fr, lay = synth.pack_side_by_side(A, B, 1)
+    host = fr.cpu().pin_memory()
+    a, b = desc(fr, lay["a"]), desc(fr, lay["b"])
+    ma, mb = 48 * 48, 24 * 24
+    s_ab, s_a, s_b = _outputs(ma, mb)
+    ws = torch.empty(cpi.cpi_acq_workspace_size(a, b, 1024), dtype=torch.uint8, device="cuda")
+    h = cpi.cpi_acq_begin(a, b, 1024, s_ab, s_a, s_b, ws)
+    f0 = 0
+    for k in sizes:
+        cpi.cpi_acq_push(h, host[f0:f0 + k], k)
+        f0 += k
+    g = torch.empty((ma, mb), dtype=torch.float64, device="cuda")
+    cpi.cpi_acq_finalize(h, g, None)
+    cpi.cpi_acq_end(h)
+    torch.cuda.synchronize()
+    assert cpi.cpi_device_status() == 0
+    want = oracle_correlate(fr.cpu().numpy(), lay["a"], lay["b"], n)
+    assert_exact({"s_ab": s_ab.cpu(), "s_a": s_a.cpu(), "s_b": s_b.cpu(), "gamma": g.cpu()}, want)
+
+
 def test_acquisition_argument_errors():
     fr = torch.zeros(4096, dtype=torch.uint8, device="cuda")
     a = cpi.frames(fr, 1, 8, 8, 0, 0, 16, 16)
