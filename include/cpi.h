@@ -169,7 +169,10 @@ CPI_API cpi_status cpi_correlate_stage(int32_t stage, const cpi_frames *a, const
  * cpi_correlate_accumulate) on the caller's stream.  The running sums s_ab,
  * s_a, s_b and the frame count are the whole state of the correlation:
  * cpi_acq_sync makes them consistent (a checkpoint), and cpi_acq_begin with
- * frames_done > 0 resumes from saved sums.
+ * frames_done > 0 resumes from saved sums.  Between checkpoints s_ab may lag
+ * the pushed frames: for binary frames the sums of full blocks stay in the
+ * workspace until the next cpi_acq_sync, cpi_acq_finalize, cpi_acq_end or a
+ * block of fewer frames.
  *
  * Layout: a and b describe the two regions inside ONE frame buffer (their
  * `data` is ignored; both must have the same frame_stride_bytes); a host block
