@@ -612,15 +612,24 @@ __global__ void __launch_bounds__(256) dn_dsplit_kernel(const float* __restrict_
     const int b = blockIdx.y;
     const int64_t p0 = (int64_t)blockIdx.x * kSplitPix, p = p0 + threadIdx.x;
     const bool in = p < HW;
+    // every channel's loads first (all in flight together), then the split
+    float v[COUT];
+#pragma unroll
+    for (int co = 0; co < COUT; ++co) v[co] = in ? __ldg(d + ((int64_t)b * COUT + co) * HW + p) : 0.0f;
+    if (mask != nullptr && in) {
+        unsigned short m[COUT];
+#pragma unroll
+        for (int co = 0; co < COUT; ++co)
+            m[co] = __ldg(reinterpret_cast<const unsigned short*>(mask) + ((int64_t)b * COUT + co) * HW + p);
+#pragma unroll
+        for (int co = 0; co < COUT; ++co)
+            if (!(__uint_as_float((uint32_t)m[co] << 16) > 0.0f)) v[co] = 0.0f;
+    }
 #pragma unroll
     for (int co = 0; co < COUT; ++co) {
-        float v = 0.0f;
         if (in) {
-            const int64_t idx = ((int64_t)b * COUT + co) * HW + p;
-            v = d[idx];
-            if (mask != nullptr && !(__bfloat162float(mask[idx]) > 0.0f)) v = 0.0f;
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            const __nv_bfloat16 lo = __float2bfloat16_rn(v - __bfloat162float(hi));
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v[co]);
+            const __nv_bfloat16 lo = __float2bfloat16_rn(v[co] - __bfloat162float(hi));
             out[((int64_t)b * 2 * COUT + co) * HW + p] = hi;
             out[((int64_t)b * 2 * COUT + COUT + co) * HW + p] = lo;
             if constexpr (COUT > 1) {
@@ -628,10 +637,14 @@ __global__ void __launch_bounds__(256) dn_dsplit_kernel(const float* __restrict_
                 reinterpret_cast<__nv_bfloat16*>(stage[1][threadIdx.x])[co] = lo;
             }
         }
-        // the warp's 32 pixels in a fixed butterfly, then the 8 warps in order
+    }
+    // bias terms: the warp's 32 pixels in a fixed butterfly, then the 8 warps in order
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][co] = v;
+    for (int co = 0; co < COUT; ++co) {
+        float t = v[co];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][co] = t;
     }
     __syncthreads();
     if constexpr (COUT > 1) {
