@@ -170,15 +170,14 @@ __global__ void __launch_bounds__(256) refocus_xtables_kernel(const PlaneBlock p
     }
 }
 
-// PT planes per thread, G groups of kBandThreads threads per CTA: a unit holds
-// PB = PT * G planes, group g taking planes g * PT .. g * PT + PT - 1 of it, so
-// every staged value serves PB planes while each thread keeps the sums of PT.
-template <int WS, int KR, int PT, int G>
-__global__ void __launch_bounds__(kBandThreads * G, 1) refocus_band_kernel(const __grid_constant__ CUtensorMap tm,
+// PT planes per thread: a unit holds PB = PT planes, so every staged value
+// serves PB planes while each thread keeps the sums of all of them.
+template <int WS, int KR, int PT>
+__global__ void __launch_bounds__(kBandThreads, 1) refocus_band_kernel(const __grid_constant__ CUtensorMap tm,
                                                                            const BandGeom g, const PlaneBlock pl,
                                                                            float* __restrict__ ubuf) {
-    constexpr int NW = kBandThreads * G / 32;
-    constexpr int PB = PT * G;
+    constexpr int NW = kBandThreads / 32;
+    constexpr int PB = PT;
     static_assert(PT % 2 == 0, "planes are processed in pairs");
     extern __shared__ __align__(128) float sm_raw[];
     float* const buf0 =
@@ -190,9 +189,7 @@ __global__ void __launch_bounds__(kBandThreads * G, 1) refocus_band_kernel(const
     const int stages = g.stages;
     const int slice_f = (g.BH * WS + 31) & ~31;    // floats per stage buffer (128-byte multiple)
     const int tid = threadIdx.x, lane = tid & 31;
-    const int grp = G > 1 ? tid / kBandThreads : 0;
-    const int tg = G > 1 ? tid - grp * kBandThreads : tid;
-    const int c = tg % g.cwt, rp = tg / g.cwt;
+    const int c = tid % g.cwt, rp = tid / g.cwt;
     const bool active = rp < g.R;
     const int per_br = g.n_pb * g.n_bands;
     const int n_units = hb * per_br;
@@ -239,7 +236,7 @@ __global__ void __launch_bounds__(kBandThreads * G, 1) refocus_band_kernel(const
         long long X[PT], dB[PT];
 #pragma unroll
         for (int j = 0; j < PT; ++j) {
-            const int pj = p0 + min(grp * PT + j, np - 1);
+            const int pj = p0 + min(j, np - 1);
             X[j] = __ldg(g.xcol + (size_t)pj * kBandThreads + c) + __ldg(g.xang + 2 * pj);
             dB[j] = __ldg(g.xang + 2 * pj + 1);
         }
@@ -343,7 +340,7 @@ __global__ void __launch_bounds__(kBandThreads * G, 1) refocus_band_kernel(const
                     unpk2(sub2(U[q][kk], C[q][kk]), v[0], v[1]);
 #pragma unroll
                     for (int l = 0; l < 2; ++l) {
-                        const int j = grp * PT + 2 * q + l;
+                        const int j = 2 * q + l;
                         if (j < np && row < ha)
                             ubuf[((int64_t)(p0 + j) * hb + br) * Ma + (int64_t)row * wa + c] = v[l];
                     }
@@ -515,13 +512,13 @@ cudaError_t set_smem_attr(K kernel, int slot, size_t bytes) {
     return cudaSuccess;
 }
 
-template <int WS, int KR, int PT, int G = 1>
+template <int WS, int KR, int PT>
 cudaError_t launch_band_t(const CUtensorMap* tm, const BandGeom& g, const PlaneBlock& pl, float* ubuf, size_t smem,
                           int grid, cudaStream_t st, int slot) {
-    auto kern = refocus_band_kernel<WS, KR, PT, G>;
+    auto kern = refocus_band_kernel<WS, KR, PT>;
     cudaError_t e = set_smem_attr(kern, slot, kSmemCap);
     if (e != cudaSuccess) return e;
-    kern<<<grid, kBandThreads * G, smem, st>>>(*tm, g, pl, ubuf);
+    kern<<<grid, kBandThreads, smem, st>>>(*tm, g, pl, ubuf);
     return cudaGetLastError();
 }
 
