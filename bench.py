@@ -676,7 +676,7 @@ def run_batched(args, world, rank):
 
 # Learned denoiser: 64x64 vs 32x32 uint8 Poisson counts (mean 2 photons), a
 # seeded object per pair; inputs Gamma from N_in = 1000 frames, targets the
-# closed-form expected Gamma; judged on held-out seeds against the plain Gamma.
+# closed-form expected Gamma; evaluated on held-out seeds against the plain Gamma.
 DENOISE = dict(side_a=64, side_b=32, n_in=1000, mean=2.0, train_seeds=256, epochs=12, eval_seeds=6,
                n_eval=(1000, 2000, 5000, 10000, 20000, 50000), n_den=(1000, 2000, 5000), n_head=5000, lr=2e-3,
                planes=32)

@@ -349,8 +349,8 @@ CPI_API cpi_status cpi_correlate_noalloc(const cpi_frames *a, const cpi_frames *
  * Learned denoiser of Gamma.  The paper has no counterpart: this is the
  * project's "learned denoiser" row, a small convolutional network that maps
  * Gamma of Eq. (1) measured from few frames to Gamma of many frames, trained on
- * pairs the method generates; the plain Gamma stays the fallback and the judge
- * of its error.
+ * pairs the method generates; the plain Gamma stays the fallback and the
+ * reference its error is measured against.
  *
  * Network, per angular slice b = (br, bc) of Gamma (float [hb*wb][ha*wa],
  * slice-major: cpi_correlate's gamma_f32):

@@ -2,7 +2,7 @@
 // "learned denoiser" row): a 4-layer 3 x 3 convolutional network that maps
 // Gamma measured from few frames to Gamma of many frames, trained on pairs the
 // method generates.  The plain Gamma of Eq. (1) stays the fallback and the
-// judge of its error.
+// reference its error is measured against.
 //
 // Network, per angular slice b = (br, bc) of Gamma (float [Mb][ha * wa]):
 //   input x: 9 channels, the slices of the 3 x 3 angular neighbourhood
