@@ -309,7 +309,7 @@ def run_native(args, world, rank, local):
 def _dtype(bits):
     if bits == 1:
         return "u1 -> e4m3 tensor-core (exact fp32 partials), int64 sums, f64 Gamma, f32 refocus"
-    return ("u8 -> bf16 tensor-core (exact fp32 partials folded into int32 every S frames, S certified from the "
+    return ("u8 -> bf16 tensor-core (exact fp32 segments below 2^24 added into uint32 every S frames, S certified from the "
             "recorded maxima), int64 sums, f64 Gamma, f32 refocus")
 
 
@@ -467,7 +467,7 @@ def measure_single(args, workload, world, rank, with_cpu=True, with_errors=True,
         "graph_replay": {"ms_per_step": graph_ms, "value": world * ops / (graph_ms / 1e3) / 1e12,
                          "unit": "TOPS (int8-equivalent)",
                          "call": "cpi_batch_correlate, one item, CPI_BATCH_GRAPH | CPI_BATCH_TUNE"},
-        "gpu_launches": KERNELS_PER_STEP * args.steps,
+        "gpu_launches": kernels_per_step(wa, n_planes) * args.steps,
         "clocks": clocks,
         "wall_s_timed_region": t_wall,
         "input_generation_s": t_gen,
@@ -482,9 +482,13 @@ def measure_single(args, workload, world, rank, with_cpu=True, with_errors=True,
     return line
 
 
-# Kernels one step launches: ingest, raw-moment GEMM, fold, refocusing pass (one
-# per 128 planes; every workload here has at most 128), angular-row reduction.
-KERNELS_PER_STEP = 5
+def kernels_per_step(wa, n_planes):
+    """Kernels one step launches: ingest, raw-moment GEMM, fold, then per chunk of
+    up to 128 planes the x coordinate tables, the x stage and the y stage, plus
+    one repack of Gamma when its rows are not 16-byte aligned for the staging
+    copies (widths not a multiple of 4, or of 16 above 248)."""
+    repack = (wa % 4 != 0) if wa <= 248 else (wa % 16 != 0)
+    return 3 + 3 * -(-n_planes // 128) + (1 if repack else 0)
 
 
 SM_COUNT = 152
