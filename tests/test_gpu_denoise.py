@@ -138,6 +138,24 @@ def test_denoise_gradient_tensor_core_weight_gradients_match_oracle():
     assert np.array_equal(got.view(np.uint32), again.view(np.uint32)) and loss2 == loss
 
 
+def test_denoise_tensor_core_weight_gradients_over_many_units():
+    """192 slices of 16 x 64: more row units than CTAs, so CTAs accumulate several
+    units in tensor memory before writing their partial sums."""
+    hb, wb, ha, wa = 8, 24, 16, 64
+    blob = _model(31)
+    g = _gamma(32, hb, wb, ha, wa)
+    t = _gamma(33, hb, wb, ha, wa) * 0.5 + g * 0.5
+    got, loss = _grad(blob, g, t, hb, wb, ha, wa)
+    want_loss, want = dn.loss_and_grad(blob, g.reshape(-1, ha, wa), t.reshape(-1, ha, wa), hb, wb)
+    assert abs(loss - want_loss) <= 1e-4 * want_loss
+    o = 0
+    for ci, co in dn.LAYERS:
+        n = co * ci * 9 + co
+        gl, wl = got[o:o + n], want[o:o + n]
+        assert np.abs(gl - wl).max() <= 2e-3 * np.abs(wl).max(), (ci, co, np.abs(gl - wl).max() / np.abs(wl).max())
+        o += n
+
+
 def _grad(blob, g, t, hb, wb, ha, wa):
     ws = torch.empty(cpi.cpi_denoise_workspace_size(ha, wa, hb, wb, training=True), dtype=torch.uint8,
                      device="cuda")
