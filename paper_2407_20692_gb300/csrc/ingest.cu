@@ -14,7 +14,6 @@
 // Frames at or beyond n_frames are written as 0, so every operand row is padded
 // to a whole number of CTA tiles.  The same pass adds the marginal sums
 // S_a = sum_i A_i (Eq. (1), second term) with exact int64 atomics.
-#include <cuda_bf16.h>
 
 #include "kernels.cuh"
 
@@ -69,9 +68,11 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
             if (valid && f + 1 < n_frames) hi = load_pixel(d, base, sh, f + 1);
             sum += lo + hi;
             mx = max(mx, max(lo, hi));
-            const uint32_t blo = __bfloat16_as_ushort(__float2bfloat16_rn((float)lo));
-            const uint32_t bhi = __bfloat16_as_ushort(__float2bfloat16_rn((float)hi));
-            w[j] = blo | (bhi << 16);
+            // BF16 of v < 2^8 without the conversion pipe: (2^23 + v) - 2^23 = v exactly,
+            // and its upper half is BF16(v)
+            const float flo = __uint_as_float(0x4B000000u | lo) - 8388608.0f;
+            const float fhi = __uint_as_float(0x4B000000u | hi) - 8388608.0f;
+            w[j] = __byte_perm(__float_as_uint(flo), __float_as_uint(fhi), 0x7632u);
         }
     } else {
 #pragma unroll
