@@ -32,7 +32,9 @@ constexpr int kRowsPerThread = kTile / 8;
 
 // CTA = 32 x 32 entries (32 x 8 threads, 4 rows each).  Every load of a
 // thread's 4 entries is issued before any of them is used, so their latencies
-// overlap; then the 4 quotients are formed and stored.
+// overlap; then the 4 quotients are formed and stored.  Idx: int32_t when every
+// index (chunk slots included) fits, else int64_t.
+template <typename Idx>
 __global__ void __launch_bounds__(256, 4) fold_kernel(const int32_t* __restrict__ partial,
                                                    int n_chunks, int64_t M, int64_t N,
                                                    int64_t* s_ab, int accumulate, int write_sab,
@@ -42,32 +44,32 @@ __global__ void __launch_bounds__(256, 4) fold_kernel(const int32_t* __restrict_
                                                    float* gamma_f32) {
     __shared__ float tile[kTile][kTile + 1];
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;    // 32 x 8
-    const int64_t b = (int64_t)blockIdx.x * kTile + tx;
+    const Idx b = (Idx)blockIdx.x * kTile + tx;
     const bool want_g = gamma != nullptr || gamma_f32 != nullptr;
-    const int64_t plane = M * N;
-    const int64_t row_tiles = (M + kTile - 1) / kTile;
+    const Idx plane = (Idx)(M * N);
+    const Idx row_tiles = (Idx)((M + kTile - 1) / kTile);
     const int64_t sb = (want_g && b < N) ? __ldg(s_b + b) : 0;
-    for (int64_t rt = blockIdx.y; rt < row_tiles; rt += gridDim.y) {
-        const int64_t a0 = rt * kTile;
+    for (Idx rt = blockIdx.y; rt < row_tiles; rt += gridDim.y) {
+        const Idx a0 = rt * kTile;
         int64_t sum[kRowsPerThread], sa[kRowsPerThread];
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
-            const int64_t a = a0 + ty + 8 * k;
+            const Idx a = a0 + ty + 8 * k;
             sum[k] = (accumulate && a < M && b < N) ? s_ab[a * N + b] : 0;
             sa[k] = (want_g && a < M) ? __ldg(s_a + a) : 0;
         }
         for (int c = 0; c < n_chunks; ++c) {
 #pragma unroll
             for (int k = 0; k < kRowsPerThread; ++k) {
-                const int64_t a = a0 + ty + 8 * k;
-                if (a < M && b < N) sum[k] += (int64_t)(uint32_t)__ldg(partial + (int64_t)c * plane + a * N + b);
+                const Idx a = a0 + ty + 8 * k;
+                if (a < M && b < N) sum[k] += (int64_t)(uint32_t)__ldg(partial + (Idx)c * plane + a * (Idx)N + b);
             }
         }
 #pragma unroll
         for (int k = 0; k < kRowsPerThread; ++k) {
-            const int64_t a = a0 + ty + 8 * k;
+            const Idx a = a0 + ty + 8 * k;
             if (a < M && b < N) {
-                const int64_t idx = a * N + b;
+                const Idx idx = a * (Idx)N + b;
                 if (write_sab) s_ab[idx] = sum[k];
                 if (want_g) {
                     const double g = wide ? gamma_from_sums_wide(sum[k], sa[k], sb, gd)
@@ -82,9 +84,9 @@ __global__ void __launch_bounds__(256, 4) fold_kernel(const int32_t* __restrict_
             // slice-major copy: gamma_f32[b][a]
 #pragma unroll
             for (int k = 0; k < kTile / 8; ++k) {
-                const int64_t bb = (int64_t)blockIdx.x * kTile + ty + 8 * k;
-                const int64_t aa = a0 + tx;
-                if (aa < M && bb < N) gamma_f32[bb * M + aa] = tile[tx][ty + 8 * k];
+                const Idx bb = (Idx)blockIdx.x * kTile + ty + 8 * k;
+                const Idx aa = a0 + tx;
+                if (aa < M && bb < N) gamma_f32[bb * (Idx)M + aa] = tile[tx][ty + 8 * k];
             }
             __syncthreads();
         }
@@ -99,9 +101,15 @@ cudaError_t launch_fold(const int32_t* partial, int n_chunks, int64_t M, int64_t
                         cudaStream_t st, int wide) {
     const int64_t gx = (N + kTile - 1) / kTile, gy = (M + kTile - 1) / kTile;
     const unsigned gyl = (unsigned)(gy < 65535 ? gy : 65535);
-    fold_kernel<<<dim3((unsigned)gx, gyl), 256, 0, st>>>(partial, n_chunks, M, N, s_ab, accumulate,
-                                                         write_sab, s_a, s_b,
-                                                         make_gamma_div(n_frames), wide, gamma, gamma_f32);
+    const int64_t span = M * N * (n_chunks > 1 ? n_chunks : 1) + (int64_t)kTile * (M + N);
+    if (span < ((int64_t)1 << 31))
+        fold_kernel<int32_t><<<dim3((unsigned)gx, gyl), 256, 0, st>>>(
+            partial, n_chunks, M, N, s_ab, accumulate, write_sab, s_a, s_b, make_gamma_div(n_frames), wide, gamma,
+            gamma_f32);
+    else
+        fold_kernel<int64_t><<<dim3((unsigned)gx, gyl), 256, 0, st>>>(
+            partial, n_chunks, M, N, s_ab, accumulate, write_sab, s_a, s_b, make_gamma_div(n_frames), wide, gamma,
+            gamma_f32);
     return cudaGetLastError();
 }
 
