@@ -16,7 +16,7 @@
 //     rarely or never.  Each segment sum, an integer below 2^24, converts
 //     exactly (cvt.rni.u32.f32).  (Bounding the segments by 2^23 instead, where
 //     f + 2^23 gives the integer in its bit pattern without a conversion,
-//     halves S; measured slower, 4.65 -> 5.25 ms on 128x128 vs 64x64 with
+//     halves S; measured slower, 3.95 -> 4.23 ms on 128x128 vs 64x64 with
 //     N = 50000.)  A chunk of <= 65536 frames keeps each total below
 //     65536 x 255^2 < 2^32 (the running sums are uint32: every product is
 //     non-negative).
@@ -237,7 +237,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------------- MMA issuer
+            // The tensor pipe takes one 128 x 256 x 16 (BF16) or x 32 (E4M3) MMA
+            // per 128 cycles only while this thread issues the next one within
+            // that time, so the loop keeps its per-K-block work to a few adds:
+            // segment bounds are counted down (no division), descriptors step
+            // by the stage size.
             constexpr uint32_t idesc = idesc_f32acc<kBf16>(kBlockM, C::kBlockN);
+            const uint64_t da0 = sdesc_kmajor_sw128(smem_u32(sA));
+            const uint64_t db0 = sdesc_kmajor_sw128(smem_u32(sB));
             int stage = 0;
             uint32_t phase = 0;
             int acc = 0;
@@ -245,28 +252,28 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true, issued_any = false;
             for (int u = blockIdx.x; ok && u < L.n_units; u += gridDim.x) {
                 const Unit w = decode_unit<K>(L, u);
-                const int kb_per_fold = kBf16 ? seg_kb[w.prob] : 0;
-                const int kb0 = w.kb0, kb1 = w.kb1;
-                for (int kb = kb0; kb < kb1; ++kb) {
-                    const int local = kb - kb0;
-                    const bool seg_start = kBf16 ? (local % kb_per_fold == 0) : (local == 0);
-                    const bool seg_end =
-                        kBf16 ? ((local + 1) % kb_per_fold == 0 || kb + 1 == kb1) : (kb + 1 == kb1);
+                const int nkb = w.kb1 - w.kb0;
+                const int kb_per_seg = kBf16 ? seg_kb[w.prob] : nkb;
+                int seg_left = 0;   // K blocks left in the current segment
+                for (int i = 0; i < nkb; ++i) {
+                    const bool seg_start = seg_left == 0;
                     if (seg_start) {
+                        seg_left = min(kb_per_seg, nkb - i);
                         if (!mbar_wait_bounded(&tempty[acc], acc_phase ^ 1, abort_flag, status, tmo)) {
                             ok = false;
                             break;
                         }
                         tc_fence_after();
                     }
+                    --seg_left;
                     if (!mbar_wait_bounded(&full[stage], phase, abort_flag, status, tmo)) {
                         ok = false;
                         break;
                     }
                     tc_fence_after();
                     const uint32_t d = tmem_base + (uint32_t)(acc * C::kBlockN);
-                    const uint64_t da = sdesc_kmajor_sw128(smem_u32(sA + stage * C::kABytes));
-                    const uint64_t db = sdesc_kmajor_sw128(smem_u32(sB + stage * C::kBBytes));
+                    const uint64_t da = da0 + (uint64_t)(stage * (C::kABytes >> 4));
+                    const uint64_t db = db0 + (uint64_t)(stage * (C::kBBytes >> 4));
 #pragma unroll
                     for (int k = 0; k < kRowBytes / 32; ++k) {
                         // advance the start address by 32 bytes (2 x 16-byte units) per MMA
@@ -279,7 +286,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         stage = 0;
                         phase ^= 1;
                     }
-                    if (seg_end) {
+                    if (seg_left == 0) {   // segment (BF16) or unit (E4M3) done: hand the accumulator over
                         umma_commit(&tfull[acc]);
                         if (++acc == C::kAcc) {
                             acc = 0;
