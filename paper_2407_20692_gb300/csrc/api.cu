@@ -83,17 +83,20 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 2-D K-major operand [rows][kstride_bytes], tile box = 128 bytes x box_rows, 128B swizzle.
+// 2-D K-major operand [rows][kstride_bytes], 128B swizzle.  BF16: tile box = 64
+// elements (128 bytes) x box_rows.  Binary (E2M1 packed two per byte): box =
+// 128 elements (64 bytes in HBM) x box_rows, each 8-byte group of 16 elements
+// landing in 16 bytes of shared memory (128 bytes per box row, the layout the
+// tensor cores read 4-bit operands in).
 bool make_operand_map(CUtensorMap* m, void* base, bool bf16, int64_t rows, int64_t kstride_bytes,
                       int box_rows) {
     EncodeTiledFn enc = encode_fn();
     if (!enc) return false;
-    const int elem = bf16 ? 2 : 1;
-    cuuint64_t dims[2] = {(cuuint64_t)(kstride_bytes / elem), (cuuint64_t)rows};
+    cuuint64_t dims[2] = {(cuuint64_t)(bf16 ? kstride_bytes / 2 : kstride_bytes * 2), (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)kstride_bytes};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / elem), (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)(bf16 ? 64 : 128), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+    CUresult r = enc(m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_16U4_ALIGN16B, 2,
                      base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
@@ -197,7 +200,8 @@ FramesDev to_dev(const cpi_frames* f) {
 struct CorrPlan {
     bool bf16;                 // BF16 operands (any 8-bit input) or FP8 (both binary)
     int64_t Ma, Mb, n;
-    int64_t kstride_bytes;     // operand row length in bytes (frames padded to the ingest tile)
+    int64_t kstride_bytes;     // operand row length in bytes (frames padded to the ingest tile;
+                               // 2 bytes per frame BF16, half a byte E2M1)
     int k_blocks, kb_per_chunk, n_chunks;
     int block_n, tiles_m, tiles_n, n_units;
     size_t off_a, off_b, off_part, off_vmax, off_sa, off_sb, ws_bytes;   // off_sa/off_sb: S_a, S_b when the caller passes none
@@ -222,8 +226,7 @@ cpi_status make_plan(const cpi_frames* a, const cpi_frames* b, int64_t n, int sm
     p.n = n;
     const int fpc = ingest_frames_per_cta(p.bf16);
     const int64_t kpad = (int64_t)round_up((size_t)n, (size_t)fpc);
-    const int elem = p.bf16 ? 2 : 1;
-    p.kstride_bytes = kpad * elem;
+    p.kstride_bytes = p.bf16 ? kpad * 2 : kpad / 2;   // BF16, or E2M1 two frames per byte
     if (block_n != 128 && block_n != 256) return CPI_ERR_INVALID_ARG;
     const MomentsShape sh = moments_shape(p.bf16, block_n);
     p.k_blocks = (int)(kpad / sh.k_per_block);

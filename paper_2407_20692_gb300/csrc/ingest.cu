@@ -5,12 +5,18 @@
 // raw-moment contraction sums over frames, so each operand row must hold one
 // pixel's values over consecutive frames (K-major):
 //   - 1-bit frames whose region rows are whole 32-pixel words apart ->
-//     FP8 E4M3 bytes (0x00 / 0x38 = 1.0), ingest_bits_kernel: a block of frames
-//     staged word-wise in shared memory, transposed 32 x 32 bits per warp;
+//     FP4 E2M1 values packed two per byte (0x0 / 0x2 = 1.0; frame 2j in the low
+//     nibble of byte j), ingest_bits_kernel: a block of frames staged word-wise
+//     in shared memory, transposed 32 x 32 bits per warp;
 //   - 8-bit frames with 4-pixel aligned regions -> BF16 (integers 0..255 are
 //     exact), ingest_u8x4_kernel: one CTA per tile of 128 pixels x 128 frames;
 //   - any other frames -> BF16 (1-bit frames that do not meet the first case as
-//     E4M3), one CTA per tile of 32 pixels x 256 output bytes.
+//     packed E2M1), one CTA per tile of 32 pixels x 128 (BF16) or 256 (E2M1)
+//     frames.
+// The raw-moment GEMM loads the packed E2M1 rows with a tensor map of 16 x 4-bit
+// groups, which spreads each 8-byte group over 16 bytes of shared memory: the
+// layout tcgen05 kind::f8f6f4 reads 4-bit operands in.  A binary operand row is
+// so half as many bytes in HBM and L2 as an 8-bit one would be.
 // Frames at or beyond n_frames are written as 0, so every operand row is padded
 // to a whole number of CTA tiles.  The same pass adds the marginal sums
 // S_a = sum_i A_i (Eq. (1), second term) with exact int64 atomics.
@@ -76,22 +82,26 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
         }
     } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < 4; ++j) {
             uint32_t word = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int64_t f = f0 + 4 * j + q;
+            for (int q = 0; q < 8; ++q) {
+                const int64_t f = f0 + 8 * j + q;
                 uint32_t v = 0;
                 if (valid && f < n_frames) v = load_pixel(d, base, sh, f);
                 sum += v;
-                word |= (v ? 0x38u : 0u) << (8 * q);   // E4M3 1.0 = 0x38
+                word |= (v ? 0x2u : 0u) << (4 * q);   // E2M1 1.0 = 0x2, frame 2k in the low nibble
             }
             w[j] = word;
         }
     }
-    uint4* dst = reinterpret_cast<uint4*>(&tile_s[lane][warp * 32]);
-    dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
-    dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    if constexpr (kBf16) {
+        uint4* dst = reinterpret_cast<uint4*>(&tile_s[lane][warp * 32]);
+        dst[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        dst[1] = make_uint4(w[4], w[5], w[6], w[7]);
+    } else {
+        *reinterpret_cast<uint4*>(&tile_s[lane][warp * 16]) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
     part[warp][lane] = sum;
     if constexpr (kBf16) {
         mx = __reduce_max_sync(0xffffffffu, mx);
@@ -107,17 +117,18 @@ __global__ void __launch_bounds__(256) ingest_kernel(FramesDev A, FramesDev B, i
         if (m > *reinterpret_cast<volatile uint32_t*>(slot)) atomicMax(slot, m);
     }
 
-    // 32 rows x 256 bytes = 512 chunks of 16 bytes; consecutive threads write
-    // consecutive chunks of one operand row.
+    // 32 rows x 256 bytes (BF16) or 128 bytes (E2M1) in chunks of 16 bytes;
+    // consecutive threads write consecutive chunks of one operand row.
+    constexpr int kRowOut = kBf16 ? kIngestRowBytes : kIngestRowBytes / 2;
+    constexpr int kChunks = kRowOut / 16;
 #pragma unroll
-    for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < kIngestPixels * kChunks / 256; ++it) {
         const int idx = it * 256 + threadIdx.x;
-        const int row = idx >> 4, chunk = idx & 15;
+        const int row = idx / kChunks, chunk = idx % kChunks;
         const int64_t pp = (int64_t)tile * kIngestPixels + row;
         if (pp < M) {
             const uint4 v = *reinterpret_cast<const uint4*>(&tile_s[row][chunk * 16]);
-            *reinterpret_cast<uint4*>(op + pp * kstride_bytes + (int64_t)blockIdx.y * kIngestRowBytes +
-                                      chunk * 16) = v;
+            *reinterpret_cast<uint4*>(op + pp * kstride_bytes + (int64_t)blockIdx.y * kRowOut + chunk * 16) = v;
         }
     }
     if (warp == 0 && valid) {
@@ -256,14 +267,14 @@ __device__ __forceinline__ uint32_t warp_transpose32(uint32_t w, int lane) {
 // whole 32-pixel tiles of the region whose first word lies in the chunk: per 32
 // frames, lane i funnel-shifts its frame's 32 pixel bits out of two words, the
 // warp transposes the 32 x 32 bit block (lane j then holds pixel j over the 32
-// frames), and each bit becomes one E4M3 byte (0x38 = 1.0; 4 bits -> 4 bytes by
-// one multiply that spreads them 8 bits apart).  The tile's 32 operand rows of
-// kFB bytes are staged per warp and stored as whole 128-byte lines; one int64
-// atomic per pixel adds the block's count to the marginal sum.
+// frames), and each bit becomes one E2M1 nibble (0x2 = 1.0; 8 bits -> 8 nibbles
+// by three shift-or-mask steps).  The tile's 32 operand rows of kFB / 2 bytes
+// are staged per warp and stored as whole 64-byte row pieces; one int64 atomic
+// per pixel adds the block's count to the marginal sum.
 constexpr int kFB = 128;                 // frames per CTA
 constexpr int kWC = 64;                  // frame words per chunk
 constexpr int kWP = kWC + 1;             // shared row pitch in words (odd)
-constexpr int kStageRow = kFB + 16;      // staged operand row, bytes
+constexpr int kStageRow = kFB / 2 + 16;  // staged operand row (E2M1, two frames per byte), bytes
 constexpr size_t kBitsSmem = sizeof(uint32_t) * kFB * kWP + (size_t)8 * 32 * kStageRow;
 static_assert(kWP % 2 == 1, "odd pitch");
 
@@ -340,22 +351,23 @@ __global__ void __launch_bounds__(256) ingest_bits_kernel(FramesDev A, FramesDev
             }
             const uint32_t col = warp_transpose32(__funnelshift_r(lo, hi, sh), lane);
             cnt += __popc(col);
-            uint32_t o[8];
+            uint32_t o[4];
 #pragma unroll
-            for (int qq = 0; qq < 8; ++qq) {
-                const uint32_t nib = (col >> (4 * qq)) & 0xFu;
-                o[qq] = ((nib * 0x00204081u) & 0x01010101u) * 0x38u;
+            for (int k = 0; k < 4; ++k) {   // frames 8k .. 8k + 7 -> nibbles 0 .. 7 of word k
+                uint32_t x = (col >> (8 * k)) & 0xFFu;
+                x = (x | (x << 12)) & 0x000F000Fu;
+                x = (x | (x << 6)) & 0x03030303u;
+                x = (x | (x << 3)) & 0x11111111u;
+                o[k] = x << 1;
             }
-            uint4* dst = reinterpret_cast<uint4*>(st + lane * kStageRow + g * 32);
-            dst[0] = make_uint4(o[0], o[1], o[2], o[3]);
-            dst[1] = make_uint4(o[4], o[5], o[6], o[7]);
+            *reinterpret_cast<uint4*>(st + lane * kStageRow + g * 16) = make_uint4(o[0], o[1], o[2], o[3]);
         }
         __syncwarp();
         const int64_t p0 = y * d.width + 32 * (int64_t)xt;
 #pragma unroll
-        for (int k = 0; k < 32 * kFB / 16 / 32; ++k) {
-            const int idx = k * 32 + lane, r = idx / (kFB / 16), c16 = idx % (kFB / 16);
-            *reinterpret_cast<uint4*>(op + (p0 + r) * kstride_bytes + f0 + c16 * 16) =
+        for (int k = 0; k < 32 * (kFB / 2) / 16 / 32; ++k) {
+            const int idx = k * 32 + lane, r = idx / (kFB / 32), c16 = idx % (kFB / 32);
+            *reinterpret_cast<uint4*>(op + (p0 + r) * kstride_bytes + f0 / 2 + c16 * 16) =
                 *reinterpret_cast<const uint4*>(st + r * kStageRow + c16 * 16);
         }
         __syncwarp();
@@ -381,7 +393,7 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
     const int64_t Ma = (int64_t)a.height * a.width, Mb = (int64_t)b.height * b.width;
     const int tiles_a = (int)((Ma + kIngestPixels - 1) / kIngestPixels);
     const int tiles_b = (int)((Mb + kIngestPixels - 1) / kIngestPixels);
-    if (!bf16 && bits_fast_ok(a) && bits_fast_ok(b) && kstride_bytes % kFB == 0) {
+    if (!bf16 && bits_fast_ok(a) && bits_fast_ok(b) && (2 * kstride_bytes) % kFB == 0) {
         static bool attr[64] = {};
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
@@ -394,7 +406,7 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
         }
         const int chunks_a = (int)((region_last_word(a) - region_first_word(a)) / kWC + 1);
         const int chunks_b = (int)((region_last_word(b) - region_first_word(b)) / kWC + 1);
-        const int64_t blocks = kstride_bytes / kFB;   // one E4M3 byte per frame
+        const int64_t blocks = 2 * kstride_bytes / kFB;   // two E2M1 frames per byte
         for (int64_t y0 = 0; y0 < blocks; y0 += 65535) {   // grid.y limit
             const int64_t ny = blocks - y0 < 65535 ? blocks - y0 : 65535;
             ingest_bits_kernel<<<dim3((unsigned)(chunks_a + chunks_b), (unsigned)ny), 256, kBitsSmem, st>>>(
@@ -403,7 +415,8 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
         }
         return cudaSuccess;
     }
-    const int64_t frame_tiles = kstride_bytes / kIngestRowBytes;
+    const int64_t row_out = bf16 ? kIngestRowBytes : kIngestRowBytes / 2;   // operand bytes per CTA row
+    const int64_t frame_tiles = kstride_bytes / row_out;
     if (bf16 && u8x4_ok(a) && u8x4_ok(b)) {
         const int xa = (int)((Ma + kX4Pixels - 1) / kX4Pixels), xb = (int)((Mb + kX4Pixels - 1) / kX4Pixels);
         for (int64_t t0 = 0; t0 < frame_tiles; t0 += 65535) {   // grid.y limit
@@ -430,15 +443,11 @@ cudaError_t launch_ingest(bool bf16, const FramesDev& a, const FramesDev& b, int
             const int64_t rem = n_frames - t0 * fpc;
             dim3 grid(tiles_a + tiles_b, (unsigned)nt);
             if (bf16)
-                ingest_kernel<true><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes,
-                                                          op_a + t0 * kIngestRowBytes,
-                                                          op_b + t0 * kIngestRowBytes, s_a, s_b,
-                                                          tiles_a, vmax);
+                ingest_kernel<true><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes, op_a + t0 * row_out,
+                                                          op_b + t0 * row_out, s_a, s_b, tiles_a, vmax);
             else
-                ingest_kernel<false><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes,
-                                                           op_a + t0 * kIngestRowBytes,
-                                                           op_b + t0 * kIngestRowBytes, s_a, s_b,
-                                                           tiles_a, nullptr);
+                ingest_kernel<false><<<grid, 256, 0, st>>>(a2, b2, rem, kstride_bytes, op_a + t0 * row_out,
+                                                           op_b + t0 * row_out, s_a, s_b, tiles_a, nullptr);
         }
         return cudaGetLastError();
     }

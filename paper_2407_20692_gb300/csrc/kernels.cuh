@@ -23,9 +23,9 @@ struct FramesDev {
 
 // ------------------------------------------------------------------ ingest
 // Frames -> K-major tensor-core operands [M][kstride] and marginal sums.
-// kBf16: values as BF16 (any bit depth); else 1-bit values as FP8 E4M3.
+// kBf16: values as BF16 (any bit depth); else 1-bit values as FP4 E2M1, two per byte.
 constexpr int kIngestPixels = 32;                 // pixels per CTA
-constexpr int kIngestRowBytes = 256;              // operand bytes per pixel per CTA
+constexpr int kIngestRowBytes = 256;              // BF16 operand bytes per pixel per CTA (E2M1: half)
 inline int ingest_frames_per_cta(bool bf16) { return bf16 ? 128 : 256; }
 
 // vmax (BF16 path, may be null): the largest A and B value seen is raised into

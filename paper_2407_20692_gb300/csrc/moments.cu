@@ -2,7 +2,8 @@
 // first term of Eq. (1)) on the 5th-generation tensor cores.
 //
 // Operands are the K-major rows written by the ingest step (one row per pixel,
-// K = frames): FP8 E4M3 0/1 values for binary frames (tcgen05 kind::f8f6f4), or
+// K = frames): E2M1 0/1 values for binary frames (tcgen05 kind::f8f6f4, packed
+// two per byte in HBM and spread to 16-byte groups in shared memory by TMA), or
 // BF16 integers 0..255 (kind::f16).  Products are small integers, accumulated
 // in FP32 in tensor memory; a sum of integers stays exact while it is below
 // 2^24, and the schedule guarantees that:
@@ -59,6 +60,9 @@ struct MomentsCfg {
     static constexpr int kKPerBlock = kRowBytes / kElem;     // 64 / 128 elements
     static constexpr int kABytes = kBlockM * kRowBytes;       // 16 KiB
     static constexpr int kBBytes = kBlockN * kRowBytes;       // 32 KiB
+    // bytes a stage's copies deliver: E2M1 rows are 64 bytes in HBM, spread over
+    // the 128-byte shared-memory row (8 bytes of values per 16-byte group)
+    static constexpr uint32_t kTxBytes = kBf16 ? kABytes + kBBytes : (kABytes + kBBytes) / 2;
     // tensor memory (2 x kBN columns): two FP32 accumulators, so the epilogue of
     // one unit (FP8) or segment (BF16) overlaps the MMAs of the next; the BF16
     // int32 running sums live in the epilogue threads' registers
@@ -213,7 +217,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[stage], C::kABytes + C::kBBytes);
+                    mbar_arrive_expect_tx(&full[stage], C::kTxBytes);
                     tma_load_2d(sA + stage * C::kABytes, ma, &full[stage], kb * C::kKPerBlock,
                                 w.tm * kBlockM);
                     tma_load_2d(sB + stage * C::kBBytes, mb, &full[stage], kb * C::kKPerBlock,
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == 1) {
         if (lane == 0) {
             // ---------------------------------------------------------- MMA issuer
-            // The tensor pipe takes one 128 x 256 x 16 (BF16) or x 32 (E4M3) MMA
+            // The tensor pipe takes one 128 x 256 x 16 (BF16) or x 32 (E2M1) MMA
             // per 128 cycles only while this thread issues the next one within
             // that time, so the loop keeps its per-K-block work to a few adds:
             // segment bounds are counted down (no division), descriptors step
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                         stage = 0;
                         phase ^= 1;
                     }
-                    if (seg_left == 0) {   // segment (BF16) or unit (E4M3) done: hand the accumulator over
+                    if (seg_left == 0) {   // segment (BF16) or unit (E2M1) done: hand the accumulator over
                         umma_commit(&tfull[acc]);
                         if (++acc == C::kAcc) {
                             acc = 0;

@@ -189,12 +189,13 @@ __device__ __forceinline__ uint64_t sdesc_kmajor_sw64(uint32_t saddr) {
 }
 
 // Instruction descriptor: D = F32, A and B K-major, shape M x N.
-// kBf16: kind::f16 with BF16 operands; else kind::f8f6f4 with E4M3 operands.
+// kBf16: kind::f16 with BF16 operands (format 1); else kind::f8f6f4 with E2M1
+// operands (format 5: 4-bit values, 16 per 16-byte shared-memory group).
 template <bool kBf16>
 __host__ __device__ constexpr uint32_t idesc_f32acc(int M, int N) {
     return (1u << 4)                                    // D format F32
-           | ((kBf16 ? 1u : 0u) << 7)                   // A format: BF16 (1) / E4M3 (0)
-           | ((kBf16 ? 1u : 0u) << 10)                  // B format
+           | ((kBf16 ? 1u : 5u) << 7)                   // A format: BF16 (1) / E2M1 (5)
+           | ((kBf16 ? 1u : 5u) << 10)                  // B format
            | ((uint32_t)(N >> 3) << 17)                 // N / 8
            | ((uint32_t)(M >> 4) << 24);                // M / 16
 }

@@ -65,11 +65,11 @@ def test_noalloc_equals_workspace_entry_point_on_consecutive_calls():
 
 
 def test_noalloc_refuses_problems_larger_than_its_scratch():
-    acq = synth.CONFIGS["spad_1bit"]     # needs ~120 MB of workspace
-    fr, lay = make_frames(acq, n=4096)
+    acq = synth.CONFIGS["spad_1bit"]     # 16384 frames: ~60 MB of workspace
+    fr, lay = make_frames(acq, n=16384)
     a, b = desc(fr, lay["a"]), desc(fr, lay["b"])
-    assert cpi.cpi_correlate_workspace_size(a, b, 4096) > cpi.NOALLOC_SCRATCH_BYTES
+    assert cpi.cpi_correlate_workspace_size(a, b, 16384) > cpi.NOALLOC_SCRATCH_BYTES
     out = _outputs(4096, 1024)
     with pytest.raises(cpi.CpiError) as e:
-        cpi.cpi_correlate_noalloc(a, b, 4096, *out)
+        cpi.cpi_correlate_noalloc(a, b, 16384, *out)
     assert e.value.code == 3
